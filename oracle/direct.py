@@ -1,0 +1,107 @@
+"""O1, the ground truth: direct FP64 sums with the Gaussian weight matrix.
+
+Test infrastructure (the oracle); see the package docstring for who may use it.
+
+Sec. 2, eq. (W_gaussian): W_ji = exp(-||v_j - v_i||^2 / sigma^2) for j != i,
+W_jj = 0.  Degree d_j = sum_i W_ji; D = diag(d); L = D - W;
+A = D^{-1/2} W D^{-1/2}; L_s = I - A (Sec. 2, eq. (nomlap)).
+Everything is in the original coordinates (no scaling, no shift).
+
+Dense numpy versions for small n; ``rows_W`` sums selected rows over all n
+sources in plain C (direct.c, built by oracle/build.py) for large n.
+
+Pins (tests/test_oracle_direct.py): n = 1 and n = 2 closed forms; L 1 = 0;
+L_s D^{1/2} 1 = 0; the quadratic form u^T L u = 1/2 sum W_ji (u_j - u_i)^2
+(Sec. 2) by an explicit pair loop; spectrum of L_s in [0, 2] with a zero
+eigenvalue; c well-separated clusters give c (numerically) zero eigenvalues;
+the C row sums against the dense matrix.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+
+def weight_matrix(v, sigma):
+    """Dense W (n x n), zero diagonal."""
+    v = np.atleast_2d(np.asarray(v, dtype=np.float64))
+    diff = v[:, None, :] - v[None, :, :]
+    W = np.exp(-(diff ** 2).sum(axis=2) / sigma ** 2)
+    np.fill_diagonal(W, 0.0)
+    return W
+
+
+def degree(v, sigma):
+    return weight_matrix(v, sigma).sum(axis=1)
+
+
+def apply_W(v, sigma, x):
+    return weight_matrix(v, sigma) @ np.asarray(x, dtype=np.float64)
+
+
+def normalized_adjacency(v, sigma):
+    """A = D^{-1/2} W D^{-1/2}."""
+    W = weight_matrix(v, sigma)
+    dinv = 1.0 / np.sqrt(W.sum(axis=1))
+    return dinv[:, None] * W * dinv[None, :]
+
+
+def apply_A(v, sigma, x):
+    return normalized_adjacency(v, sigma) @ np.asarray(x, dtype=np.float64)
+
+
+def apply_Ls(v, sigma, x):
+    x = np.asarray(x, dtype=np.float64)
+    return x - apply_A(v, sigma, x)
+
+
+def laplacian(v, sigma):
+    """L = D - W."""
+    W = weight_matrix(v, sigma)
+    return np.diag(W.sum(axis=1)) - W
+
+
+# --------------------------------------------------------------------------
+# Plain-C row sums for large n.
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = os.path.join(os.path.dirname(__file__), "_build", "liboracle_direct.so")
+        if not os.path.exists(path):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(path)
+        lib.oracle_gauss_rows.restype = ctypes.c_int
+        lib.oracle_gauss_rows.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_max_threads.argtypes = []
+        _LIB = lib
+    return _LIB
+
+
+def max_threads():
+    return int(_lib().oracle_max_threads())
+
+
+def rows_W(v, sigma, x, rows, nthreads=0):
+    """(W x)_j for j in rows, each summed over all n sources, x (n,) or (n, r)."""
+    v = np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
+    n, d = v.shape
+    x = np.asarray(x, dtype=np.float64)
+    squeeze = x.ndim == 1
+    X = np.asfortranarray(x.reshape(n, -1))
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros((rows.size, X.shape[1]), dtype=np.float64, order="F")
+    rc = _lib().oracle_gauss_rows(
+        v.ctypes.data, n, d, float(sigma), X.ctypes.data, X.shape[1], n,
+        rows.ctypes.data, rows.size, out.ctypes.data, int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_gauss_rows: bad arguments")
+    return out[:, 0] if squeeze else out

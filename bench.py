@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Throughput of the normalized-Laplacian product L_s x on one GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch):
+  n = 10,000,000 nodes in d = 3: half uniform in the unit ball, half in five
+  Gaussian clusters (centres at radius 0.6, std 0.04); Gaussian kernel
+  sigma = 0.08; fast summation N = 128, m = 6, p = 6, eps_B = 6/128.
+  A step applies L_s to a block of ``--nrhs`` right-hand sides x ~ N(0, 1)
+  (spread, FFT with the fused multiplier, gather with the fused D^{-1/2}
+  epilogue, per column), with the FP32-compensated arithmetic.
+
+Reported: L_s matvecs/s (columns per second, all ranks), the same through
+host buffers (e2e), the plain FP64 single-vector form on the same data, the
+error of the product against the FP64 direct sum on sampled rows, the
+roofline of the dominant kernel from CUDA events recorded around each stage
+inside the timed region, and the direct-sum oracle timed on the host cores.
+
+``--impl reference`` times the CPU oracle (direct FP64 sums, plain C with
+OpenMP) on a bounded sample of the same workload instead.
+Multi-GPU (torchrun): every rank runs an independent replica on its own GPU
+(weak scaling); the only collectives are the timing barrier and max.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_NODES = 10_000_000
+CFG = dict(sigma=0.08, N=128, m=6, p=6)
+WORKLOAD = ("ball10M: n=10,000,000 d=3, 50% uniform in the unit ball + 50% in 5 Gaussian clusters "
+            "(centres at radius 0.6, std 0.04); Gaussian sigma=0.08; N=128, m=6, p=6, eps_B=6/128")
+METRIC = "L_s matvecs/s (n=10M, d=3) mixed+batched vs FP64 plain, rel err <=1e-6"
+FP32_LANES_PER_SM = 128
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=4)
+    ap.add_argument("--n", type=int, default=N_NODES)
+    ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp32", "fp64"])
+    ap.add_argument("--baseline-rows", type=int, default=1024)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=timestamp," + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (t, l) in self.lines if t0 - 0.25 <= t <= t1 + 0.25] or [l for (_, l) in self.lines]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_sha(path):
+    return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+
+
+def profiled_traffic(kernel_file):
+    """dram bytes per launch from the committed ncu summary, if it matches the current source."""
+    summ = os.path.join(ROOT, "profiles", "spread3_columns_ball10M.md")
+    if not os.path.exists(summ):
+        return None
+    vals = {}
+    for line in open(summ):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != source_sha(kernel_file):
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+def oracle_rows(v, x, rows):
+    from oracle import direct
+    t = time.perf_counter()
+    out = direct.rows_W(v, CFG["sigma"], x, rows)
+    return out, time.perf_counter() - t, direct.max_threads()
+
+
+def run_reference(args, world, rank):
+    """The oracle (direct FP64 sums on the host cores) as the reference arm."""
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_1808_04580_gb300 import workloads
+    v = workloads.ball_plus_clusters(args.n, seed=0)
+    x = workloads.rhs(args.n, seed=1)
+    rng = np.random.default_rng(2)
+    rows_per_step = 64
+    for _ in range(args.warmup):
+        oracle_rows(v, x, rng.choice(args.n, 8, replace=False))
+    total = 0.0
+    cores = 1
+    for _ in range(args.steps):
+        _, dt, cores = oracle_rows(v, x, rng.choice(args.n, rows_per_step, replace=False))
+        total += dt
+    value = rows_per_step * args.steps / total / args.n
+    sample = "%d steps x %d of %d target rows, each summed over all %d sources; matvecs/s extrapolated as rows/s / n" % (
+        args.steps, rows_per_step, args.n, args.n)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "rows_per_step": rows_per_step},
+        "cpu_baseline": {"value": value, "unit": "matvecs/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    from paper_1808_04580_gb300 import Plan, workloads
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n, nrhs = args.n, args.nrhs
+    v = workloads.ball_plus_clusters(n, seed=rank)
+    X = workloads.rhs(n, nrhs=nrhs, seed=rank + 1)
+    X = X.reshape(n, nrhs)
+    vg = torch.from_numpy(v).to(dev)
+    xg = torch.from_numpy(np.asfortranarray(X)).to(dev)
+    plan = Plan(vg, CFG["sigma"], CFG["N"], CFG["m"], CFG["p"], -1.0, args.precision)
+    info = plan.info()
+    ycols = torch.empty((nrhs, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.apply_Ls(xg, out=ycols)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    plan.set_profiling(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall1 = time.time()
+    sampler.stop()
+    stages = plan.stage_times()
+    plan.set_profiling(False)
+    ms_local = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms_local, world)
+    columns = nrhs * args.steps
+    value = world * columns / (ms / 1000.0)
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    # dominant kernel and its roofline (ALU: one multiply-add per window tap)
+    taps = (2 * CFG["m"]) ** 3
+    spread_ms = stages["spread"] / max(1, stages["columns"])
+    gather_ms = stages["gather"] / max(1, stages["columns"])
+    fft_ms = stages["fft"] / max(1, stages["columns"])
+    dom = "spread" if spread_ms >= gather_ms else "gather"
+    dom_ms = max(spread_ms, gather_ms)
+    flops = 2.0 * taps * n
+    achieved = flops / (dom_ms / 1000.0) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    kernel_file = os.path.join(ROOT, "paper_1808_04580_gb300", "csrc",
+                               "spread3.cu" if dom == "spread" else "gather.cu")
+    traffic = profiled_traffic(kernel_file) if dom == "spread" else None
+    hbm_bytes = n * (16 + 8 + 4 + 8)  # node record, x, perm, dinv read once per column
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "spread3_columns" if dom == "spread" else "gather_kernel",
+                "flops_per_launch": flops, "ms_per_launch": dom_ms,
+                "hbm_achieved_gbs": hbm_bytes / (dom_ms / 1000.0) / 1e9,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no measured FP32 peak)"}
+
+    # end to end through the public API with host buffers
+    Xh = torch.from_numpy(np.ascontiguousarray(X.T)).pin_memory()
+    Yh = torch.empty((nrhs, n), dtype=torch.float64).pin_memory()
+    xdev = torch.empty((nrhs, n), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    barrier(world)
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        xdev.copy_(Xh, non_blocking=True)
+        plan.apply_Ls(xdev.t(), out=ycols)
+        Yh.copy_(ycols, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t, world)
+    e2e = {"value": world * nrhs * args.e2e_steps / e2e_s, "unit": "matvecs/s",
+           "h2d_bytes_per_step": n * nrhs * 8, "d2h_bytes_per_step": n * nrhs * 8}
+
+    # plain FP64 single-vector form on the same data
+    fp64 = None
+    x0 = xg[:, 0].contiguous()
+    if args.fp64_steps > 0:
+        p64 = Plan(vg, CFG["sigma"], CFG["N"], CFG["m"], CFG["p"], -1.0, "fp64")
+        y64 = p64.apply_Ls(x0)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.fp64_steps):
+            p64.apply_Ls(x0, out=y64)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(s0.elapsed_time(s1) / args.fp64_steps, world)
+        w64 = p64.apply_W(x0).cpu().numpy()
+        p64.close()
+        fp64 = {"value": world * 1000.0 / ms64, "unit": "matvecs/s", "ms_per_matvec": ms64}
+
+    # accuracy of the timed form: W x on sampled rows against the direct FP64 sum
+    wmix = plan.apply_W(x0).cpu().numpy()
+    err = {}
+    if fp64 is not None:
+        err["vs_gpu_fp64_all_rows"] = float(np.linalg.norm(wmix - w64) / np.linalg.norm(w64))
+    cpu_baseline = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        rows = np.random.default_rng(3).choice(n, args.baseline_rows, replace=False)
+        ref, secs, cores = oracle_rows(v, X[:, 0].copy(), rows)
+        err["vs_direct_sample"] = float(np.linalg.norm(wmix[rows] - ref) / np.linalg.norm(ref))
+        err["sample_rows"] = int(args.baseline_rows)
+        cpu_baseline = {"value": args.baseline_rows / secs / n, "unit": "matvecs/s", "cores": cores,
+                        "kind": "oracle",
+                        "sample": "direct FP64 sum of W x for %d of %d target rows over all %d sources "
+                                  "(plain C, OpenMP), %.1f s; extrapolated as rows/s / n" % (
+                                      args.baseline_rows, n, n, secs)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32+i64" if args.precision == "fp32c" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nrhs_per_step": nrhs, "precision": args.precision,
+                       "l2": "inputs larger than L2 (x block %d MB, node records %d MB)" % (
+                           n * nrhs * 8 // 2**20, n * 16 // 2**20),
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "box": info["box"], "work_items": info["work_items"]},
+            "stage_ms_per_column": {"prep": stages["prep"] / max(1, stages["columns"]), "spread": spread_ms,
+                                    "fft": fft_ms, "gather": gather_ms},
+            "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": (value / world) / fp64["value"] * world if fp64 else None,
+            "rel_err_W": err,
+            "roofline": roofline,
+            "cpu_baseline": cpu_baseline,
+            "e2e": e2e,
+            "gpu_launches": plan.kernels_per_column() * columns,
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

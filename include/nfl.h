@@ -1,0 +1,192 @@
+/*
+ * nfl -- NFFT-based fast summation for the graph Laplacian of fully
+ * connected Gaussian-weighted graphs, on one GB300 GPU (sm_103a).
+ *
+ * Method: Alfke, Potts, Stoll, Volkmer, "NFFT meets Krylov methods: Fast
+ * matrix-vector products for the graph Laplacian of fully connected
+ * networks" (2018).
+ *
+ *   W_ji = exp(-||v_j - v_i||^2 / sigma^2) for j != i, W_jj = 0   (Sec. 2, eq. (W_gaussian))
+ *   d = W 1, D = diag(d), A = D^{-1/2} W D^{-1/2}, L_s = I - A     (Sec. 2, eq. (nomlap))
+ *
+ * W is never formed.  Products with W~ = W + K(0) I use Alg. 1 (adjoint
+ * NFFT, multiply by the Fourier coefficients b_l of the regularized kernel,
+ * NFFT); products with A use Alg. 2 (Sec. 3.1).  A plan performs Alg. 2's
+ * steps 1-4 once; the apply calls perform step 5.
+ *
+ * Conventions for every call below:
+ *   - Pointers named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  The plan owns all of its own device
+ *     memory (sorted nodes, grids, coefficients, D^{-1/2}).
+ *   - Vectors are FP64.  Blocks of r right-hand sides are column-major with
+ *     a leading dimension ld >= n (column c starts at x + c * ld).
+ *   - Work is ordered on the plan's stream.  Apply calls do not synchronize
+ *     the host; plan creation and the solvers do (they read scalars back).
+ *   - Inputs and outputs must not alias.
+ *   - Every call returns an nfl_status.  Errors never trap on the device:
+ *     arguments are checked on the host, numerical failures are reported by
+ *     status, CUDA errors map to NFL_ERR_CUDA.  After NFL_ERR_CUDA the plan
+ *     should be destroyed.
+ */
+#ifndef NFL_H
+#define NFL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nfl_plan nfl_plan;
+
+typedef enum {
+    NFL_OK = 0,
+    NFL_ERR_INVALID_ARG = 1,        /* an argument is out of range (see each call)          */
+    NFL_ERR_NONPOSITIVE_DEGREE = 2, /* min_j d_E,j <= 0: D_E^{-1/2} undefined (Lemma 3.1)  */
+    NFL_ERR_BREAKDOWN = 3,          /* Lanczos beta ~ 0: an invariant subspace was found   */
+    NFL_ERR_NOT_CONVERGED = 4,      /* iteration limit reached before the tolerance        */
+    NFL_ERR_NAN = 5,                /* a NaN or Inf appeared in a solver's scalars          */
+    NFL_ERR_TIMEOUT = 6,            /* a bounded device wait gave up                        */
+    NFL_ERR_CUDA = 7,               /* a CUDA runtime call failed                           */
+    NFL_ERR_OUT_OF_MEMORY = 8       /* a device allocation failed                           */
+} nfl_status;
+
+enum { NFL_KERNEL_GAUSSIAN = 0 };
+
+/* Arithmetic of the spread / FFT / gather steps.  Epilogues (-K(0) x,
+ * D^{-1/2} scaling, x - A x) and all solver scalars are FP64 in every mode.
+ *   FP64  : everything in FP64.
+ *   FP32  : window weights, spreading grid, FFT and interpolation in FP32.
+ *   FP32C : FP32 window weights; the spreading grid is accumulated exactly
+ *           in 64-bit fixed point; FFT in FP64; interpolation in FP32.      */
+enum { NFL_PREC_FP64 = 0, NFL_PREC_FP32 = 1, NFL_PREC_FP32C = 2 };
+
+typedef struct {
+    int64_t n;            /* number of nodes                                   */
+    int d;                /* dimension 1..3                                    */
+    int N, m, p;          /* bandwidth, window cut-off, regularization order   */
+    int precision;        /* NFL_PREC_*                                        */
+    double sigma;         /* kernel width in the caller's coordinates          */
+    double eps_B;         /* regularization width                              */
+    double rho;           /* node scale factor (Alg. 2 step 1)                 */
+    double sigma_tilde;   /* rho * sigma (Alg. 2 step 2)                       */
+    double center[3];     /* bounding-box midpoint subtracted before scaling   */
+    int box[3];           /* extent of the active oversampled grid per axis    */
+    int64_t tiles;        /* non-empty spreading tiles                         */
+    int64_t work_items;   /* tile chunks processed by the spread/gather grids  */
+    double min_degree;    /* min_j d_E,j                                       */
+    double max_degree;    /* max_j d_E,j                                       */
+    int degree_ok;        /* 1 if min_degree > 0 (A, L_s and solvers usable)  */
+} nfl_info;
+
+/*
+ * Alg. 2 steps 1-4 (Sec. 3.1): shift the nodes by their bounding-box
+ * midpoint and scale them by rho = (1/4 - eps_B/2) / max_j ||v_j - c||
+ * (rho = 1 when all nodes coincide), set sigma~ = rho sigma, compute the
+ * coefficients b_l of the regularized kernel by the trapezoidal rule
+ * (Sec. 3, eq. (b_l::K_RF)) and the degrees d_E = W~_E 1 - K(0) 1.
+ *
+ *   v         device, n x d row-major FP64 node coordinates (read only; may
+ *             be freed after the call returns).
+ *   n         >= 1.   d in {1, 2, 3}.
+ *   kernel    NFL_KERNEL_GAUSSIAN.
+ *   sigma     > 0.
+ *   N         bandwidth: a power of two in [4, 512] (Fig. tab:fastsum_param).
+ *   m         window cut-off, 1 <= m <= 12.
+ *   p         regularization smoothness; p <= 0 selects the default p = m.
+ *   eps_B     regularization width in [0, 1/2); eps_B < 0 selects p / N.
+ *   precision NFL_PREC_FP64, NFL_PREC_FP32 or NFL_PREC_FP32C.
+ *   stream    a cudaStream_t (0 = legacy default stream).
+ *   out       receives the plan.
+ *
+ * Returns NFL_OK even when some degree is <= 0; the A / L_s products and the
+ * solvers then return NFL_ERR_NONPOSITIVE_DEGREE (nfl_plan_info tells).
+ */
+nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double sigma,
+                           int N, int m, int p, double eps_B, int precision,
+                           void *stream, nfl_plan **out);
+
+/* Release the plan and its device memory (synchronizes its stream). NULL is ignored. */
+void nfl_plan_destroy(nfl_plan *plan);
+
+/* Copy the plan's parameters and degree summary into *info. */
+nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info);
+
+/* Move subsequent work of the plan to another stream. */
+nfl_status nfl_set_stream(nfl_plan *plan, void *stream);
+
+/* d (device, n FP64, node order of the input) = d_E = W~_E 1 - K(0) 1
+ * (Alg. 2 step 4), as computed at plan creation. */
+nfl_status nfl_degree(const nfl_plan *plan, double *d);
+
+/*
+ * y = W_E x = W~_E x - K(0) x   (Alg. 1 and Sec. 3, W = W~ - K(0) I).
+ * x, y: device FP64 blocks of nrhs >= 1 columns, leading dims ldx, ldy >= n.
+ */
+nfl_status nfl_apply_W(nfl_plan *plan, const double *x, int64_t ldx,
+                       double *y, int64_t ldy, int nrhs);
+
+/* y = A_E x = D_E^{-1/2} (W~_E (D_E^{-1/2} x) - K(0) D_E^{-1/2} x)   (Alg. 2 step 5). */
+nfl_status nfl_apply_A(nfl_plan *plan, const double *x, int64_t ldx,
+                       double *y, int64_t ldy, int nrhs);
+
+/* y = L_s x = x - A_E x   (Sec. 2, eq. (nomlap), with Alg. 2 step 5). */
+nfl_status nfl_apply_Ls(nfl_plan *plan, const double *x, int64_t ldx,
+                        double *y, int64_t ldy, int nrhs);
+
+/*
+ * k smallest eigenpairs of L_s, i.e. the k largest of A (Sec. 2), by the
+ * Lanczos process with full reorthogonalization (Sec. 4, eq. (krylov1)).
+ * Ritz pair (theta, Q_k w) is accepted when |beta_{k+1} w_k| <= tol (Sec. 4).
+ *
+ *   k       1 <= k < n.
+ *   tol     residual tolerance (e.g. 1e-10).
+ *   maxit   maximum Krylov dimension, k < maxit <= min(n, 4096).
+ *   seed    seed of the random start vector.
+ *   evals   host, k FP64: eigenvalues of L_s ascending (1 - theta).
+ *   evecs   device, n x k FP64 column-major (ld = n), unit 2-norm eigenvectors;
+ *           may be NULL.
+ *   iters   host, receives the number of Lanczos steps taken (may be NULL).
+ * Returns NFL_ERR_NOT_CONVERGED (results still written) when maxit steps do
+ * not converge all k pairs.
+ */
+nfl_status nfl_lanczos_k_smallest(nfl_plan *plan, int k, double tol, int maxit,
+                                  uint64_t seed, double *evals, double *evecs, int *iters);
+
+/*
+ * Conjugate gradients for (beta L_s + diag(s)) u = f, the system of Sec. 6.2.2
+ * (eq. (ssl::system) is beta L_s + I).  Stops when ||r||_2 <= tol ||f||_2.
+ *
+ *   beta    > 0.
+ *   shift   device n FP64 diagonal s >= 0 (NULL means s = 1), so that the
+ *           operator is symmetric positive definite.
+ *   f       device n FP64 right-hand side.
+ *   u       device n FP64: initial guess on entry, solution on exit.
+ *   iters   host (may be NULL); relres host (may be NULL): final ||r|| / ||f||.
+ */
+nfl_status nfl_cg_solve(nfl_plan *plan, double beta, const double *shift,
+                        const double *f, double *u, double tol, int maxit,
+                        int *iters, double *relres);
+
+/*
+ * Stage timing (tracing).  When enabled, CUDA events on the plan's stream
+ * bracket the four stages of every product column: prep (grid clear and, for
+ * FP32C, the fixed-point scale), spread, FFT (all passes, multiply fused) and
+ * gather.  nfl_plan_stage_times synchronizes the stream, writes the
+ * accumulated milliseconds per stage into ms[0..3] and the number of columns
+ * timed into *columns, then clears the accumulators.  Disabled by default.
+ */
+nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable);
+nfl_status nfl_plan_stage_times(nfl_plan *plan, double *ms, int64_t *columns);
+
+/* Number of kernel launches one product column makes (for launch accounting). */
+nfl_status nfl_plan_kernels_per_column(const nfl_plan *plan, int *kernels);
+
+/* Human-readable name of a status code. */
+const char *nfl_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NFL_H */

@@ -23,6 +23,7 @@ Readings:
     with the largest admissible rho = (1/4 - eps_B/2) / max_j ||v_j - c||,
     also when the nodes already fit.  K is translation invariant, so the
     shift changes nothing exact.
+  * When all nodes coincide the scale is free; rho = 1.
   * Alg. 1's output is complex because I_N is not symmetric; the matrix
     product for real x is its real part.  The real part of a Hermitian form
     is symmetric, so the resulting operator is exactly symmetric.
@@ -43,9 +44,9 @@ def scale_nodes(v, eps_B):
     v = np.atleast_2d(np.asarray(v, dtype=np.float64))
     c = 0.5 * (v.min(axis=0) + v.max(axis=0))
     radius = np.sqrt(((v - c) ** 2).sum(axis=1)).max()
-    if radius <= 0.0:
-        raise ValueError("all nodes coincide")
-    rho = (0.25 - 0.5 * eps_B) / radius
+    # all nodes coincide (n = 1 included): after the shift every node is 0,
+    # so any rho satisfies ||rho v_j|| <= 1/4 - eps_B/2; take rho = 1.
+    rho = (0.25 - 0.5 * eps_B) / radius if radius > 0.0 else 1.0
     return (v - c) * rho, rho, c
 
 

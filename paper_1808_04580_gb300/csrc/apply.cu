@@ -1,0 +1,100 @@
+// Products with W, A and L_s: Alg. 1 (spread, FFT/multiply/inverse FFT,
+// interpolate) with the Alg. 2 step 5 scalings fused into spread and gather.
+#include "internal.h"
+
+namespace nfl {
+
+int kernels_per_column(const Plan &P) {
+    const int passes = P.d == 1 ? 1 : (P.d == 2 ? 3 : 5);
+    return (P.prec == NFL_PREC_FP32C ? 1 : 0) + 1 + passes + 1;
+}
+
+static cudaError_t mark(Plan &P, int stage) {
+    if (!P.profile) return cudaSuccess;
+    const size_t idx = P.events_used + stage;
+    while (P.events.size() <= idx) {
+        cudaEvent_t e;
+        NFL_CUDA_TRY(cudaEventCreate(&e));
+        P.events.push_back(e);
+    }
+    NFL_CUDA_TRY(cudaEventRecord(P.events[idx], P.stream));
+    if (stage == 4) P.events_used += 5;
+    return cudaSuccess;
+}
+
+nfl_status run_column(Plan &P, int op, const double *x, double *y) {
+    const bool ones = (op == OP_DEGREE);
+    const bool scale = (op == OP_A || op == OP_LS);
+    NFL_STATUS_TRY(mark(P, 0));
+    NFL_STATUS_TRY(prepare_spread(P, x, ones, scale));
+    NFL_STATUS_TRY(mark(P, 1));
+    NFL_STATUS_TRY(launch_spread(P, x, 0, ones, scale));
+    NFL_STATUS_TRY(mark(P, 2));
+    NFL_STATUS_TRY(launch_fft(P));
+    NFL_STATUS_TRY(mark(P, 3));
+    NFL_STATUS_TRY(launch_gather(P, op, x, y));
+    NFL_STATUS_TRY(mark(P, 4));
+    return NFL_OK;
+}
+
+static nfl_status apply(nfl_plan *plan, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
+    if (!plan || !x || !y || nrhs < 1) return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (ldx < P.n || ldy < P.n) return NFL_ERR_INVALID_ARG;
+    if (op != OP_W && !P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
+    for (int c = 0; c < nrhs; ++c) {
+        nfl_status st = run_column(P, op, x + c * ldx, y + c * ldy);
+        if (st != NFL_OK) return st;
+    }
+    return NFL_OK;
+}
+
+}  // namespace nfl
+
+extern "C" {
+
+nfl_status nfl_apply_W(nfl_plan *plan, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
+    return nfl::apply(plan, nfl::OP_W, x, ldx, y, ldy, nrhs);
+}
+
+nfl_status nfl_apply_A(nfl_plan *plan, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
+    return nfl::apply(plan, nfl::OP_A, x, ldx, y, ldy, nrhs);
+}
+
+nfl_status nfl_apply_Ls(nfl_plan *plan, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
+    return nfl::apply(plan, nfl::OP_LS, x, ldx, y, ldy, nrhs);
+}
+
+nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable) {
+    if (!plan) return NFL_ERR_INVALID_ARG;
+    nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plan);
+    P.profile = enable != 0;
+    P.events_used = 0;
+    return NFL_OK;
+}
+
+nfl_status nfl_plan_stage_times(nfl_plan *plan, double *ms, int64_t *columns) {
+    if (!plan || !ms) return NFL_ERR_INVALID_ARG;
+    nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plan);
+    if (cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
+    for (int s = 0; s < 4; ++s) ms[s] = 0.0;
+    const size_t cols = P.events_used / 5;
+    for (size_t c = 0; c < cols; ++c)
+        for (int s = 0; s < 4; ++s) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, P.events[5 * c + s], P.events[5 * c + s + 1]) != cudaSuccess)
+                return NFL_ERR_CUDA;
+            ms[s] += t;
+        }
+    if (columns) *columns = (int64_t)cols;
+    P.events_used = 0;
+    return NFL_OK;
+}
+
+nfl_status nfl_plan_kernels_per_column(const nfl_plan *plan, int *kernels) {
+    if (!plan || !kernels) return NFL_ERR_INVALID_ARG;
+    *kernels = nfl::kernels_per_column(*reinterpret_cast<const nfl::Plan *>(plan));
+    return NFL_OK;
+}
+
+}  // extern "C"

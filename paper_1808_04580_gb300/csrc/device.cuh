@@ -1,0 +1,46 @@
+// Device helpers shared by the spread and gather kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace nfl {
+
+// Normalized Kaiser-Bessel window phi(delta) / phi(0) at grid offset delta,
+// |delta| <= m:  (m / s) sinh(b s) / sinh(b m),  s = sqrt(m^2 - delta^2).
+// Written as  exp(-b delta^2 / (s + m)) * m * (1 - e^{-2 b s}) / (s (1 - e^{-2 b m}))
+// because b (s - m) = -b delta^2 / (s + m) has no cancellation: forming
+// sinh(b s) / sinh(b m) directly in FP32 turns the rounding of b into a
+// relative bias of b m ulp (~2e-6) shared by every weight.  The limit at
+// s = 0 is 2 b m e^{-b m} / (1 - e^{-2 b m}).  phi(0) is put back into the
+// Fourier multiplier.  inv_den = 1 / (1 - e^{-2 b m}).
+template <typename T>
+__device__ __forceinline__ T kb_weight(T delta, T m, T b, T inv_den) {
+    T s2 = m * m - delta * delta;
+    s2 = s2 > T(0) ? s2 : T(0);
+    const T s = sqrt(s2);
+    const T head = exp(-b * delta * delta / (s + m));
+    const T tail = s > T(0) ? -expm1(T(-2) * b * s) / s : T(2) * b;
+    return head * m * tail * inv_den;
+}
+
+__device__ __forceinline__ int cell_axis(int32_t packed, int a) { return (packed >> (10 * a)) & 1023; }
+__device__ __forceinline__ int cell_axis(int64_t packed, int a) { return (int)((packed >> (10 * a)) & 1023); }
+
+template <typename T> struct PointOf;
+template <> struct PointOf<float> { using type = PointF; };
+template <> struct PointOf<double> { using type = PointD; };
+
+// Decompose a linear tile id into per-axis tile coordinates (axis 0 slowest).
+template <int D>
+__device__ __forceinline__ void tile_coords(int32_t tile, const int *ntile, int *tc) {
+    int r = tile;
+    for (int a = D - 1; a >= 0; --a) {
+        tc[a] = r % ntile[a];
+        r /= ntile[a];
+    }
+}
+
+}  // namespace nfl

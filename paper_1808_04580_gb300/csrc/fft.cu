@@ -1,0 +1,265 @@
+// The FFT part of Alg. 1: forward DFT of the spread grid restricted to the
+// kept frequencies, multiplication by the Fourier multiplier (step 2 with
+// both window deconvolutions folded in), inverse DFT back to the active box.
+//
+// The grid holds only the active box (L_a <= n = 2N positions per axis); the
+// rest of the n-periodic line is zero, and only frequencies |k| <= N/2 are
+// kept (k in [0, N/2] on the last axis, whose transform is real-to-complex).
+// Shifting the box origin multiplies the spectrum by a phase that the
+// inverse transform removes again, so box position s is used as FFT index s.
+//
+// Every pass transforms contiguous lines: a CTA loads BB consecutive lines
+// (a, b0..b0+BB-1) of length Lin, runs a radix-2 Stockham FFT of length n on
+// each line in shared memory, and writes the result "rotated" so that b is
+// the fastest output index (out[c' oC + a oA + b]); the next pass then again
+// reads contiguous lines.  3-D sequence (x2 fastest in the spread grid):
+//   F1 axis 2 R2C   h[x0][x1][x2]  -> A[k2][x0][x1]
+//   F2 axis 1 C2C   A[k2][x0][x1]  -> B[k1][k2][x0]
+//   F3 axis 0 fwd, multiply, inv   -> C[x0][k2][k1]
+//   I2 axis 1 inv   C[x0][k2][k1]  -> D[x1][x0][k2]
+//   I1 axis 2 C2R   D[x1][x0][k2]  -> g[x2][x1][x0]
+#include <type_traits>
+
+#include "internal.h"
+
+namespace nfl {
+
+enum PassMode { P_FWD_R2C = 0, P_FWD_C2C = 1, P_FUSED = 2, P_INV_C2C = 3, P_INV_C2R = 4 };
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+struct PassArgs {
+    const void *in;
+    void *out;
+    int nA, nB;
+    int64_t sA, sB;
+    int Lin;
+    int64_t oC, oA;
+    int Lout;
+    int n, logn, N;
+    int BB;
+    const void *tw;       // e^{-2 pi i q / n}, q < n/2
+    const void *M;        // fused multiplier, index ((b * nA) + a) * (N + 1) + (k + N/2)
+    int real_in, real_out;
+    const double *abs_sum;  // int64 fixed-point input: sum |x~| of the spread call
+};
+
+// 2^-k for the fixed-point scale 2^k used by the spread kernel.
+__device__ __forceinline__ double fixed_point_unscale(double abs_sum) {
+    if (!(abs_sum > 0.0)) return 1.0;
+    int e;
+    frexp(abs_sum, &e);
+    int k = 62 - e;
+    k = k > 1000 ? 1000 : (k < -1000 ? -1000 : k);
+    return ldexp(1.0, -k);
+}
+
+// Radix-2 Stockham autosort FFT on nl lines of length n held in x (scratch y).
+// Stage with half-length l and stride s (l s = n/2):  for j < l, k < s
+//   Y[k + 2 j s]     = X[k + j s] + X[k + j s + n/2]
+//   Y[k + 2 j s + s] = (X[k + j s] - X[k + j s + n/2]) w^{j s},  w = e^{-+2 pi i / n}.
+template <typename C>
+__device__ C *stockham(C *x, C *y, int nl, int n, int logn, const C *tw, bool inverse) {
+    const int half = n >> 1;
+    int s = 1;
+    for (int stage = 0; stage < logn; ++stage) {
+        for (int e = threadIdx.x; e < nl * half; e += blockDim.x) {
+            const int line = e / half;
+            const int bidx = e - line * half;
+            const int j = bidx / s;
+            const int k = bidx - j * s;
+            const C *X = x + line * n;
+            C *Y = y + line * n;
+            const C c0 = X[k + j * s];
+            const C c1 = X[k + j * s + half];
+            C w = tw[j * s];
+            if (inverse) w.y = -w.y;
+            Y[k + 2 * j * s] = cadd(c0, c1);
+            Y[k + 2 * j * s + s] = cmul(csub(c0, c1), w);
+        }
+        __syncthreads();
+        C *t = x;
+        x = y;
+        y = t;
+        s <<= 1;
+    }
+    return x;
+}
+
+template <typename T, typename TIN, int MODE>
+__global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *bx = reinterpret_cast<C *>(smem_raw);
+    C *by = bx + a.BB * a.n;
+    const int ai = blockIdx.y;
+    const int b0 = blockIdx.x * a.BB;
+    const int nb = min(a.BB, a.nB - b0);
+    const int n = a.n, N = a.N;
+    const C *tw = reinterpret_cast<const C *>(a.tw);
+
+    for (int e = threadIdx.x; e < a.BB * n; e += blockDim.x) bx[e] = C{T(0), T(0)};
+    __syncthreads();
+
+    double in_scale = 1.0;
+    if (std::is_same<TIN, long long>::value) in_scale = fixed_point_unscale(*a.abs_sum);
+
+    // load
+    for (int e = threadIdx.x; e < nb * a.Lin; e += blockDim.x) {
+        const int bb = e / a.Lin;
+        const int c = e - bb * a.Lin;
+        const int64_t src = ai * a.sA + (int64_t)(b0 + bb) * a.sB + c;
+        C v;
+        if (MODE == P_FWD_R2C || (MODE == P_FUSED && a.real_in)) {
+            const TIN *in = reinterpret_cast<const TIN *>(a.in);
+            v = C{T(double(in[src]) * in_scale), T(0)};
+        } else {
+            v = reinterpret_cast<const C *>(a.in)[src];
+        }
+        if (MODE == P_INV_C2C) {
+            const int k = c - N / 2;
+            bx[bb * n + ((k + n) % n)] = v;
+        } else if (MODE == P_INV_C2R) {
+            bx[bb * n + c] = v;
+            if (c >= 1) bx[bb * n + (n - c)] = C{v.x, -v.y};
+        } else {
+            bx[bb * n + c] = v;
+        }
+    }
+    __syncthreads();
+
+    const bool inverse = (MODE == P_INV_C2C || MODE == P_INV_C2R);
+    C *res = stockham<C>(bx, by, a.BB, n, a.logn, tw, inverse);
+
+    if (MODE == P_FUSED) {
+        const T *M = reinterpret_cast<const T *>(a.M);
+        for (int e = threadIdx.x; e < a.BB * n; e += blockDim.x) {
+            const int bb = e / n;
+            const int q = e - bb * n;
+            const int k = q < n / 2 ? q : q - n;
+            C v = res[e];
+            if (bb < nb && k >= -N / 2 && k <= N / 2) {
+                const T mv = M[((int64_t)(b0 + bb) * a.nA + ai) * (N + 1) + (k + N / 2)];
+                v = C{v.x * mv, v.y * mv};
+            } else {
+                v = C{T(0), T(0)};
+            }
+            res[e] = v;
+        }
+        __syncthreads();
+        C *other = (res == bx) ? by : bx;
+        res = stockham<C>(res, other, a.BB, n, a.logn, tw, true);
+    }
+
+    // store, b fastest
+    for (int e = threadIdx.x; e < nb * a.Lout; e += blockDim.x) {
+        const int cc = e / nb;
+        const int bb = e - cc * nb;
+        int idx;
+        if (MODE == P_FWD_R2C) idx = cc;
+        else if (MODE == P_FWD_C2C) idx = (cc - N / 2 + n) % n;
+        else idx = cc;
+        const C v = res[bb * n + idx];
+        const int64_t dst = cc * a.oC + (int64_t)ai * a.oA + b0 + bb;
+        if (MODE == P_INV_C2R || (MODE == P_FUSED && a.real_out)) reinterpret_cast<T *>(a.out)[dst] = v.x;
+        else reinterpret_cast<C *>(a.out)[dst] = v;
+    }
+}
+
+template <typename T, typename TIN, int MODE>
+static cudaError_t run_pass(Plan &P, PassArgs a) {
+    using C = typename Cplx<T>::type;
+    const int cap = std::is_same<T, float>::value ? 4096 : 2048;
+    int BB = cap / a.n;
+    BB = BB > 16 ? 16 : (BB < 1 ? 1 : BB);
+    if (!std::is_same<T, float>::value && BB > 8) BB = 8;
+    a.BB = BB;
+    const int smem = 2 * BB * a.n * (int)sizeof(C);
+    NFL_CUDA_TRY(cudaFuncSetAttribute(fft_pass<T, TIN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((a.nB + BB - 1) / BB, a.nA);
+    fft_pass<T, TIN, MODE><<<grid, 256, smem, P.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, typename TIN>
+static cudaError_t launch_fft_t(Plan &P) {
+    const int N = P.N, n = P.ngrid;
+    int logn = 0;
+    while ((1 << logn) < n) ++logn;
+    PassArgs base{};
+    base.n = n;
+    base.logn = logn;
+    base.N = N;
+    base.tw = P.twiddle;
+    base.M = P.mult;
+    base.abs_sum = P.scratch;
+    const int64_t L0 = P.L[0], L1 = P.L[1], L2 = P.L[2];
+    if (P.d == 1) {
+        PassArgs a = base;
+        a.in = P.grid; a.out = P.g;
+        a.nA = 1; a.nB = 1; a.sA = 0; a.sB = 0; a.Lin = (int)L0;
+        a.oC = 1; a.oA = 0; a.Lout = (int)L0;
+        a.real_in = 1; a.real_out = 1;
+        return run_pass<T, TIN, P_FUSED>(P, a);
+    }
+    if (P.d == 2) {
+        const int64_t K1 = N / 2 + 1;
+        PassArgs f1 = base;
+        f1.in = P.grid; f1.out = P.bufA;
+        f1.nA = 1; f1.nB = (int)L0; f1.sA = 0; f1.sB = L1; f1.Lin = (int)L1;
+        f1.oC = L0; f1.oA = 0; f1.Lout = (int)K1;
+        NFL_CUDA_TRY((run_pass<T, TIN, P_FWD_R2C>(P, f1)));
+        PassArgs f3 = base;
+        f3.in = P.bufA; f3.out = P.bufB;
+        f3.nA = 1; f3.nB = (int)K1; f3.sA = 0; f3.sB = L0; f3.Lin = (int)L0;
+        f3.oC = K1; f3.oA = 0; f3.Lout = (int)L0;
+        NFL_CUDA_TRY((run_pass<T, T, P_FUSED>(P, f3)));
+        PassArgs i1 = base;
+        i1.in = P.bufB; i1.out = P.g;
+        i1.nA = 1; i1.nB = (int)L0; i1.sA = 0; i1.sB = K1; i1.Lin = (int)K1;
+        i1.oC = L0; i1.oA = 0; i1.Lout = (int)L1;
+        return run_pass<T, T, P_INV_C2R>(P, i1);
+    }
+    const int64_t K2 = N / 2 + 1, K1 = N + 1;
+    PassArgs f1 = base;
+    f1.in = P.grid; f1.out = P.bufA;
+    f1.nA = (int)L0; f1.nB = (int)L1; f1.sA = L1 * L2; f1.sB = L2; f1.Lin = (int)L2;
+    f1.oC = L0 * L1; f1.oA = L1; f1.Lout = (int)K2;
+    NFL_CUDA_TRY((run_pass<T, TIN, P_FWD_R2C>(P, f1)));
+    PassArgs f2 = base;
+    f2.in = P.bufA; f2.out = P.bufB;
+    f2.nA = (int)K2; f2.nB = (int)L0; f2.sA = L0 * L1; f2.sB = L1; f2.Lin = (int)L1;
+    f2.oC = K2 * L0; f2.oA = L0; f2.Lout = (int)K1;
+    NFL_CUDA_TRY((run_pass<T, T, P_FWD_C2C>(P, f2)));
+    PassArgs f3 = base;
+    f3.in = P.bufB; f3.out = P.bufA;
+    f3.nA = (int)K2; f3.nB = (int)K1; f3.sA = L0; f3.sB = K2 * L0; f3.Lin = (int)L0;
+    f3.oC = K2 * K1; f3.oA = K1; f3.Lout = (int)L0;
+    NFL_CUDA_TRY((run_pass<T, T, P_FUSED>(P, f3)));
+    PassArgs i2 = base;
+    i2.in = P.bufA; i2.out = P.bufB;
+    i2.nA = (int)L0; i2.nB = (int)K2; i2.sA = K2 * K1; i2.sB = K1; i2.Lin = (int)K1;
+    i2.oC = L0 * K2; i2.oA = K2; i2.Lout = (int)L1;
+    NFL_CUDA_TRY((run_pass<T, T, P_INV_C2C>(P, i2)));
+    PassArgs i1 = base;
+    i1.in = P.bufB; i1.out = P.g;
+    i1.nA = (int)L1; i1.nB = (int)L0; i1.sA = L0 * K2; i1.sB = K2; i1.Lin = (int)K2;
+    i1.oC = L1 * L0; i1.oA = L0; i1.Lout = (int)L2;
+    return run_pass<T, T, P_INV_C2R>(P, i1);
+}
+
+cudaError_t launch_fft(Plan &P) {
+    if (P.prec == NFL_PREC_FP32) return launch_fft_t<float, float>(P);
+    if (P.prec == NFL_PREC_FP32C) return launch_fft_t<double, long long>(P);
+    return launch_fft_t<double, double>(P);
+}
+
+}  // namespace nfl

@@ -1,0 +1,125 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/nfl.h"
+
+namespace nfl {
+
+// Gather epilogues (Alg. 2 step 5 and its pieces); K(0) = 1 for the Gaussian.
+enum Op { OP_W = 0, OP_A = 1, OP_LS = 2, OP_DEGREE = 3 };
+
+// Per-node record in tile-sorted order: fractional offsets of n v~ - floor(n v~)
+// on each axis and the box-local base cell packed 10 bits per axis.
+struct __align__(16) PointF {
+    float f[3];
+    int32_t cell;
+};
+struct __align__(32) PointD {
+    double f[3];
+    int64_t cell;
+};
+
+// One unit of spread/gather work: a chunk of the nodes of one tile.
+struct WorkItem {
+    int32_t tile;
+    int32_t start;
+    int32_t count;
+    int32_t pad;
+};
+
+constexpr int kMaxM = 12;
+
+struct Plan {
+    // problem
+    int64_t n = 0;
+    int d = 0, N = 0, m = 0, p = 0, prec = 0;
+    double sigma = 0, sigma_t = 0, rho = 1, eps_B = 0;
+    double center[3] = {0, 0, 0};
+    cudaStream_t stream = 0;
+
+    // oversampled grid and its active box
+    int ngrid = 0;              // 2N
+    int L[3] = {1, 1, 1};       // stored box extent per axis (<= ngrid)
+    int wrap[3] = {0, 0, 0};    // 1 when the taps span more than ngrid on that axis
+    int64_t t0[3] = {0, 0, 0};  // global index of box position 0 (information only)
+    int64_t box_elems = 0;
+
+    // tiles and work items
+    int tile_edge = 0;          // cells per tile edge
+    int ntile[3] = {1, 1, 1};
+    int64_t tiles_total = 0, tiles_nonempty = 0;
+    int64_t nitems = 0;
+    WorkItem *items = nullptr;
+
+    // tile-sorted nodes
+    void *pts = nullptr;        // PointF or PointD
+    int32_t *perm = nullptr;    // sorted position -> input index
+    double *dinv_sorted = nullptr;  // D_E^{-1/2} in sorted order
+    double *degree = nullptr;   // d_E in input order
+    double min_deg = 0, max_deg = 0;
+    bool degree_ok = false;
+
+    // window phi(delta)/phi(0) = (m / s) sinh(b s) / sinh(b m), s = sqrt(m^2 - delta^2);
+    // kb_inv_sinh_bm holds 1 / (1 - e^{-2 b m}) for the cancellation-free form
+    double kb_b = 0, kb_inv_sinh_bm = 0;
+
+    // FFT data
+    int K[3] = {1, 1, 1};       // kept frequencies per axis (R2C axis N/2+1, others N+1)
+    void *grid = nullptr;       // spreading grid: float, double or int64 (FP32C)
+    void *bufA = nullptr;       // complex FFT intermediates
+    void *bufB = nullptr;
+    void *g = nullptr;          // interpolation grid (real, FFT type)
+    void *mult = nullptr;       // fused multiplier M_eff (real, FFT type)
+    void *twiddle = nullptr;    // e^{-2 pi i q / ngrid}, q < ngrid/2 (complex, FFT type)
+    double *scratch = nullptr;  // small device scalars (reductions, fixed-point scale)
+    int num_sms = 0;
+
+    // stage timing: 5 events per timed column (before prep, spread, fft, gather, after)
+    bool profile = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+};
+
+// Precision-dependent element types.
+inline bool fft_is_double(int prec) { return prec != NFL_PREC_FP32; }
+inline bool points_are_double(int prec) { return prec == NFL_PREC_FP64; }
+
+// launchers (stream-ordered, no host sync)
+cudaError_t prepare_spread(Plan &P, const double *x, bool ones, bool scale_dinv);
+cudaError_t launch_spread(Plan &P, const double *x, int64_t col_off, bool ones, bool scale_dinv);
+cudaError_t launch_fft(Plan &P);
+cudaError_t launch_gather(Plan &P, int op, const double *x, double *y);
+cudaError_t launch_fixed_scale(Plan &P, const double *x, bool ones, bool scale_dinv);
+
+// the whole Alg. 1 pipeline for one column: y = epilogue(W~ x)
+nfl_status run_column(Plan &P, int op, const double *x, double *y);
+
+// 3-D atomic-free spreading (spread3.cu): tile edge it needs for cut-off m (0: not available)
+int column_tile_edge(int m);
+cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool scale_dinv);
+
+// number of kernels one column launches
+int kernels_per_column(const Plan &P);
+
+// plan-time pieces
+nfl_status compute_coefficients(Plan &P);
+
+}  // namespace nfl
+
+#define NFL_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return _e;                    \
+    } while (0)
+
+#define NFL_STATUS_TRY(expr)                                                         \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess)                                                       \
+            return _e == cudaErrorMemoryAllocation ? NFL_ERR_OUT_OF_MEMORY : NFL_ERR_CUDA; \
+    } while (0)

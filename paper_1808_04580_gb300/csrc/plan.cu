@@ -1,0 +1,723 @@
+// Plan creation: Alg. 2 steps 1-4 (Sec. 3.1) on the device.
+//   step 1  shift by the bounding-box midpoint c, scale by
+//           rho = (1/4 - eps_B/2) / max_j ||v_j - c||                    (Sec. 3)
+//   step 2  sigma~ = rho sigma
+//   step 3  b_l = N^{-d} sum_{j in I_N} K_R(j/N) e^{-2 pi i j.l/N}       (Sec. 3, eq. (b_l::K_RF))
+//   step 4  d_E = W~_E 1 - K(0) 1, D_E^{-1/2}
+// plus the layout work of the fast path: each node's base cell and
+// fractional offsets on the oversampled grid, a counting sort of the nodes
+// into tiles, and the list of tile chunks the spread/gather grids walk.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace nfl {
+
+static constexpr int kChunk = 2048;  // nodes per work item
+
+// ---------------------------------------------------------------- reductions
+__global__ void bbox_partials(const double *v, int64_t n, int d, double *part) {
+    __shared__ double lo[3][256], hi[3][256];
+    double l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;   // fmin/fmax drop NaNs, so non-finite input is tracked separately
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < d; ++a) {
+            const double x = v[i * d + a];
+            l[a] = fmin(l[a], x);
+            h[a] = fmax(h[a], x);
+            bad = bad || !isfinite(x);
+        }
+    for (int a = 0; a < 3; ++a) {
+        lo[a][threadIdx.x] = bad ? NAN : l[a];
+        hi[a][threadIdx.x] = bad ? NAN : h[a];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int a = 0; a < 3; ++a) {
+                const double l2 = lo[a][threadIdx.x + s], h2 = hi[a][threadIdx.x + s];
+                lo[a][threadIdx.x] = (l2 != l2) ? l2 : fmin(lo[a][threadIdx.x], l2);
+                hi[a][threadIdx.x] = (h2 != h2) ? h2 : fmax(hi[a][threadIdx.x], h2);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) { part[blockIdx.x * 6 + a] = lo[a][0]; part[blockIdx.x * 6 + 3 + a] = hi[a][0]; }
+}
+
+__global__ void radius_partials(const double *v, int64_t n, int d, double c0, double c1, double c2, double *part) {
+    __shared__ double red[256];
+    const double c[3] = {c0, c1, c2};
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double r2 = 0.0;
+        for (int a = 0; a < d; ++a) {
+            const double t = v[i * d + a] - c[a];
+            r2 += t * t;
+        }
+        mx = fmax(mx, r2);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void minmax_partials(const double *x, int64_t n, double *part) {
+    __shared__ double lo[256], hi[256];
+    double l = INFINITY, h = -INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double t = x[i];
+        if (t != t) { l = -INFINITY; h = INFINITY; }  // NaN degree: report as failure
+        l = fmin(l, t);
+        h = fmax(h, t);
+    }
+    lo[threadIdx.x] = l;
+    hi[threadIdx.x] = h;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            lo[threadIdx.x] = fmin(lo[threadIdx.x], lo[threadIdx.x + s]);
+            hi[threadIdx.x] = fmax(hi[threadIdx.x], hi[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = lo[0]; part[2 * blockIdx.x + 1] = hi[0]; }
+}
+
+// ------------------------------------------------------- node layout / sort
+struct Geometry {
+    int d;
+    double c[3];
+    double rho;
+    double ngrid;
+    int64_t t0[3];
+    int tile_edge;
+    int ntile[3];
+};
+
+__device__ __forceinline__ void node_cell(const double *v, int64_t i, const Geometry &G, int *cell, double *frac) {
+    for (int a = 0; a < G.d; ++a) {
+        const double u = G.ngrid * (G.rho * (v[i * G.d + a] - G.c[a]));
+        const double base = floor(u);
+        frac[a] = u - base;
+        cell[a] = (int)((int64_t)base - G.t0[a]);
+    }
+}
+
+__device__ __forceinline__ int tile_of(const int *cell, const Geometry &G) {
+    int t = 0;
+    for (int a = 0; a < G.d; ++a) t = t * G.ntile[a] + cell[a] / G.tile_edge;
+    return t;
+}
+
+__global__ void count_tiles(const double *v, int64_t n, Geometry G, int32_t *tile_id, int32_t *rank, int32_t *count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int cell[3];
+        double frac[3];
+        node_cell(v, i, G, cell, frac);
+        const int t = tile_of(cell, G);
+        tile_id[i] = t;
+        rank[i] = atomicAdd(&count[t], 1);
+    }
+}
+
+template <typename PT, typename T>
+__global__ void scatter_nodes(const double *v, int64_t n, Geometry G, const int32_t *tile_id, const int32_t *rank,
+                              const int64_t *start, PT *pts, int32_t *perm) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int cell[3] = {0, 0, 0};
+        double frac[3] = {0, 0, 0};
+        node_cell(v, i, G, cell, frac);
+        const int64_t pos = start[tile_id[i]] + rank[i];
+        PT p;
+        for (int a = 0; a < 3; ++a) p.f[a] = T(a < G.d ? frac[a] : 0.0);
+        p.cell = cell[0] | (cell[1] << 10) | (cell[2] << 20);
+        pts[pos] = p;
+        perm[pos] = (int32_t)i;
+    }
+}
+
+// Single-block exclusive scan of 32-bit counts into 64-bit offsets; out[n] = total.
+__global__ void exclusive_scan(const int32_t *in, int64_t n, int64_t *out) {
+    __shared__ int64_t part[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = threadIdx.x * per, hi = min(n, lo + per);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += in[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int64_t v = part[t];
+            part[t] = acc;
+            acc += v;
+        }
+        out[n] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t i = lo; i < hi; ++i) {
+        out[i] = acc;
+        acc += in[i];
+    }
+}
+
+__global__ void chunks_per_tile(const int32_t *count, int64_t ntiles, int32_t *chunks, unsigned long long *nonempty) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = count[t];
+        chunks[t] = (c + kChunk - 1) / kChunk;
+        if (c > 0) atomicAdd(nonempty, 1ull);
+    }
+}
+
+__global__ void fill_items(const int32_t *count, const int64_t *start, const int64_t *item_off, int64_t ntiles, WorkItem *items) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = count[t];
+        int64_t o = item_off[t];
+        for (int s = 0; s < c; s += kChunk) {
+            WorkItem w;
+            w.tile = (int32_t)t;
+            w.start = (int32_t)(start[t] + s);
+            w.count = min(kChunk, c - s);
+            w.pad = 0;
+            items[o++] = w;
+        }
+    }
+}
+
+// ----------------------------------------------------------- coefficients
+struct KRParams {
+    int N, d;
+    double sigma_t, eps_B;
+    int ncoef;
+    double coef[32];
+};
+
+// K_R(j / N) for j in I_N^d, axis 0 slowest (Sec. 3, the K_R ansatz).
+__global__ void kr_samples(double *S, KRParams p) {
+    int64_t total = 1;
+    for (int a = 0; a < p.d; ++a) total *= p.N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e;
+        double r2 = 0.0;
+        for (int a = p.d - 1; a >= 0; --a) {
+            const int j = (int)(r % p.N) - p.N / 2;
+            r /= p.N;
+            const double y = double(j) / p.N;
+            r2 += y * y;
+        }
+        const double rr = sqrt(r2);
+        double val;
+        const double a0 = 0.5 - p.eps_B;
+        if (p.eps_B <= 0.0 || rr <= a0) {
+            const double q = fmin(rr, 0.5) / p.sigma_t;
+            val = exp(-q * q);
+        } else {
+            const double s = (fmin(rr, 0.5) - a0) / p.eps_B;
+            val = 0.0;
+            for (int k = p.ncoef - 1; k >= 0; --k) val = val * s + p.coef[k];
+        }
+        S[e] = val;
+    }
+}
+
+// out = sum_{j in I_N} in[.., j, ..] cos(2 pi j l / N), l in [0, N/2], along axis ax.
+__global__ void cosine_axis(const double *in, double *out, int64_t outer, int N, int64_t inner, const double *ctab) {
+    const int K = N / 2 + 1;
+    const int64_t total = outer * K * inner;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ii = e % inner;
+        const int64_t rest = e / inner;
+        const int l = (int)(rest % K);
+        const int64_t o = rest / K;
+        const double *src = in + o * N * inner + ii;
+        double acc = 0.0;
+        for (int jj = 0; jj < N; ++jj) {
+            const int j = jj - N / 2;
+            int q = (j * l) % N;
+            if (q < 0) q += N;
+            acc += src[(int64_t)jj * inner] * ctab[q];
+        }
+        out[e] = acc;
+    }
+}
+
+struct MultParams {
+    int N, d;
+    int64_t nA, nB;
+    double inv_Nd;
+};
+
+// M_eff(l) = b_|l| * prod_a dec(|l_a|) * w(l) in the fused pass's layout.
+// w(l) keeps the real part of the sum over I_N exactly: 1 when no |l_a| = N/2,
+// 1/2 when all components with |l_a| = N/2 have the same sign, else 0.
+template <typename T>
+__global__ void build_multiplier(const double *bsum, const double *dec, MultParams p, T *M) {
+    const int N = p.N, K0 = N + 1, Kh = N / 2 + 1;
+    const int64_t total = p.nA * p.nB * K0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j0 = (int)(e % K0);
+        const int64_t line = e / K0;
+        const int64_t a = line % p.nA;
+        const int64_t b = line / p.nA;
+        int k[3] = {0, 0, 0};
+        k[0] = j0 - N / 2;
+        if (p.d == 2) k[1] = (int)b;                 // R2C axis, >= 0
+        if (p.d == 3) { k[1] = (int)b - N / 2; k[2] = (int)a; }
+        int64_t bi = 0;
+        double prod = 1.0;
+        int npos = 0, nneg = 0;
+        for (int ax = 0; ax < p.d; ++ax) {
+            const int ak = abs(k[ax]);
+            bi = bi * Kh + ak;
+            prod *= dec[ak];
+            if (ak == N / 2) { if (k[ax] > 0) ++npos; else ++nneg; }
+        }
+        double w = 1.0;
+        if (npos + nneg > 0) w = (npos == 0 || nneg == 0) ? 0.5 : 0.0;
+        M[e] = T(bsum[bi] * p.inv_Nd * prod * w);
+    }
+}
+
+// ---------------------------------------------------------------- host math
+static double hermite_phys(int k, double x) {
+    double h0 = 1.0, h1 = 2.0 * x;
+    if (k == 0) return h0;
+    for (int j = 1; j < k; ++j) {
+        const double h2 = 2.0 * x * h1 - 2.0 * j * h0;
+        h0 = h1;
+        h1 = h2;
+    }
+    return h1;
+}
+
+// k-th r-derivative of exp(-(r/sigma)^2): (-1/sigma)^k H_k(r/sigma) exp(-(r/sigma)^2).
+static double gauss_deriv(double r, double sigma, int k) {
+    const double x = r / sigma;
+    return std::pow(-1.0 / sigma, k) * hermite_phys(k, x) * std::exp(-x * x);
+}
+
+// Two-point Taylor polynomial T_B(r) = sum_k c_k s^k, s = (r - a)/eps_B, a = 1/2 - eps_B:
+// T_B^(k)(a) = K^(k)(a) for k < p;  T_B(1/2) = K(1/2), T_B^(k)(1/2) = 0 for 1 <= k < p.
+static bool boundary_coefficients(double sigma, double eps_B, int p, double *c) {
+    const double a = 0.5 - eps_B;
+    double fact = 1.0;
+    for (int k = 0; k < p; ++k) {
+        if (k > 0) fact *= k;
+        c[k] = gauss_deriv(a, sigma, k) * std::pow(eps_B, k) / fact;
+    }
+    auto dpow = [](int k, int j) {
+        if (k < j) return 0.0;
+        double r = 1.0;
+        for (int t = k - j + 1; t <= k; ++t) r *= t;
+        return r;
+    };
+    std::vector<double> A(p * p), rhs(p);
+    for (int j = 0; j < p; ++j) {
+        double s = (j == 0) ? std::exp(-0.25 / (sigma * sigma)) : 0.0;
+        for (int k = 0; k < p; ++k) s -= c[k] * dpow(k, j);
+        rhs[j] = s;
+        for (int col = 0; col < p; ++col) A[j * p + col] = dpow(p + col, j);
+    }
+    for (int col = 0; col < p; ++col) {  // Gaussian elimination, partial pivoting
+        int piv = col;
+        for (int r = col + 1; r < p; ++r)
+            if (std::fabs(A[r * p + col]) > std::fabs(A[piv * p + col])) piv = r;
+        if (A[piv * p + col] == 0.0) return false;
+        if (piv != col) {
+            for (int t = 0; t < p; ++t) std::swap(A[col * p + t], A[piv * p + t]);
+            std::swap(rhs[col], rhs[piv]);
+        }
+        for (int r = col + 1; r < p; ++r) {
+            const double f = A[r * p + col] / A[col * p + col];
+            for (int t = col; t < p; ++t) A[r * p + t] -= f * A[col * p + t];
+            rhs[r] -= f * rhs[col];
+        }
+    }
+    for (int r = p - 1; r >= 0; --r) {
+        double s = rhs[r];
+        for (int t = r + 1; t < p; ++t) s -= A[r * p + t] * c[p + t];
+        c[p + r] = s / A[r * p + r];
+    }
+    return true;
+}
+
+// Modified Bessel function I_0 by its power series sum ((z/2)^2)^k / (k!)^2.
+static double bessel_i0(double z) {
+    const double q = 0.25 * z * z;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= q / (double(k) * k);
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+nfl_status compute_coefficients(Plan &P) {
+    const int N = P.N, d = P.d, Kh = N / 2 + 1;
+    KRParams kp{};
+    kp.N = N;
+    kp.d = d;
+    kp.sigma_t = P.sigma_t;
+    kp.eps_B = P.eps_B;
+    kp.ncoef = 0;
+    if (P.eps_B > 0.0) {
+        if (2 * P.p > 32) return NFL_ERR_INVALID_ARG;
+        if (!boundary_coefficients(P.sigma_t, P.eps_B, P.p, kp.coef)) return NFL_ERR_INVALID_ARG;
+        kp.ncoef = 2 * P.p;
+    }
+    int64_t full = 1;
+    for (int a = 0; a < d; ++a) full *= N;
+    double *S = nullptr, *T1 = nullptr, *ctab = nullptr, *dec = nullptr;
+    auto cleanup = [&]() { cudaFree(S); cudaFree(T1); cudaFree(ctab); cudaFree(dec); };
+    if (cudaMalloc(&S, full * sizeof(double)) != cudaSuccess || cudaMalloc(&T1, full * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctab, N * sizeof(double)) != cudaSuccess || cudaMalloc(&dec, Kh * sizeof(double)) != cudaSuccess) {
+        cleanup();
+        return NFL_ERR_OUT_OF_MEMORY;
+    }
+    std::vector<double> h_ct(N), h_dec(Kh);
+    for (int q = 0; q < N; ++q) h_ct[q] = std::cos(2.0 * M_PI * q / N);
+    // dec(k) = (phi(0) / (n phi_hat(k)))^2 = (phi(0) / I_0(m sqrt(b^2 - (2 pi k / n)^2)))^2
+    const double b = P.kb_b, m = P.m, n = P.ngrid;
+    const double phi0 = std::sinh(b * m) / (M_PI * m);
+    for (int k = 0; k < Kh; ++k) {
+        const double arg = b * b - std::pow(2.0 * M_PI * k / n, 2);
+        const double r = phi0 / bessel_i0(m * std::sqrt(arg));
+        h_dec[k] = r * r;
+    }
+    cudaStream_t s = P.stream;
+    if (cudaMemcpyAsync(ctab, h_ct.data(), N * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dec, h_dec.data(), Kh * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cleanup();
+        return NFL_ERR_CUDA;
+    }
+    const int blocks = P.num_sms * 8;
+    kr_samples<<<blocks, 256, 0, s>>>(S, kp);
+    // cosine transform along each axis, last axis first
+    int64_t ext[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) ext[a] = N;
+    double *src = S, *dst = T1;
+    for (int ax = d - 1; ax >= 0; --ax) {
+        int64_t outer = 1, inner = 1;
+        for (int a = 0; a < ax; ++a) outer *= ext[a];
+        for (int a = ax + 1; a < d; ++a) inner *= ext[a];
+        cosine_axis<<<blocks, 256, 0, s>>>(src, dst, outer, N, inner, ctab);
+        ext[ax] = Kh;
+        std::swap(src, dst);
+    }
+    MultParams mp;
+    mp.N = N;
+    mp.d = d;
+    mp.inv_Nd = 1.0 / double(full);
+    if (d == 1) { mp.nA = 1; mp.nB = 1; }
+    else if (d == 2) { mp.nA = 1; mp.nB = Kh; }
+    else { mp.nA = Kh; mp.nB = N + 1; }
+    if (fft_is_double(P.prec)) build_multiplier<double><<<blocks, 256, 0, s>>>(src, dec, mp, (double *)P.mult);
+    else build_multiplier<float><<<blocks, 256, 0, s>>>(src, dec, mp, (float *)P.mult);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    return e == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+}
+
+static void free_plan(Plan *P) {
+    if (!P) return;
+    for (cudaEvent_t e : P->events) cudaEventDestroy(e);
+    cudaFree(P->items);
+    cudaFree(P->pts);
+    cudaFree(P->perm);
+    cudaFree(P->dinv_sorted);
+    cudaFree(P->degree);
+    cudaFree(P->grid);
+    cudaFree(P->bufA);
+    cudaFree(P->bufB);
+    cudaFree(P->g);
+    cudaFree(P->mult);
+    cudaFree(P->twiddle);
+    cudaFree(P->scratch);
+    delete P;
+}
+
+static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sigma, int N, int m, int p,
+                                   double eps_B, int prec, cudaStream_t stream, Plan *P) {
+    P->n = n; P->d = d; P->N = N; P->m = m; P->p = p; P->prec = prec;
+    P->sigma = sigma; P->eps_B = eps_B; P->stream = stream;
+    P->ngrid = 2 * N;
+    P->kb_b = M_PI * (2.0 - 1.0 / 2.0);
+    P->kb_inv_sinh_bm = 1.0 / -std::expm1(-2.0 * P->kb_b * m);   // 1 / (1 - e^{-2 b m})
+    int dev = 0;
+    NFL_STATUS_TRY(cudaGetDevice(&dev));
+    NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    NFL_STATUS_TRY(cudaMalloc(&P->scratch, 64 * sizeof(double)));
+
+    const int rblocks = 1024;
+    double *part = nullptr;
+    NFL_STATUS_TRY(cudaMalloc(&part, rblocks * 6 * sizeof(double)));
+    std::vector<double> hp(rblocks * 6);
+    // step 1: bounding box, centre, radius, rho
+    bbox_partials<<<rblocks, 256, 0, stream>>>(v, n, d, part);
+    cudaError_t ce = cudaMemcpyAsync(hp.data(), part, rblocks * 6 * sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) { cudaFree(part); return NFL_ERR_CUDA; }
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+        for (int b = 0; b < rblocks; ++b) {
+            lo[a] = std::fmin(lo[a], hp[b * 6 + a]);
+            hi[a] = std::fmax(hi[a], hp[b * 6 + 3 + a]);
+            if (std::isnan(hp[b * 6 + a]) || std::isnan(hp[b * 6 + 3 + a])) lo[a] = NAN;
+        }
+        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a])) { cudaFree(part); return NFL_ERR_INVALID_ARG; }
+        P->center[a] = 0.5 * (lo[a] + hi[a]);
+    }
+    radius_partials<<<rblocks, 256, 0, stream>>>(v, n, d, P->center[0], P->center[1], P->center[2], part);
+    ce = cudaMemcpyAsync(hp.data(), part, rblocks * sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) { cudaFree(part); return NFL_ERR_CUDA; }
+    double r2 = 0.0;
+    for (int b = 0; b < rblocks; ++b) r2 = std::fmax(r2, hp[b]);
+    const double radius = std::sqrt(r2);
+    P->rho = radius > 0.0 ? (0.25 - 0.5 * eps_B) / radius : 1.0;   // all nodes coincide: any rho fits
+    P->sigma_t = P->rho * sigma;                                    // step 2
+
+    // active box: cells floor(n v~) - t0 with t0 leaving m taps (and one cell) of room
+    Geometry G{};
+    G.d = d;
+    G.rho = P->rho;
+    G.ngrid = P->ngrid;
+    for (int a = 0; a < 3; ++a) G.c[a] = P->center[a];
+    // 3-D: the column spreading kernel's tile edge where it exists; otherwise
+    // tile + halo must fit shared memory at 8 bytes per cell: (T + 2m - 1)^3 <= 29^3
+    if (d == 3) P->tile_edge = column_tile_edge(m) > 0 ? column_tile_edge(m) : std::min(8, 30 - 2 * m);
+    else P->tile_edge = d == 2 ? 32 : 256;
+    G.tile_edge = P->tile_edge;
+    P->box_elems = 1;
+    for (int a = 0; a < d; ++a) {
+        const double umin = P->ngrid * (P->rho * (lo[a] - P->center[a]));
+        const double umax = P->ngrid * (P->rho * (hi[a] - P->center[a]));
+        const int64_t bmin = (int64_t)std::floor(umin), bmax = (int64_t)std::floor(umax);
+        P->t0[a] = bmin - (m - 1) - 1;
+        G.t0[a] = P->t0[a];
+        const int64_t span = bmax - P->t0[a] + m + 2;   // box positions touched, unwrapped
+        if (span > 1023) { cudaFree(part); return NFL_ERR_INVALID_ARG; }
+        P->wrap[a] = span > P->ngrid ? 1 : 0;
+        P->L[a] = (int)(span > P->ngrid ? P->ngrid : span);
+        P->ntile[a] = (int)((span + P->tile_edge - 1) / P->tile_edge);
+        G.ntile[a] = P->ntile[a];
+        P->box_elems *= P->L[a];
+    }
+    cudaFree(part);
+    P->tiles_total = 1;
+    for (int a = 0; a < d; ++a) P->tiles_total *= P->ntile[a];
+
+    // counting sort of the nodes by tile
+    int32_t *tile_id = nullptr, *rank = nullptr, *count = nullptr, *chunks = nullptr;
+    int64_t *start = nullptr, *item_off = nullptr;
+    unsigned long long *nonempty = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(tile_id); cudaFree(rank); cudaFree(count); cudaFree(chunks);
+        cudaFree(start); cudaFree(item_off); cudaFree(nonempty);
+    };
+    const int64_t nt = P->tiles_total;
+    if (cudaMalloc(&tile_id, n * 4) != cudaSuccess || cudaMalloc(&rank, n * 4) != cudaSuccess ||
+        cudaMalloc(&count, nt * 4) != cudaSuccess || cudaMalloc(&chunks, nt * 4) != cudaSuccess ||
+        cudaMalloc(&start, (nt + 1) * 8) != cudaSuccess || cudaMalloc(&item_off, (nt + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&nonempty, 8) != cudaSuccess) {
+        cleanup();
+        return NFL_ERR_OUT_OF_MEMORY;
+    }
+    const bool dbl = points_are_double(prec);
+    if (cudaMalloc(&P->pts, n * (dbl ? sizeof(PointD) : sizeof(PointF))) != cudaSuccess ||
+        cudaMalloc(&P->perm, n * 4) != cudaSuccess || cudaMalloc(&P->dinv_sorted, n * 8) != cudaSuccess ||
+        cudaMalloc(&P->degree, n * 8) != cudaSuccess) {
+        cleanup();
+        return NFL_ERR_OUT_OF_MEMORY;
+    }
+    const int blocks = P->num_sms * 8;
+    ce = cudaMemsetAsync(count, 0, nt * 4, stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(nonempty, 0, 8, stream);
+    if (ce != cudaSuccess) { cleanup(); return NFL_ERR_CUDA; }
+    count_tiles<<<blocks, 256, 0, stream>>>(v, n, G, tile_id, rank, count);
+    exclusive_scan<<<1, 1024, 0, stream>>>(count, nt, start);
+    if (dbl) scatter_nodes<PointD, double><<<blocks, 256, 0, stream>>>(v, n, G, tile_id, rank, start, (PointD *)P->pts, P->perm);
+    else scatter_nodes<PointF, float><<<blocks, 256, 0, stream>>>(v, n, G, tile_id, rank, start, (PointF *)P->pts, P->perm);
+    chunks_per_tile<<<blocks, 256, 0, stream>>>(count, nt, chunks, nonempty);
+    exclusive_scan<<<1, 1024, 0, stream>>>(chunks, nt, item_off);
+    unsigned long long h_nonempty = 0;
+    ce = cudaMemcpyAsync(&P->nitems, item_off + nt, 8, cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_nonempty, nonempty, 8, cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) { cleanup(); return NFL_ERR_CUDA; }
+    P->tiles_nonempty = (int64_t)h_nonempty;
+    if (cudaMalloc(&P->items, std::max<int64_t>(P->nitems, 1) * sizeof(WorkItem)) != cudaSuccess) {
+        cleanup();
+        return NFL_ERR_OUT_OF_MEMORY;
+    }
+    fill_items<<<blocks, 256, 0, stream>>>(count, start, item_off, nt, P->items);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    cleanup();
+    if (ce != cudaSuccess) return NFL_ERR_CUDA;
+
+    // FFT buffers, twiddles, multiplier
+    const bool fd = fft_is_double(prec);
+    const size_t real_sz = fd ? 8 : 4, cplx_sz = 2 * real_sz;
+    const int64_t Kh = N / 2 + 1, K0 = N + 1;
+    const int64_t L0 = P->L[0], L1 = P->L[1], L2 = P->L[2];
+    int64_t bufA = 1, bufB = 1, mult = K0;
+    if (d == 2) { bufA = Kh * L0; bufB = Kh * L0; mult = Kh * K0; }
+    if (d == 3) {
+        bufA = std::max(Kh * L0 * L1, Kh * K0 * L0);
+        bufB = std::max(K0 * Kh * L0, L1 * L0 * Kh);
+        mult = K0 * Kh * K0;
+    }
+    const size_t grid_sz = prec == NFL_PREC_FP32 ? 4 : 8;
+    if (cudaMalloc(&P->grid, P->box_elems * grid_sz) != cudaSuccess ||
+        cudaMalloc(&P->bufA, bufA * cplx_sz) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz) != cudaSuccess ||
+        cudaMalloc(&P->g, P->box_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
+        cudaMalloc(&P->twiddle, (P->ngrid / 2) * cplx_sz) != cudaSuccess)
+        return NFL_ERR_OUT_OF_MEMORY;
+    {
+        const int half = P->ngrid / 2;
+        std::vector<double> tw(2 * half);
+        for (int q = 0; q < half; ++q) {
+            tw[2 * q] = std::cos(2.0 * M_PI * q / P->ngrid);
+            tw[2 * q + 1] = -std::sin(2.0 * M_PI * q / P->ngrid);
+        }
+        if (fd) {
+            NFL_STATUS_TRY(cudaMemcpy(P->twiddle, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> twf(tw.begin(), tw.end());
+            NFL_STATUS_TRY(cudaMemcpy(P->twiddle, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice));
+        }
+    }
+    nfl_status st = compute_coefficients(*P);   // step 3
+    if (st != NFL_OK) return st;
+
+    // step 4: degrees through the fast path with x = 1
+    st = run_column(*P, OP_DEGREE, nullptr, nullptr);
+    if (st != NFL_OK) return st;
+    double *mm = nullptr;
+    NFL_STATUS_TRY(cudaMalloc(&mm, rblocks * 2 * sizeof(double)));
+    minmax_partials<<<rblocks, 256, 0, stream>>>(P->degree, n, mm);
+    ce = cudaMemcpyAsync(hp.data(), mm, rblocks * 2 * sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    cudaFree(mm);
+    if (ce != cudaSuccess) return NFL_ERR_CUDA;
+    P->min_deg = INFINITY;
+    P->max_deg = -INFINITY;
+    for (int b = 0; b < rblocks; ++b) {
+        P->min_deg = std::fmin(P->min_deg, hp[2 * b]);
+        P->max_deg = std::fmax(P->max_deg, hp[2 * b + 1]);
+    }
+    P->degree_ok = P->min_deg > 0.0 && std::isfinite(P->max_deg);
+    return NFL_OK;
+}
+
+}  // namespace nfl
+
+using nfl::Plan;
+
+extern "C" {
+
+const char *nfl_status_string(int s) {
+    switch (s) {
+        case NFL_OK: return "ok";
+        case NFL_ERR_INVALID_ARG: return "invalid argument";
+        case NFL_ERR_NONPOSITIVE_DEGREE: return "non-positive degree: D^{-1/2} undefined";
+        case NFL_ERR_BREAKDOWN: return "Lanczos breakdown (invariant subspace)";
+        case NFL_ERR_NOT_CONVERGED: return "not converged";
+        case NFL_ERR_NAN: return "NaN or Inf in solver scalars";
+        case NFL_ERR_TIMEOUT: return "bounded device wait timed out";
+        case NFL_ERR_CUDA: return "CUDA runtime error";
+        case NFL_ERR_OUT_OF_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double sigma, int N, int m, int p,
+                           double eps_B, int precision, void *stream, nfl_plan **out) {
+    if (!out) return NFL_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!v || n < 1 || n > 0x7fffffff || d < 1 || d > 3 || kernel != NFL_KERNEL_GAUSSIAN) return NFL_ERR_INVALID_ARG;
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return NFL_ERR_INVALID_ARG;
+    if (N < 4 || N > 512 || (N & (N - 1)) != 0) return NFL_ERR_INVALID_ARG;
+    if (m < 1 || m > nfl::kMaxM) return NFL_ERR_INVALID_ARG;
+    if (p <= 0) p = m;
+    if (p > 16) return NFL_ERR_INVALID_ARG;
+    if (eps_B < 0.0) eps_B = double(p) / N;
+    if (!(eps_B < 0.5)) return NFL_ERR_INVALID_ARG;
+    if (precision != NFL_PREC_FP64 && precision != NFL_PREC_FP32 && precision != NFL_PREC_FP32C)
+        return NFL_ERR_INVALID_ARG;
+    Plan *P = new (std::nothrow) Plan();
+    if (!P) return NFL_ERR_OUT_OF_MEMORY;
+    nfl_status st = nfl::plan_create_impl(v, n, d, sigma, N, m, p, eps_B, precision, (cudaStream_t)stream, P);
+    if (st != NFL_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        nfl::free_plan(P);
+        return st;
+    }
+    *out = reinterpret_cast<nfl_plan *>(P);
+    return NFL_OK;
+}
+
+void nfl_plan_destroy(nfl_plan *plan) {
+    if (!plan) return;
+    Plan *P = reinterpret_cast<Plan *>(plan);
+    cudaStreamSynchronize(P->stream);
+    nfl::free_plan(P);
+}
+
+nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
+    if (!plan || !info) return NFL_ERR_INVALID_ARG;
+    const Plan *P = reinterpret_cast<const Plan *>(plan);
+    std::memset(info, 0, sizeof(*info));
+    info->n = P->n;
+    info->d = P->d;
+    info->N = P->N;
+    info->m = P->m;
+    info->p = P->p;
+    info->precision = P->prec;
+    info->sigma = P->sigma;
+    info->eps_B = P->eps_B;
+    info->rho = P->rho;
+    info->sigma_tilde = P->sigma_t;
+    for (int a = 0; a < 3; ++a) {
+        info->center[a] = P->center[a];
+        info->box[a] = a < P->d ? P->L[a] : 1;
+    }
+    info->tiles = P->tiles_nonempty;
+    info->work_items = P->nitems;
+    info->min_degree = P->min_deg;
+    info->max_degree = P->max_deg;
+    info->degree_ok = P->degree_ok ? 1 : 0;
+    return NFL_OK;
+}
+
+nfl_status nfl_set_stream(nfl_plan *plan, void *stream) {
+    if (!plan) return NFL_ERR_INVALID_ARG;
+    reinterpret_cast<Plan *>(plan)->stream = (cudaStream_t)stream;
+    return NFL_OK;
+}
+
+nfl_status nfl_degree(const nfl_plan *plan, double *d) {
+    if (!plan || !d) return NFL_ERR_INVALID_ARG;
+    const Plan *P = reinterpret_cast<const Plan *>(plan);
+    return cudaMemcpyAsync(d, P->degree, P->n * sizeof(double), cudaMemcpyDeviceToDevice, P->stream) == cudaSuccess
+               ? NFL_OK
+               : NFL_ERR_CUDA;
+}
+
+}  // extern "C"

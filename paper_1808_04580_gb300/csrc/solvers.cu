@@ -1,0 +1,437 @@
+// Krylov solvers on top of the fast products, all vector work in FP64 on
+// the device.
+//
+// Lanczos (Sec. 4): q_1 = r / ||r||, and for j = 1, 2, ...
+//   w = A q_j,  alpha_j = q_j^T w,  w -= alpha_j q_j + beta_j q_{j-1},
+//   full reorthogonalization w -= Q_j (Q_j^T w), done twice (classical
+//   Gram-Schmidt twice, DGKS), beta_{j+1} = ||w||, q_{j+1} = w / beta_{j+1},
+// so that A Q_k = Q_k T_k + beta_{k+1} q_{k+1} e_k^T (eq. (krylov1)).
+// Ritz pairs (theta, Q_k s) of T_k have residual |beta_{k+1} s_k| (Sec. 4);
+// the k largest theta of A give the k smallest eigenvalues 1 - theta of L_s.
+// T_k is diagonalised on the device by implicit QL with Wilkinson shifts.
+//
+// CG (Sec. 6.2.2, eq. (ssl::system)): conjugate gradients on the SPD
+// operator u -> beta L_s u + diag(s) u, stopping at ||r|| <= tol ||f||.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace nfl {
+
+static constexpr int kRedBlocks = 512;
+
+// ---------------------------------------------------------- vector kernels
+__global__ void dot_partials(const double *a, const double *b, int64_t n, double *part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += a[i] * b[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// c[t] = sum_i Q[i + t n] w[i] for t < ncol: grid (kRedBlocks, ncol) of partials.
+__global__ void multidot_partials(const double *Q, int64_t n, const double *w, double *part) {
+    __shared__ double red[256];
+    const int t = blockIdx.y;
+    const double *q = Q + (int64_t)t * n;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += q[i] * w[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)t * gridDim.x + blockIdx.x] = red[0];
+}
+
+// out[t] = sum of the nblk partials of column t, in a fixed order.
+__global__ void sum_partials(const double *part, int nblk, int ncol, double *out) {
+    __shared__ double red[256];
+    for (int t = blockIdx.x; t < ncol; t += gridDim.x) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[(int64_t)t * nblk + i];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[t] = red[0];
+        __syncthreads();
+    }
+}
+
+// w[i] -= sum_t Q[i + t n] c[t]
+__global__ void sub_Qc(const double *Q, int64_t n, int ncol, const double *c, double *w) {
+    extern __shared__ double cs[];
+    for (int t = threadIdx.x; t < ncol; t += blockDim.x) cs[t] = c[t];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int t = 0; t < ncol; ++t) acc += Q[i + (int64_t)t * n] * cs[t];
+        w[i] -= acc;
+    }
+}
+
+// y[i] = sum_t Q[i + t n] S[t]  (a Ritz vector)
+__global__ void gemv_Qs(const double *Q, int64_t n, int ncol, const double *S, double *y) {
+    extern __shared__ double cs[];
+    for (int t = threadIdx.x; t < ncol; t += blockDim.x) cs[t] = S[t];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int t = 0; t < ncol; ++t) acc += Q[i + (int64_t)t * n] * cs[t];
+        y[i] = acc;
+    }
+}
+
+// w = w - alpha q - beta qprev  (qprev may be null)
+__global__ void three_term(double *w, const double *q, const double *qprev, int64_t n, double alpha, double beta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = w[i] - alpha * q[i];
+        if (qprev) v -= beta * qprev[i];
+        w[i] = v;
+    }
+}
+
+__global__ void scale_copy(const double *src, double *dst, int64_t n, double s) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] * s;
+}
+
+// splitmix64 counter hash -> two uniforms -> one standard normal (Box-Muller)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void random_normal(double *x, int64_t n, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t h1 = splitmix64(seed * 0x632be59bd9b4e019ull + 2 * (uint64_t)i);
+        const uint64_t h2 = splitmix64(seed * 0x632be59bd9b4e019ull + 2 * (uint64_t)i + 1);
+        const double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);   // (0, 1]
+        const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);            // [0, 1)
+        x[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    }
+}
+
+// CG helpers
+__global__ void cg_operator(const double *Lp, const double *p, const double *shift, int64_t n, double beta, double *q) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = beta * Lp[i] + (shift ? shift[i] : 1.0) * p[i];
+}
+
+__global__ void sub_into(const double *f, const double *q, int64_t n, double *r) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = f[i] - q[i];
+}
+
+__global__ void cg_update(double *u, double *r, const double *p, const double *q, int64_t n, double alpha) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+    }
+}
+
+__global__ void cg_direction(double *p, const double *r, int64_t n, double gamma) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = r[i] + gamma * p[i];
+}
+
+// --------------------------------------------- tridiagonal eigensolver (QL)
+// Symmetric tridiagonal T (diag d[0..k), off-diagonal e[0..k-1)) -> eigenvalues
+// in d and orthonormal eigenvectors in the columns of Z (row-major k x k).
+// Implicit QL sweeps with a Wilkinson-type shift; each sweep's Givens
+// rotations are computed by one thread and then applied to all rows of Z by
+// the whole block (rows are independent).  info[0] = 0 on success, 1 if an
+// eigenvalue needed more than 64 sweeps.
+__global__ void tridiag_ql(double *d, double *e_in, int k, double *Z, int *info) {
+    extern __shared__ double sh[];
+    double *cs = sh;           // cosines of the current sweep
+    double *sn = sh + k;       // sines
+    __shared__ int sweep_lo, sweep_hi, done_flag, fail;
+    double *e = e_in;          // length k (e[k-1] = 0 used as sentinel)
+    for (int i = threadIdx.x; i < k * k; i += blockDim.x) Z[i] = (i / k == i % k) ? 1.0 : 0.0;
+    if (threadIdx.x == 0) { fail = 0; e[k - 1] = 0.0; }
+    __syncthreads();
+    for (int l = 0; l < k; ++l) {
+        int iter = 0;
+        while (true) {
+            if (threadIdx.x == 0) {
+                int m = l;
+                for (; m < k - 1; ++m) {
+                    const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                    if (fabs(e[m]) <= 2.220446049250313e-16 * dd) break;
+                }
+                done_flag = (m == l);
+                sweep_lo = l;
+                sweep_hi = m;
+                if (!done_flag) {
+                    if (++iter > 64) { fail = 1; done_flag = 1; }
+                }
+                if (!done_flag) {
+                    // shift from the leading 2x2 block
+                    double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+                    double r = hypot(g, 1.0);
+                    g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+                    double s = 1.0, c = 1.0, p = 0.0;
+                    int i = m - 1;
+                    bool underflow = false;
+                    for (; i >= l; --i) {
+                        const double f = s * e[i];
+                        const double b = c * e[i];
+                        r = hypot(f, g);
+                        e[i + 1] = r;
+                        if (r == 0.0) {
+                            d[i + 1] -= p;
+                            e[m] = 0.0;
+                            underflow = true;
+                            break;
+                        }
+                        s = f / r;
+                        c = g / r;
+                        g = d[i + 1] - p;
+                        r = (d[i] - g) * s + 2.0 * c * b;
+                        p = s * r;
+                        d[i + 1] = g + p;
+                        g = c * r - b;
+                        cs[i] = c;
+                        sn[i] = s;
+                    }
+                    sweep_lo = underflow ? i + 1 : l;   // rotations recorded for [sweep_lo, m)
+                    if (!underflow) {
+                        d[l] -= p;
+                        e[l] = g;
+                        e[m] = 0.0;
+                    }
+                }
+            }
+            __syncthreads();
+            if (done_flag) break;
+            // apply the recorded rotations (i = m-1 down to sweep_lo) to every row of Z
+            const int lo = sweep_lo, hi = sweep_hi;
+            for (int row = threadIdx.x; row < k; row += blockDim.x) {
+                double *z = Z + (int64_t)row * k;
+                for (int i = hi - 1; i >= lo; --i) {
+                    const double f = z[i + 1];
+                    z[i + 1] = sn[i] * z[i] + cs[i] * f;
+                    z[i] = cs[i] * z[i] - sn[i] * f;
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) info[0] = fail;
+}
+
+// ----------------------------------------------------------------- helpers
+struct Dev {
+    double *buf = nullptr;
+    ~Dev() { cudaFree(buf); }
+};
+
+static cudaError_t dot(Plan &P, const double *a, const double *b, double *part, double *dres, double *hres) {
+    dot_partials<<<kRedBlocks, 256, 0, P.stream>>>(a, b, P.n, part);
+    sum_partials<<<1, 256, 0, P.stream>>>(part, kRedBlocks, 1, dres);
+    NFL_CUDA_TRY(cudaMemcpyAsync(hres, dres, sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    return cudaStreamSynchronize(P.stream);
+}
+
+static int vec_blocks(const Plan &P) { return std::max(1, P.num_sms * 8); }
+
+}  // namespace nfl
+
+using nfl::Plan;
+
+extern "C" {
+
+nfl_status nfl_lanczos_k_smallest(nfl_plan *plan, int k, double tol, int maxit, uint64_t seed,
+                                  double *evals, double *evecs, int *iters) {
+    using namespace nfl;
+    if (!plan || !evals || k < 1 || !(tol > 0.0)) return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (k >= P.n || maxit <= k || maxit > P.n || maxit > 4096) return NFL_ERR_INVALID_ARG;
+    if (!P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
+    const int64_t n = P.n;
+    const int kmax = maxit;
+    const cudaStream_t s = P.stream;
+    Dev Qm, W, part, sc, Tm;
+    // Q: n x (kmax + 1); part: kRedBlocks x (kmax + 1); sc: (kmax+1) scalars + 2; Tm: d, e, Z, S
+    if (cudaMalloc(&Qm.buf, (size_t)n * (kmax + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&W.buf, (size_t)n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&part.buf, (size_t)kRedBlocks * (kmax + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&sc.buf, (size_t)(kmax + 4) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&Tm.buf, (size_t)(2 * (kmax + 1) + (size_t)kmax * kmax + 2) * sizeof(double)) != cudaSuccess)
+        return NFL_ERR_OUT_OF_MEMORY;
+    double *Q = Qm.buf, *w = W.buf;
+    double *td = Tm.buf, *te = td + (kmax + 1), *Z = te + (kmax + 1);
+    int *info = reinterpret_cast<int *>(Z + (size_t)kmax * kmax);
+    const int vb = vec_blocks(P);
+    std::vector<double> alpha, beta;   // beta[j] couples q_j and q_{j+1}
+    double h = 0.0;
+
+    random_normal<<<vb, 256, 0, s>>>(Q, n, seed);
+    if (dot(P, Q, Q, part.buf, sc.buf, &h) != cudaSuccess) return NFL_ERR_CUDA;
+    if (!(h > 0.0)) return NFL_ERR_NAN;
+    scale_copy<<<vb, 256, 0, s>>>(Q, Q, n, 1.0 / std::sqrt(h));
+
+    std::vector<double> hd, he, hZ, theta;
+    std::vector<int> order;
+    int steps = 0;
+    nfl_status result = NFL_ERR_NOT_CONVERGED;
+    auto ritz = [&](int j) -> nfl_status {
+        // eigen-decompose T_j on the device
+        if (cudaMemcpyAsync(td, alpha.data(), j * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) return NFL_ERR_CUDA;
+        std::vector<double> eh(j, 0.0);
+        for (int i = 0; i + 1 < j; ++i) eh[i] = beta[i];
+        if (cudaMemcpyAsync(te, eh.data(), j * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) return NFL_ERR_CUDA;
+        tridiag_ql<<<1, 256, 2 * j * sizeof(double), s>>>(td, te, j, Z, info);
+        hd.resize(j);
+        hZ.resize((size_t)j * j);
+        int hinfo = 0;
+        if (cudaMemcpyAsync(hd.data(), td, j * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(hZ.data(), Z, (size_t)j * j * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return NFL_ERR_CUDA;
+        if (hinfo) return NFL_ERR_NOT_CONVERGED;
+        order.resize(j);
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return hd[a] > hd[b]; });
+        return NFL_OK;
+    };
+
+    for (int j = 0; j < kmax; ++j) {
+        double *qj = Q + (int64_t)j * n;
+        nfl_status st = run_column(P, OP_A, qj, w);                     // w = A q_j
+        if (st != NFL_OK) return st;
+        double a = 0.0;
+        if (dot(P, qj, w, part.buf, sc.buf, &a) != cudaSuccess) return NFL_ERR_CUDA;
+        if (!std::isfinite(a)) return NFL_ERR_NAN;
+        three_term<<<vb, 256, 0, s>>>(w, qj, j > 0 ? qj - n : nullptr, n, a, j > 0 ? beta[j - 1] : 0.0);
+        for (int pass = 0; pass < 2; ++pass) {                           // DGKS
+            dim3 g(kRedBlocks, j + 1);
+            multidot_partials<<<g, 256, 0, s>>>(Q, n, w, part.buf);
+            sum_partials<<<std::min(j + 1, 1024), 256, 0, s>>>(part.buf, kRedBlocks, j + 1, sc.buf);
+            sub_Qc<<<vb, 256, (j + 1) * sizeof(double), s>>>(Q, n, j + 1, sc.buf, w);
+        }
+        double bb = 0.0;
+        if (dot(P, w, w, part.buf, sc.buf, &bb) != cudaSuccess) return NFL_ERR_CUDA;
+        if (!std::isfinite(bb)) return NFL_ERR_NAN;
+        const double b = std::sqrt(bb);
+        alpha.push_back(a);
+        beta.push_back(b);
+        steps = j + 1;
+        const bool breakdown = b <= 1e-14 * std::max(1.0, std::fabs(a));
+        if (steps >= k && (steps % 5 == 0 || breakdown || steps == kmax)) {
+            st = ritz(steps);
+            if (st == NFL_ERR_CUDA) return st;
+            if (st == NFL_OK) {
+                bool conv = true;
+                for (int t = 0; t < k; ++t) {
+                    const int c = order[t];
+                    const double resid = std::fabs(b * hZ[(size_t)(steps - 1) * steps + c]);
+                    if (resid > tol) conv = false;
+                }
+                if (conv || breakdown) {
+                    result = NFL_OK;
+                    break;
+                }
+            }
+        }
+        if (breakdown) {
+            result = steps >= k ? NFL_OK : NFL_ERR_BREAKDOWN;
+            break;
+        }
+        scale_copy<<<vb, 256, 0, s>>>(w, Q + (int64_t)(j + 1) * n, n, 1.0 / b);
+    }
+    if (steps < k) return result == NFL_OK ? NFL_ERR_BREAKDOWN : result;
+    if (order.size() != (size_t)steps) {
+        nfl_status st = ritz(steps);
+        if (st != NFL_OK) return st;
+    }
+    // eigenvalues of L_s ascending = 1 - theta for theta descending
+    for (int t = 0; t < k; ++t) evals[t] = 1.0 - hd[order[t]];
+    if (evecs) {
+        std::vector<double> col(steps);
+        double *dcol = sc.buf;
+        for (int t = 0; t < k; ++t) {
+            for (int i = 0; i < steps; ++i) col[i] = hZ[(size_t)i * steps + order[t]];
+            if (cudaMemcpyAsync(dcol, col.data(), steps * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return NFL_ERR_CUDA;
+            gemv_Qs<<<vb, 256, steps * sizeof(double), s>>>(Q, n, steps, dcol, evecs + (int64_t)t * n);
+            if (cudaStreamSynchronize(s) != cudaSuccess) return NFL_ERR_CUDA;
+        }
+    }
+    if (iters) *iters = steps;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NFL_ERR_CUDA;
+    return result;
+}
+
+nfl_status nfl_cg_solve(nfl_plan *plan, double beta, const double *shift, const double *f, double *u, double tol,
+                        int maxit, int *iters, double *relres) {
+    using namespace nfl;
+    if (!plan || !f || !u || !(beta > 0.0) || !(tol > 0.0) || maxit < 1) return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (!P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    Dev R, Pv, Qv, Lp, part, sc;
+    if (cudaMalloc(&R.buf, n * 8) != cudaSuccess || cudaMalloc(&Pv.buf, n * 8) != cudaSuccess ||
+        cudaMalloc(&Qv.buf, n * 8) != cudaSuccess || cudaMalloc(&Lp.buf, n * 8) != cudaSuccess ||
+        cudaMalloc(&part.buf, kRedBlocks * 8) != cudaSuccess || cudaMalloc(&sc.buf, 8 * 8) != cudaSuccess)
+        return NFL_ERR_OUT_OF_MEMORY;
+    const int vb = vec_blocks(P);
+    double *r = R.buf, *p = Pv.buf, *q = Qv.buf, *lp = Lp.buf;
+    double fn2 = 0.0;
+    if (dot(P, f, f, part.buf, sc.buf, &fn2) != cudaSuccess) return NFL_ERR_CUDA;
+    const double fn = std::sqrt(fn2);
+    // r = f - op(u)
+    nfl_status st = run_column(P, OP_LS, u, lp);
+    if (st != NFL_OK) return st;
+    cg_operator<<<vb, 256, 0, s>>>(lp, u, shift, n, beta, q);
+    sub_into<<<vb, 256, 0, s>>>(f, q, n, r);
+    if (cudaMemcpyAsync(p, r, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return NFL_ERR_CUDA;
+    double rr = 0.0;
+    if (dot(P, r, r, part.buf, sc.buf, &rr) != cudaSuccess) return NFL_ERR_CUDA;
+    int it = 0;
+    nfl_status result = NFL_ERR_NOT_CONVERGED;
+    const double target = tol * fn;
+    for (; it <= maxit; ++it) {
+        if (!std::isfinite(rr)) return NFL_ERR_NAN;
+        if (std::sqrt(rr) <= target) { result = NFL_OK; break; }
+        if (it == maxit) break;
+        st = run_column(P, OP_LS, p, lp);
+        if (st != NFL_OK) return st;
+        cg_operator<<<vb, 256, 0, s>>>(lp, p, shift, n, beta, q);
+        double pq = 0.0;
+        if (dot(P, p, q, part.buf, sc.buf, &pq) != cudaSuccess) return NFL_ERR_CUDA;
+        if (!(pq > 0.0)) return std::isfinite(pq) ? NFL_ERR_BREAKDOWN : NFL_ERR_NAN;
+        const double alpha = rr / pq;
+        cg_update<<<vb, 256, 0, s>>>(u, r, p, q, n, alpha);
+        double rr_new = 0.0;
+        if (dot(P, r, r, part.buf, sc.buf, &rr_new) != cudaSuccess) return NFL_ERR_CUDA;
+        cg_direction<<<vb, 256, 0, s>>>(p, r, n, rr_new / rr);
+        rr = rr_new;
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = fn > 0.0 ? std::sqrt(rr) / fn : std::sqrt(rr);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NFL_ERR_CUDA;
+    return result;
+}
+
+}  // extern "C"

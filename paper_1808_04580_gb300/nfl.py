@@ -1,0 +1,230 @@
+"""ctypes binding over the C ABI of include/nfl.h (libnfl.so).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors are torch CUDA float64 tensors (torch provides device memory and the
+current stream); blocks of right-hand sides are passed column-major.  There is
+no CPU fallback: if the library is missing or a tensor is not on the GPU, the
+call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libnfl.so")
+
+NFL_OK = 0
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32c": 2}
+
+_STATUS = {
+    0: "NFL_OK", 1: "NFL_ERR_INVALID_ARG", 2: "NFL_ERR_NONPOSITIVE_DEGREE", 3: "NFL_ERR_BREAKDOWN",
+    4: "NFL_ERR_NOT_CONVERGED", 5: "NFL_ERR_NAN", 6: "NFL_ERR_TIMEOUT", 7: "NFL_ERR_CUDA",
+    8: "NFL_ERR_OUT_OF_MEMORY",
+}
+
+
+class NflError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = int(status)
+        self.name = _STATUS.get(self.status, str(status))
+        msg = _lib().nfl_status_string(self.status).decode() if _LIB is not None else self.name
+        super().__init__("%s: %s (%s)" % (where, self.name, msg))
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("d", ctypes.c_int), ("N", ctypes.c_int), ("m", ctypes.c_int),
+        ("p", ctypes.c_int), ("precision", ctypes.c_int), ("sigma", ctypes.c_double),
+        ("eps_B", ctypes.c_double), ("rho", ctypes.c_double), ("sigma_tilde", ctypes.c_double),
+        ("center", ctypes.c_double * 3), ("box", ctypes.c_int * 3), ("tiles", ctypes.c_int64),
+        ("work_items", ctypes.c_int64), ("min_degree", ctypes.c_double), ("max_degree", ctypes.c_double),
+        ("degree_ok", ctypes.c_int),
+    ]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_L = ctypes.c_int64
+
+SIGNATURES = {
+    "nfl_plan_create": (_I, [_P, _L, _I, _I, _D, _I, _I, _I, _D, _I, _P, ctypes.POINTER(_P)]),
+    "nfl_plan_destroy": (None, [_P]),
+    "nfl_plan_info": (_I, [_P, ctypes.POINTER(Info)]),
+    "nfl_set_stream": (_I, [_P, _P]),
+    "nfl_degree": (_I, [_P, _P]),
+    "nfl_apply_W": (_I, [_P, _P, _L, _P, _L, _I]),
+    "nfl_apply_A": (_I, [_P, _P, _L, _P, _L, _I]),
+    "nfl_apply_Ls": (_I, [_P, _P, _L, _P, _L, _I]),
+    "nfl_lanczos_k_smallest": (_I, [_P, _I, _D, _I, ctypes.c_uint64, _P, _P, ctypes.POINTER(_I)]),
+    "nfl_cg_solve": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nfl_plan_set_profiling": (_I, [_P, _I]),
+    "nfl_plan_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
+    "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
+    "nfl_status_string": (ctypes.c_char_p, [_I]),
+}
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnfl.so is not built (%s); run paper_1808_04580_gb300.build.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def library():
+    """The loaded ctypes library (raises if it is not built)."""
+    return _lib()
+
+
+def _check(status, where):
+    if status != NFL_OK:
+        raise NflError(status, where)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _cuda_f64(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64:
+        raise TypeError("%s must be float64" % name)
+    return t
+
+
+def _as_columns(x, n):
+    """(n,) or (n, r) -> column-major (r, n) contiguous storage, r."""
+    _cuda_f64(x, "x")
+    if x.dim() == 1:
+        if x.shape[0] != n:
+            raise ValueError("x has %d rows, plan has %d" % (x.shape[0], n))
+        return x.contiguous(), 1, True
+    if x.dim() != 2 or x.shape[0] != n:
+        raise ValueError("x must be (n,) or (n, r)")
+    return x.t().contiguous(), x.shape[1], False
+
+
+class Plan:
+    """Alg. 2 setup for one point cloud; products with W, A and L_s."""
+
+    def __init__(self, v, sigma, N, m, p=0, eps_B=-1.0, precision="fp64"):
+        _cuda_f64(v, "v")
+        if v.dim() != 2:
+            raise ValueError("v must be (n, d)")
+        v = v.contiguous()
+        self.n, self.d = int(v.shape[0]), int(v.shape[1])
+        self.device = v.device
+        self._h = None
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = _lib().nfl_plan_create(v.data_ptr(), self.n, self.d, 0, float(sigma), int(N), int(m), int(p),
+                                        float(eps_B), PRECISIONS[precision], _stream(), ctypes.byref(h))
+        _check(st, "nfl_plan_create")
+        self._h = h
+
+    def close(self):
+        if self._h is not None and _LIB is not None:
+            _LIB.nfl_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = Info()
+        _check(_lib().nfl_plan_info(self._h, ctypes.byref(inf)), "nfl_plan_info")
+        out = {f: getattr(inf, f) for f, _ in Info._fields_}
+        out["center"] = list(inf.center)
+        out["box"] = list(inf.box)
+        return out
+
+    def set_profiling(self, enable=True):
+        _check(_lib().nfl_plan_set_profiling(self._h, 1 if enable else 0), "nfl_plan_set_profiling")
+
+    def stage_times(self):
+        """Accumulated ms per stage since the last call: dict(prep, spread, fft, gather, columns)."""
+        ms = (ctypes.c_double * 4)()
+        cols = ctypes.c_int64(0)
+        _check(_lib().nfl_plan_stage_times(self._h, ms, ctypes.byref(cols)), "nfl_plan_stage_times")
+        return dict(prep=ms[0], spread=ms[1], fft=ms[2], gather=ms[3], columns=cols.value)
+
+    def kernels_per_column(self):
+        k = ctypes.c_int(0)
+        _check(_lib().nfl_plan_kernels_per_column(self._h, ctypes.byref(k)), "nfl_plan_kernels_per_column")
+        return k.value
+
+    def _sync_stream(self):
+        _check(_lib().nfl_set_stream(self._h, _stream()), "nfl_set_stream")
+
+    def degree(self):
+        self._sync_stream()
+        d = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        _check(_lib().nfl_degree(self._h, d.data_ptr()), "nfl_degree")
+        return d
+
+    def _apply(self, fn, name, x, out=None):
+        self._sync_stream()
+        xc, r, vec = _as_columns(x, self.n)
+        y = torch.empty_like(xc) if out is None else out
+        _check(fn(self._h, xc.data_ptr(), self.n, y.data_ptr(), self.n, r), name)
+        return y if vec else y.t()
+
+    def apply_W(self, x, out=None):
+        """W_E x (Alg. 1 with W = W~ - K(0) I)."""
+        return self._apply(_lib().nfl_apply_W, "nfl_apply_W", x, out)
+
+    def apply_A(self, x, out=None):
+        """A_E x (Alg. 2 step 5)."""
+        return self._apply(_lib().nfl_apply_A, "nfl_apply_A", x, out)
+
+    def apply_Ls(self, x, out=None):
+        """L_s x = x - A_E x."""
+        return self._apply(_lib().nfl_apply_Ls, "nfl_apply_Ls", x, out)
+
+    def lanczos_k_smallest(self, k, tol=1e-10, maxit=None, seed=0, vectors=True, check=True):
+        """k smallest eigenpairs of L_s: (evals ndarray ascending, evecs (n, k) tensor or None, iters, status)."""
+        self._sync_stream()
+        if maxit is None:
+            maxit = min(self.n, max(2 * k + 40, 60))
+        evals = np.zeros(k, dtype=np.float64)
+        evecs = torch.empty((k, self.n), dtype=torch.float64, device=self.device) if vectors else None
+        iters = ctypes.c_int(0)
+        st = _lib().nfl_lanczos_k_smallest(self._h, int(k), float(tol), int(maxit), int(seed),
+                                           evals.ctypes.data, evecs.data_ptr() if vectors else None,
+                                           ctypes.byref(iters))
+        if check:
+            _check(st, "nfl_lanczos_k_smallest")
+        return evals, (evecs.t() if vectors else None), iters.value, st
+
+    def cg_solve(self, f, beta=1.0, shift=None, u0=None, tol=1e-10, maxit=1000, check=True):
+        """Solve (beta L_s + diag(shift)) u = f: (u, iters, relres, status)."""
+        self._sync_stream()
+        _cuda_f64(f, "f")
+        f = f.contiguous()
+        u = torch.zeros_like(f) if u0 is None else _cuda_f64(u0, "u0").clone()
+        sp = None
+        if shift is not None:
+            shift = _cuda_f64(shift, "shift").contiguous()
+            sp = shift.data_ptr()
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = _lib().nfl_cg_solve(self._h, float(beta), sp, f.data_ptr(), u.data_ptr(), float(tol), int(maxit),
+                                 ctypes.byref(it), ctypes.byref(rel))
+        if check:
+            _check(st, "nfl_cg_solve")
+        return u, it.value, rel.value, st

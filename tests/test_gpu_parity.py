@@ -1,0 +1,210 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+FP64 plans must match the oracle's plain Alg. 1/2 (O3, same N, m, p, eps_B,
+Kaiser-Bessel window, oversampling 2) to 1e-10 relative; the mixed forms are
+held to their own tolerances against the same O3 output.  Sizes span several
+tiles and ragged tails; edge cases: n = 1, 2, 3, coincident nodes, supports
+that wrap around the periodic grid, d = 1, 2, 3.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import direct, fastsum, spectral
+from paper_1808_04580_gb300 import NflError, Plan, workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _cloud(kind, n, d, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "spiral":
+        return workloads.two_arm_spiral(n, seed=seed)[:, :d]
+    if kind == "normal":
+        return rng.standard_normal((n, d))
+    if kind == "clusters":
+        c = rng.uniform(-1, 1, (4, d))
+        return c[rng.integers(0, 4, n)] + 0.05 * rng.standard_normal((n, d))
+    raise ValueError(kind)
+
+
+# (kind, n, d, sigma, N, m, p, eps_B)
+FP64_CASES = [
+    ("spiral", 1000, 3, 0.5, 16, 4, 4, -1.0),
+    ("normal", 17, 3, 1.0, 8, 2, 2, -1.0),
+    ("normal", 3, 3, 1.0, 16, 3, 3, -1.0),
+    ("clusters", 2500, 3, 0.3, 32, 3, 3, -1.0),
+    ("normal", 700, 2, 0.5, 32, 3, 3, -1.0),
+    ("clusters", 900, 2, 0.2, 64, 6, 6, -1.0),
+    ("normal", 500, 1, 0.3, 64, 5, 5, -1.0),
+    ("normal", 200, 3, 1.0, 8, 4, 4, 0.125),     # taps wrap around the periodic grid
+    ("normal", 300, 2, 1.0, 8, 6, 2, 0.125),     # wrap, d = 2
+    ("spiral", 800, 3, 3.5, 16, 2, 2, 0.0),      # eps_B = 0 (paper's setup #1 form)
+]
+
+
+@pytest.mark.parametrize("case", FP64_CASES, ids=lambda c: "%s-n%d-d%d-N%d-m%d" % (c[0], c[1], c[2], c[4], c[5]))
+def test_fp64_matches_alg2_oracle(case):
+    kind, n, d, sigma, N, m, p, eps_B = case
+    v = _cloud(kind, n, d, seed=n + d)
+    x = workloads.rhs(n, seed=n)
+    ref = fastsum.NormalizedFastsum(v, sigma, N, m, p, None if eps_B < 0 else eps_B)
+    plan = Plan(gpu(v), sigma, N, m, p, eps_B, "fp64")
+    info = plan.info()
+    assert info["rho"] == pytest.approx(ref.rho, rel=1e-14)
+    xt = gpu(x)
+    assert rel(plan.apply_W(xt).cpu().numpy(), ref.apply_W(x)) < 1e-10
+    deg = plan.degree().cpu().numpy()
+    np.testing.assert_allclose(deg, ref.degree, rtol=1e-10, atol=1e-12 * np.abs(ref.degree).max())
+    # Lemma 3.1: a coarse plan can push a small degree below zero (eps >= eta);
+    # the oracle sees the same degrees, and the GPU must then refuse A and L_s.
+    assert info["degree_ok"] == int(ref.degree.min() > 0)
+    if not info["degree_ok"]:
+        with pytest.raises(NflError):
+            plan.apply_A(xt)
+        return
+    assert rel(plan.apply_A(xt).cpu().numpy(), ref.apply_A(x)) < 1e-10
+    assert rel(plan.apply_Ls(xt).cpu().numpy(), ref.apply_Ls(x)) < 1e-10
+
+
+def test_spiral5k_fp64_against_alg2_and_direct():
+    """Small FP64 workload: n = 5000 two-arm spiral, sigma 0.5, N 32, m 4, p 4."""
+    v = workloads.two_arm_spiral(5000, seed=0)
+    x = workloads.rhs(5000, seed=1)
+    plan = Plan(gpu(v), 0.5, 32, 4, 4, -1.0, "fp64")
+    y = plan.apply_W(gpu(x)).cpu().numpy()
+    ref = fastsum.NormalizedFastsum(v, 0.5, 32, 4, 4)
+    assert rel(y, ref.apply_W(x)) < 1e-10
+    # against the exact sum: within the method's own error (window m = 4 ~ 1e-7)
+    assert rel(y, direct.apply_W(v, 0.5, x)) < 5e-7
+    yl = plan.apply_Ls(gpu(x)).cpu().numpy()
+    assert rel(yl, ref.apply_Ls(x)) < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("fp32c", 1e-6)])
+def test_mixed_precision_forms(prec, tol):
+    v = _cloud("clusters", 3000, 3, seed=11)
+    x = workloads.rhs(3000, seed=12)
+    ref = fastsum.NormalizedFastsum(v, 0.3, 32, 4, 4)
+    plan = Plan(gpu(v), 0.3, 32, 4, 4, -1.0, prec)
+    assert rel(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x)) < tol
+    assert rel(plan.apply_A(gpu(x)).cpu().numpy(), ref.apply_A(x)) < tol
+
+
+def test_block_of_right_hand_sides_equals_columns():
+    v = workloads.two_arm_spiral(1200, seed=3)
+    X = workloads.rhs(1200, nrhs=3, seed=4)
+    plan = Plan(gpu(v), 0.5, 32, 4, 4, -1.0, "fp64")
+    Y = plan.apply_Ls(gpu(X)).cpu().numpy()
+    for c in range(3):
+        yc = plan.apply_Ls(gpu(X[:, c])).cpu().numpy()
+        np.testing.assert_allclose(Y[:, c], yc, rtol=1e-12, atol=1e-14)
+
+
+def test_single_node():
+    v = np.array([[0.2, -0.3, 1.0]])
+    plan = Plan(gpu(v), 0.7, 16, 3, 3, -1.0, "fp64")
+    y = plan.apply_W(gpu(np.array([3.0]))).cpu().numpy()
+    # W = [0]; the fast sum returns its own error, K_RF(0) - K(0), times x
+    ref = fastsum.NormalizedFastsum(v, 0.7, 16, 3, 3).apply_W(np.array([3.0]))
+    assert abs(y[0] - ref[0]) < 1e-12
+    assert abs(y[0]) < 1e-3
+    assert plan.info()["degree_ok"] == int(ref[0] / 3.0 > 0)
+    plan = Plan(gpu(v), 0.7, 16, 3, 3, -1.0, "fp64")
+    if not plan.info()["degree_ok"]:
+        with pytest.raises(NflError) as e:
+            plan.apply_A(gpu(np.array([1.0])))
+        assert e.value.name == "NFL_ERR_NONPOSITIVE_DEGREE"
+
+
+def test_two_nodes_closed_form():
+    v = np.array([[0.0, 0.0, 0.0], [0.3, 0.4, 0.0]])
+    w = math.exp(-0.25 / 0.64)
+    x = np.array([2.0, -3.0])
+    plan = Plan(gpu(v), 0.8, 64, 8, 4, -1.0, "fp64")
+    y = plan.apply_W(gpu(x)).cpu().numpy()
+    ref = fastsum.NormalizedFastsum(v, 0.8, 64, 8, 4)
+    assert rel(y, ref.apply_W(x)) < 1e-10
+    # sigma~ = 0.7 after scaling: a wide kernel on the torus, method error ~3e-4
+    np.testing.assert_allclose(y, [-3.0 * w, 2.0 * w], rtol=2e-3)
+    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=1e-10)
+
+
+def test_coincident_nodes():
+    v = np.tile([[1.0, 2.0, 3.0]], (5, 1))
+    x = np.arange(1.0, 6.0)
+    plan = Plan(gpu(v), 0.5, 16, 4, 4, -1.0, "fp64")
+    y = plan.apply_W(gpu(x)).cpu().numpy()
+    ref = fastsum.NormalizedFastsum(v, 0.5, 16, 4, 4)
+    assert rel(y, ref.apply_W(x)) < 1e-10
+    np.testing.assert_allclose(y, x.sum() - x, rtol=1e-4)          # W = 1 1^T - I exactly
+
+
+def test_invalid_arguments_raise():
+    v = gpu(np.random.default_rng(0).standard_normal((10, 3)))
+    for kw in [dict(N=30), dict(m=0), dict(eps_B=0.6), dict(sigma=0.0)]:
+        args = dict(sigma=1.0, N=16, m=3)
+        args.update(kw)
+        with pytest.raises(NflError) as e:
+            Plan(v, args["sigma"], args["N"], args["m"], 0, kw.get("eps_B", -1.0), "fp64")
+        assert e.value.name == "NFL_ERR_INVALID_ARG"
+    bad = np.random.default_rng(0).standard_normal((10, 3))
+    bad[4, 1] = np.nan
+    with pytest.raises(NflError):
+        Plan(gpu(bad), 1.0, 16, 3)
+
+
+def test_operator_symmetry_and_degree_identity():
+    v = _cloud("clusters", 4000, 3, seed=21)
+    for prec, tol in (("fp64", 1e-13), ("fp32c", 1e-6)):
+        plan = Plan(gpu(v), 0.3, 32, 4, 4, -1.0, prec)
+        rng = np.random.default_rng(5)
+        u, w = rng.standard_normal(4000), rng.standard_normal(4000)
+        Wu = plan.apply_W(gpu(u)).cpu().numpy()
+        Ww = plan.apply_W(gpu(w)).cpu().numpy()
+        scale = np.abs(u) @ plan.apply_W(gpu(np.abs(w))).cpu().numpy()
+        assert abs(u @ Ww - Wu @ w) < tol * scale
+        d = plan.degree().cpu().numpy()
+        Ls_sqrtd = plan.apply_Ls(gpu(np.sqrt(d))).cpu().numpy()
+        assert np.abs(Ls_sqrtd).max() < 10 * tol * np.sqrt(d).max()
+
+
+def test_lanczos_smallest_eigenpairs():
+    """10 smallest of L_s to 1e-8 against the dense eigendecomposition (Sec. 6.1 setup)."""
+    n = 2000
+    v = workloads.two_arm_spiral(n, seed=2)
+    lam_ref, V_ref = spectral.smallest_Ls(v, 0.5, 10)
+    plan = Plan(gpu(v), 0.5, 64, 8, 8, -1.0, "fp64")    # kernel error ~1e-14 (high-accuracy plan)
+    evals, evecs, iters, st = plan.lanczos_k_smallest(10, tol=1e-10, maxit=200, seed=1)
+    assert np.abs(evals - lam_ref).max() < 1e-8
+    E = evecs.cpu().numpy()
+    # residual of each pair against the exact operator (eq. (max_res_norm))
+    A = direct.normalized_adjacency(v, 0.5)
+    res = np.linalg.norm(A @ E - E * (1.0 - evals)[None, :], axis=0)
+    assert res.max() < 1e-6
+    assert np.abs(E.T @ E - np.eye(10)).max() < 1e-8
+
+
+def test_cg_solve_matches_dense_solve():
+    n = 1500
+    v = workloads.two_arm_spiral(n, seed=4)
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal(n)
+    shift = np.where(rng.uniform(size=n) < 0.1, 10.0, 0.0) + 0.5
+    beta = 2.0
+    u_ref = spectral.solve_shifted(v, 0.5, beta, shift, f)
+    plan = Plan(gpu(v), 0.5, 64, 8, 8, -1.0, "fp64")
+    u, iters, relres, st = plan.cg_solve(gpu(f), beta=beta, shift=gpu(shift), tol=1e-12, maxit=2000)
+    assert relres <= 1e-12
+    assert rel(u.cpu().numpy(), u_ref) < 1e-9

@@ -169,6 +169,28 @@ nfl_status nfl_cg_solve(nfl_plan *plan, double beta, const double *shift,
                         int *iters, double *relres);
 
 /*
+ * nfl_cg_solve without device allocation.  The paper has no counterpart:
+ * this is a deployment variant of nfl_cg_solve for callers that cannot
+ * call cudaMalloc / cudaFree while they solve (work captured into a CUDA
+ * graph, a process whose device footprint is fixed at start-up, an
+ * allocator that must not see foreign allocations).  Arguments, results and
+ * status codes are those of nfl_cg_solve.
+ *
+ * The four work vectors and the reduction partials live in one static
+ * device array of this library, sized for n <= NFL_NOALLOC_MAX_N nodes
+ * (4 x 262144 + 520 doubles, about 8 MiB, held by every GPU that loads the
+ * library until the process exits).  A plan with more nodes returns
+ * NFL_ERR_INVALID_ARG.  The plan's device must be current; the first call
+ * on a device looks up the array's device address, so make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (other streams, plans or threads) race on it.
+ */
+#define NFL_NOALLOC_MAX_N 262144
+nfl_status nfl_cg_solve_noalloc(nfl_plan *plan, double beta, const double *shift,
+                                const double *f, double *u, double tol, int maxit,
+                                int *iters, double *relres);
+
+/*
  * Stage timing (tracing).  When enabled, CUDA events on the plan's stream
  * bracket the four stages of every product column: prep (grid clear and, for
  * FP32C, the fixed-point scale), spread, FFT (all passes, multiply fused) and

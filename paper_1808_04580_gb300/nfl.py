@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libnfl.so")
 
 NFL_OK = 0
+NOALLOC_MAX_N = 262144   # NFL_NOALLOC_MAX_N in include/nfl.h
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32c": 2}
 
 _STATUS = {
@@ -61,6 +62,7 @@ SIGNATURES = {
     "nfl_apply_Ls": (_I, [_P, _P, _L, _P, _L, _I]),
     "nfl_lanczos_k_smallest": (_I, [_P, _I, _D, _I, ctypes.c_uint64, _P, _P, ctypes.POINTER(_I)]),
     "nfl_cg_solve": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nfl_cg_solve_noalloc": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_plan_set_profiling": (_I, [_P, _I]),
     "nfl_plan_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
     "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
@@ -211,8 +213,12 @@ class Plan:
             _check(st, "nfl_lanczos_k_smallest")
         return evals, (evecs.t() if vectors else None), iters.value, st
 
-    def cg_solve(self, f, beta=1.0, shift=None, u0=None, tol=1e-10, maxit=1000, check=True):
-        """Solve (beta L_s + diag(shift)) u = f: (u, iters, relres, status)."""
+    def cg_solve(self, f, beta=1.0, shift=None, u0=None, tol=1e-10, maxit=1000, check=True, noalloc=False):
+        """Solve (beta L_s + diag(shift)) u = f: (u, iters, relres, status).
+
+        noalloc=True calls nfl_cg_solve_noalloc, whose scratch is a static
+        device array (n <= NOALLOC_MAX_N) instead of per-call allocations.
+        """
         self._sync_stream()
         _cuda_f64(f, "f")
         f = f.contiguous()
@@ -223,8 +229,9 @@ class Plan:
             sp = shift.data_ptr()
         it = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
-        st = _lib().nfl_cg_solve(self._h, float(beta), sp, f.data_ptr(), u.data_ptr(), float(tol), int(maxit),
-                                 ctypes.byref(it), ctypes.byref(rel))
+        fn = _lib().nfl_cg_solve_noalloc if noalloc else _lib().nfl_cg_solve
+        st = fn(self._h, float(beta), sp, f.data_ptr(), u.data_ptr(), float(tol), int(maxit),
+                ctypes.byref(it), ctypes.byref(rel))
         if check:
-            _check(st, "nfl_cg_solve")
+            _check(st, "nfl_cg_solve_noalloc" if noalloc else "nfl_cg_solve")
         return u, it.value, rel.value, st

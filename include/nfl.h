@@ -57,8 +57,9 @@ enum { NFL_KERNEL_GAUSSIAN = 0 };
  * D^{-1/2} scaling, x - A x) and all solver scalars are FP64 in every mode.
  *   FP64  : everything in FP64.
  *   FP32  : window weights, spreading grid, FFT and interpolation in FP32.
- *   FP32C : FP32 window weights; the spreading grid is accumulated exactly
- *           in 64-bit fixed point; FFT in FP64; interpolation in FP32.      */
+ *   FP32C : FP32 window weights and products; spreading sums are carried
+ *           into 64-bit fixed point every 32 nodes and accumulated exactly;
+ *           FFT and interpolation in FP32.                                  */
 enum { NFL_PREC_FP64 = 0, NFL_PREC_FP32 = 1, NFL_PREC_FP32C = 2 };
 
 typedef struct {

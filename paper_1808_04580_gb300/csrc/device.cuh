@@ -17,12 +17,29 @@ namespace nfl {
 // s = 0 is 2 b m e^{-b m} / (1 - e^{-2 b m}).  phi(0) is put back into the
 // Fourier multiplier.  inv_den = 1 / (1 - e^{-2 b m}).
 template <typename T>
-__device__ __forceinline__ T kb_weight(T delta, T m, T b, T inv_den) {
-    T s2 = m * m - delta * delta;
-    s2 = s2 > T(0) ? s2 : T(0);
-    const T s = sqrt(s2);
-    const T head = exp(-b * delta * delta / (s + m));
-    const T tail = s > T(0) ? -expm1(T(-2) * b * s) / s : T(2) * b;
+__device__ __forceinline__ T kb_weight(T delta, T m, T b, T inv_den);
+
+template <>
+__device__ __forceinline__ double kb_weight<double>(double delta, double m, double b, double inv_den) {
+    double s2 = m * m - delta * delta;
+    s2 = s2 > 0.0 ? s2 : 0.0;
+    const double s = sqrt(s2);
+    const double head = exp(-b * delta * delta / (s + m));
+    const double tail = s > 0.0 ? -expm1(-2.0 * b * s) / s : 2.0 * b;
+    return head * m * tail * inv_den;
+}
+
+// FP32: single-precision functions only (the FP64 pipe of this GPU is narrow).
+// The head factor carries the weight's magnitude and uses the accurate expf;
+// the tail (1 - e^{-2bs})/s differs from 1/s only where s is small, i.e. where
+// the weight is ~e^{-bm} relative to its peak, so fast intrinsics suffice there.
+template <>
+__device__ __forceinline__ float kb_weight<float>(float delta, float m, float b, float inv_den) {
+    float s2 = fmaf(-delta, delta, m * m);
+    s2 = s2 > 0.f ? s2 : 0.f;
+    const float s = s2 > 0.f ? s2 * rsqrtf(s2) : 0.f;
+    const float head = expf(-__fdividef(b * delta * delta, s + m));
+    const float tail = s > 1e-4f ? __fdividef(1.f - __expf(-2.f * b * s), s) : 2.f * b;
     return head * m * tail * inv_den;
 }
 

@@ -258,7 +258,7 @@ static cudaError_t launch_fft_t(Plan &P) {
 
 cudaError_t launch_fft(Plan &P) {
     if (P.prec == NFL_PREC_FP32) return launch_fft_t<float, float>(P);
-    if (P.prec == NFL_PREC_FP32C) return launch_fft_t<double, long long>(P);
+    if (P.prec == NFL_PREC_FP32C) return launch_fft_t<float, long long>(P);
     return launch_fft_t<double, double>(P);
 }
 

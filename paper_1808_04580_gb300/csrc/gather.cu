@@ -196,9 +196,9 @@ cudaError_t launch_gather(Plan &P, int op, const double *x, double *y) {
         case NFL_PREC_FP32 * 4 + 1: return launch_gather_t<float, float, 1>(P, a);
         case NFL_PREC_FP32 * 4 + 2: return launch_gather_t<float, float, 2>(P, a);
         case NFL_PREC_FP32 * 4 + 3: return launch_gather_t<float, float, 3>(P, a);
-        case NFL_PREC_FP32C * 4 + 1: return launch_gather_t<float, double, 1>(P, a);
-        case NFL_PREC_FP32C * 4 + 2: return launch_gather_t<float, double, 2>(P, a);
-        case NFL_PREC_FP32C * 4 + 3: return launch_gather_t<float, double, 3>(P, a);
+        case NFL_PREC_FP32C * 4 + 1: return launch_gather_t<float, float, 1>(P, a);
+        case NFL_PREC_FP32C * 4 + 2: return launch_gather_t<float, float, 2>(P, a);
+        case NFL_PREC_FP32C * 4 + 3: return launch_gather_t<float, float, 3>(P, a);
     }
     return cudaErrorInvalidValue;
 }

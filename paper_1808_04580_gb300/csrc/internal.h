@@ -86,7 +86,7 @@ struct Plan {
 };
 
 // Precision-dependent element types.
-inline bool fft_is_double(int prec) { return prec != NFL_PREC_FP32; }
+inline bool fft_is_double(int prec) { return prec == NFL_PREC_FP64; }
 inline bool points_are_double(int prec) { return prec == NFL_PREC_FP64; }
 
 // launchers (stream-ordered, no host sync)

@@ -40,9 +40,10 @@ __global__ void bbox_partials(const double *v, int64_t n, int d, double *part) {
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s)
             for (int a = 0; a < 3; ++a) {
-                const double l2 = lo[a][threadIdx.x + s], h2 = hi[a][threadIdx.x + s];
-                lo[a][threadIdx.x] = (l2 != l2) ? l2 : fmin(lo[a][threadIdx.x], l2);
-                hi[a][threadIdx.x] = (h2 != h2) ? h2 : fmax(hi[a][threadIdx.x], h2);
+                const double l1 = lo[a][threadIdx.x], l2 = lo[a][threadIdx.x + s];
+                const double h1 = hi[a][threadIdx.x], h2 = hi[a][threadIdx.x + s];
+                lo[a][threadIdx.x] = (l1 != l1 || l2 != l2) ? NAN : fmin(l1, l2);
+                hi[a][threadIdx.x] = (h1 != h1 || h2 != h2) ? NAN : fmax(h1, h2);
             }
         __syncthreads();
     }
@@ -474,12 +475,13 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     for (int a = 0; a < d; ++a) {
         lo[a] = INFINITY;
         hi[a] = -INFINITY;
+        bool bad = false;   // a block saw a non-finite coordinate (fmin/fmax would drop NaN)
         for (int b = 0; b < rblocks; ++b) {
+            bad = bad || std::isnan(hp[b * 6 + a]) || std::isnan(hp[b * 6 + 3 + a]);
             lo[a] = std::fmin(lo[a], hp[b * 6 + a]);
             hi[a] = std::fmax(hi[a], hp[b * 6 + 3 + a]);
-            if (std::isnan(hp[b * 6 + a]) || std::isnan(hp[b * 6 + 3 + a])) lo[a] = NAN;
         }
-        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a])) { cudaFree(part); return NFL_ERR_INVALID_ARG; }
+        if (bad || !std::isfinite(lo[a]) || !std::isfinite(hi[a])) { cudaFree(part); return NFL_ERR_INVALID_ARG; }
         P->center[a] = 0.5 * (lo[a] + hi[a]);
     }
     radius_partials<<<rblocks, 256, 0, stream>>>(v, n, d, P->center[0], P->center[1], P->center[2], part);

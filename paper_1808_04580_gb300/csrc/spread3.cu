@@ -51,6 +51,43 @@ __device__ __forceinline__ double fixed_scale_of(double abs_sum) {
     return ldexp(1.0, k);
 }
 
+// acc[q] += coef * row[q], q < PA, with 16-byte shared loads of the row.
+template <typename T, int PA>
+__device__ __forceinline__ void fma_row(T *acc, T coef, const T *row) {
+    if (sizeof(T) == 4) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int q = 0; q < (PA + 3) / 4; ++q) {
+            const float4 w = r4[q];
+            if (4 * q + 0 < PA) acc[4 * q + 0] += coef * T(w.x);
+            if (4 * q + 1 < PA) acc[4 * q + 1] += coef * T(w.y);
+            if (4 * q + 2 < PA) acc[4 * q + 2] += coef * T(w.z);
+            if (4 * q + 3 < PA) acc[4 * q + 3] += coef * T(w.w);
+        }
+    } else {
+        const double2 *r2 = reinterpret_cast<const double2 *>(row);
+#pragma unroll
+        for (int q = 0; q < (PA + 1) / 2; ++q) {
+            const double2 w = r2[q];
+            if (2 * q + 0 < PA) acc[2 * q + 0] += coef * T(w.x);
+            if (2 * q + 1 < PA) acc[2 * q + 1] += coef * T(w.y);
+        }
+    }
+}
+
+// FP32 value (already scaled by 2^k, |v| < 2^62) -> nearest int64 with 32-bit
+// conversions only.  |v| = h 2^32 + l with h = floor(|v| 2^-32) and
+// 0 <= l < 2^32: both parts are exact in FP32 (power-of-two scaling; l keeps
+// a subset of the bits of |v|), and the sign is applied to the integer.
+__device__ __forceinline__ long long to_fixed(float v) {
+    const float av = fabsf(v);
+    const float hf = floorf(av * 2.3283064365386963e-10f);
+    const float lf = fmaf(hf, -4294967296.0f, av);
+    const unsigned long long mag = ((unsigned long long)__float2uint_rn(hf) << 32) + __float2uint_rn(lf);
+    return v < 0.f ? -(long long)mag : (long long)mag;
+}
+__device__ __forceinline__ long long to_fixed(double v) { return __double2ll_rn(v); }
+
 template <int M, int TE>
 struct ColGeom {
     static constexpr int PA = TE + 2 * M - 1;
@@ -126,15 +163,13 @@ __global__ void __launch_bounds__(ColGeom<M, TE>::NT) spread3_columns(Spread3Arg
                     const int jc = cc - ss[pt][2];
                     if ((unsigned)jb < (unsigned)TAPS && (unsigned)jc < (unsigned)TAPS) {
                         const T coef = xs[pt] * w1s[pt][jb] * w2s[pt][jc];
-                        const T *row = w0row[pt];
-#pragma unroll
-                        for (int q = 0; q < PA; ++q) acc[q] += coef * row[q];
+                        fma_row<T, PA>(acc, coef, w0row[pt]);
                     }
                 }
                 if (FIXED) {
 #pragma unroll
                     for (int q = 0; q < PA; ++q) {
-                        iacc[q] += __double2ll_rn(double(acc[q] * fscale));
+                        iacc[q] += to_fixed(acc[q] * fscale);
                         acc[q] = T(0);
                     }
                 }

@@ -78,6 +78,8 @@ typedef struct {
     double min_degree;    /* min_j d_E,j                                       */
     double max_degree;    /* max_j d_E,j                                       */
     int degree_ok;        /* 1 if min_degree > 0 (A, L_s and solvers usable)  */
+    int device_error;     /* 1 if a kernel's bounded wait ran out (results of
+                             the products since then are unreliable)          */
 } nfl_info;
 
 /*
@@ -110,7 +112,8 @@ nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double
 /* Release the plan and its device memory (synchronizes its stream). NULL is ignored. */
 void nfl_plan_destroy(nfl_plan *plan);
 
-/* Copy the plan's parameters and degree summary into *info. */
+/* Copy the plan's parameters, degree summary and device error flag into *info
+ * (synchronizes the plan's stream to read the flag). */
 nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info);
 
 /* Move subsequent work of the plan to another stream. */

@@ -166,6 +166,7 @@ static cudaError_t launch_gather_t(Plan &P, GatherArgs &a) {
 }
 
 cudaError_t launch_gather(Plan &P, int op, const double *x, double *y) {
+    if (gather_tc_available(P)) return launch_gather_tc(P, op, x, y);
     GatherArgs a;
     a.pts = P.pts;
     a.perm = P.perm;

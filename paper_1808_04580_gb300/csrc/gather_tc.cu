@@ -1,0 +1,346 @@
+// Interpolation in 3-D on the 5th-generation tensor cores (Alg. 1 step 3,
+// the window half of the NFFT):
+//   f_i = sum_{b,c} w1_i(b) w2_i(c) T[i, (b,c)],   T[i, (b,c)] = sum_a w0_i(a) G[a, (b,c)].
+//
+// For one tile of TE^3 cells the grid values G (tile plus halo, PA <= 16
+// positions per axis) are the B operand, K = a (padded to 16), N = (b, c)
+// (PA^2 padded to a multiple of 16).  Each batch of up to 128 nodes gives the
+// A operand W0 (M = 128 nodes, K = 16: node i's axis-0 window placed at its
+// offset, zero elsewhere).  T = W0 G is a dense 128 x N x 16 product, computed
+// by tcgen05.mma (kind::tf32) into TMEM.  FP32 accuracy comes from splitting
+// both operands into TF32 hi + lo parts: T = A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (the dropped A_lo B_lo term is ~2^-22 relative).
+//
+// Then thread i (TMEM lane i) reads its row of T in 16-column pieces and
+// contracts it with its own axis-1/axis-2 windows held in registers (column
+// n = b PA + c is a compile-time index in the unrolled loop), and applies the
+// W / A / L_s / degree epilogue in FP64.
+//
+// Operands use the canonical K-major layout without swizzle: core matrices
+// of 8 rows x 16 bytes (8 x 4 TF32 values), k-blocks of one 8-row group
+// 128 B apart (leading-dimension offset), 8-row groups 512 B apart (stride
+// offset).  One thread issues the MMAs; tcgen05.commit arrives on an mbarrier
+// that the CTA waits on with a bounded spin (a wait that runs out sets an
+// error flag and the kernel skips ahead rather than hang).
+#include <stdint.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace nfl {
+
+struct GatherTCArgs {
+    const PointF *pts;
+    const int32_t *perm;
+    const double *x;
+    double *y;
+    const double *dinv;
+    double *degree_out;
+    double *dinv_out;
+    const WorkItem *items;
+    int64_t nitems;
+    int ntile[3];
+    int L[3];
+    int wrap[3];
+    int ngrid;
+    const float *g;   // layout [x2][x1][x0]
+    int op;
+    float b, inv_den;
+    int *error_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float to_tf32(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N)
+// byte offsets in 16-byte units, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Byte offset of element (row, k) in a K-major, no-swizzle operand of K = 16.
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
+    return (uint32_t)((((row >> 3) * 4 + (k >> 2)) * 128) + ((row & 7) * 16) + ((k & 3) * 4));
+}
+
+template <int M, int TE>
+struct TCGeom {
+    static constexpr int PA = TE + 2 * M - 1;             // <= 16
+    static constexpr int NCOL = PA * PA;                  // (b, c) columns used
+    static constexpr int N = (NCOL + 15) / 16 * 16;       // MMA N (multiple of 16, <= 256)
+    static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    static constexpr int A_BYTES = 128 * 64;              // 128 rows x 16 TF32
+    static constexpr int B_BYTES = N * 64;
+};
+
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+template <int M, int TE>
+__global__ void __launch_bounds__(128, 1) gather3_tc(GatherTCArgs a) {
+    using G = TCGeom<M, TE>;
+    constexpr int PA = G::PA, N = G::N, NCOL = G::NCOL, TAPS = 2 * M;
+    static_assert(PA <= 16, "K is padded to 16");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sA_hi = smem_raw;
+    unsigned char *sA_lo = sA_hi + G::A_BYTES;
+    unsigned char *sB_hi = sA_lo + G::A_BYTES;
+    unsigned char *sB_lo = sB_hi + G::B_BYTES;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const float tm = float(M), tb = a.b, tden = a.inv_den;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(G::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    uint32_t phase = 0;
+    bool failed = false;
+
+    // instruction descriptor: D f32, A/B tf32, both K-major, N, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+
+    for (int64_t it = blockIdx.x; it < a.nitems && !failed; it += gridDim.x) {
+        const WorkItem w = a.items[it];
+        int tc[3];
+        tile_coords<3>(w.tile, a.ntile, tc);
+        // B operand: G[a][(b, c)] as rows n = b PA + c, k = a; hi/lo TF32 parts; zero padding
+        for (int e = tid; e < N * 16; e += 128) {
+            const int n = e >> 4, k = e & 15;
+            float v = 0.f;
+            if (n < NCOL && k < PA) {
+                const int bq = n / PA, cq = n - (n / PA) * PA;
+                int p0 = tc[0] * TE - (M - 1) + k;
+                int p1 = tc[1] * TE - (M - 1) + bq;
+                int p2 = tc[2] * TE - (M - 1) + cq;
+                if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+                if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+                if (p0 >= 0 && p0 < a.L[0] && p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2])
+                    v = a.g[((int64_t)p2 * a.L[1] + p1) * a.L[0] + p0];
+            }
+            const float hi = to_tf32(v);
+            const float lo = to_tf32(v - hi);
+            const uint32_t off = kmajor_off(n, k);
+            *reinterpret_cast<float *>(sB_hi + off) = hi;
+            *reinterpret_cast<float *>(sB_lo + off) = lo;
+        }
+
+        for (int base = w.start; base < w.start + w.count && !failed; base += 128) {
+            const int nb = min(128, w.start + w.count - base);
+            const bool live = tid < nb;
+            float w1p[PA], w2p[PA];
+            int kq = 0;
+            {
+                float w0p[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) w0p[q] = 0.f;
+#pragma unroll
+                for (int q = 0; q < PA; ++q) { w1p[q] = 0.f; w2p[q] = 0.f; }
+                if (live) {
+                    kq = base + tid;
+                    const PointF p = a.pts[kq];
+                    const int s0 = cell_axis(p.cell, 0) - tc[0] * TE;
+                    const int s1 = cell_axis(p.cell, 1) - tc[1] * TE;
+                    const int s2 = cell_axis(p.cell, 2) - tc[2] * TE;
+#pragma unroll
+                    for (int q = 0; q < PA; ++q) {
+                        const int j0 = q - s0, j1 = q - s1, j2 = q - s2;
+                        if ((unsigned)j0 < (unsigned)TAPS) w0p[q] = kb_weight<float>(p.f[0] + float(M - 1 - j0), tm, tb, tden);
+                        if ((unsigned)j1 < (unsigned)TAPS) w1p[q] = kb_weight<float>(p.f[1] + float(M - 1 - j1), tm, tb, tden);
+                        if ((unsigned)j2 < (unsigned)TAPS) w2p[q] = kb_weight<float>(p.f[2] + float(M - 1 - j2), tm, tb, tden);
+                    }
+                }
+                // A operand row tid: hi/lo TF32 parts, four 16-byte k-blocks
+#pragma unroll
+                for (int kb = 0; kb < 4; ++kb) {
+                    float4 h, l;
+                    h.x = to_tf32(w0p[4 * kb + 0]); l.x = to_tf32(w0p[4 * kb + 0] - h.x);
+                    h.y = to_tf32(w0p[4 * kb + 1]); l.y = to_tf32(w0p[4 * kb + 1] - h.y);
+                    h.z = to_tf32(w0p[4 * kb + 2]); l.z = to_tf32(w0p[4 * kb + 2] - h.z);
+                    h.w = to_tf32(w0p[4 * kb + 3]); l.w = to_tf32(w0p[4 * kb + 3] - h.w);
+                    const uint32_t off = kmajor_off(tid, 4 * kb);
+                    *reinterpret_cast<float4 *>(sA_hi + off) = h;
+                    *reinterpret_cast<float4 *>(sA_lo + off) = l;
+                }
+            }
+            // make the generic-proxy stores visible to the tensor core
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) {
+                const uint32_t aH = smem_u32(sA_hi), aL = smem_u32(sA_lo);
+                const uint32_t bH = smem_u32(sB_hi), bL = smem_u32(sB_lo);
+                int issued = 0;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {          // K = 16 in two steps of 8
+                    const uint32_t koff = ks * 256;        // two 128-byte k-blocks per step
+                    const uint64_t dAh = smem_desc(aH + koff, 128, 512), dAl = smem_desc(aL + koff, 128, 512);
+                    const uint64_t dBh = smem_desc(bH + koff, 128, 512), dBl = smem_desc(bL + koff, 128, 512);
+                    const uint64_t As[3] = {dAh, dAh, dAl};
+                    const uint64_t Bs[3] = {dBh, dBl, dBh};
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        const uint32_t acc = issued > 0 ? 1u : 0u;
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                            "l"(As[t]), "l"(Bs[t]), "r"(idesc), "r"(acc));
+                        ++issued;
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar)));
+            }
+            // bounded wait for the MMAs
+            {
+                uint32_t done = 0, spins = 0;
+                while (!done) {
+                    asm volatile(
+                        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                        : "=r"(done)
+                        : "r"(smem_u32(&mbar)), "r"(phase));
+                    if (!done && ++spins > kSpinLimit) break;
+                }
+                // every thread takes the same decision (barriers below stay matched)
+                if (__syncthreads_or(!done)) {
+                    failed = true;
+                    if (tid == 0) atomicExch(a.error_flag, 1);
+                }
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!failed) {
+                // thread tid owns TMEM lane tid: contract its row of T with w1 w2
+                float accb[PA];
+#pragma unroll
+                for (int q = 0; q < PA; ++q) accb[q] = 0.f;
+                const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+                for (int ch = 0; ch < N / 16; ++ch) {
+                    uint32_t r[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                          "=r"(r[15])
+                        : "r"(row_addr + ch * 16));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int n = ch * 16 + e;
+                        if (n < NCOL) accb[n / PA] += w2p[n % PA] * __uint_as_float(r[e]);
+                    }
+                }
+                float f = 0.f;
+#pragma unroll
+                for (int q = 0; q < PA; ++q) f += w1p[q] * accb[q];
+                if (live) {
+                    const int i = a.perm[kq];
+                    const double fd = double(f);
+                    if (a.op == OP_DEGREE) {
+                        const double dd = fd - 1.0;
+                        a.degree_out[i] = dd;
+                        a.dinv_out[kq] = dd > 0.0 ? 1.0 / sqrt(dd) : 0.0;
+                    } else if (a.op == OP_W) {
+                        a.y[i] = fd - a.x[i];
+                    } else {
+                        const double di = a.dinv[kq];
+                        const double xi = a.x[i];
+                        const double ax = di * (fd - di * xi);
+                        a.y[i] = a.op == OP_A ? ax : xi - ax;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        __syncthreads();
+    }
+    if (failed) {
+        // give MMAs still in flight a second bounded chance to finish before freeing TMEM
+        uint32_t done = 0, spins = 0;
+        while (!done && spins++ < kSpinLimit)
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_u32(&mbar)), "r"(phase ^ 1u));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS));
+}
+
+template <int M, int TE>
+static cudaError_t launch_tc(Plan &P, const GatherTCArgs &a) {
+    using G = TCGeom<M, TE>;
+    auto kern = gather3_tc<M, TE>;
+    // 100 KB of dynamic shared memory keeps at most two CTAs (2 x TMEM_COLS <= 512 columns) per SM
+    const int smem = 100 * 1024;
+    static_assert(2 * G::A_BYTES + 2 * G::B_BYTES + 1024 <= 100 * 1024, "operands fit");
+    NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int64_t grid = 2LL * P.num_sms;
+    if (grid > P.nitems) grid = P.nitems;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, 128, smem, P.stream>>>(a);
+    return cudaGetLastError();
+}
+
+bool gather_tc_available(const Plan &P) {
+    if (P.d != 3 || P.prec == NFL_PREC_FP64 || P.tile_edge != column_tile_edge(P.m)) return false;
+    return P.m == 2 || P.m == 3 || P.m == 4 || P.m == 6 || P.m == 7;
+}
+
+cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
+    GatherTCArgs a;
+    a.pts = reinterpret_cast<const PointF *>(P.pts);
+    a.perm = P.perm;
+    a.x = x;
+    a.y = y;
+    a.dinv = P.dinv_sorted;
+    a.degree_out = P.degree;
+    a.dinv_out = P.dinv_sorted;
+    a.items = P.items;
+    a.nitems = P.nitems;
+    for (int i = 0; i < 3; ++i) {
+        a.ntile[i] = P.ntile[i];
+        a.L[i] = P.L[i];
+        a.wrap[i] = P.wrap[i];
+    }
+    a.ngrid = P.ngrid;
+    a.g = reinterpret_cast<const float *>(P.g);
+    a.op = op;
+    a.b = float(P.kb_b);
+    a.inv_den = float(P.kb_inv_sinh_bm);
+    a.error_flag = P.error_flag;
+    switch (P.m) {
+        case 2: return launch_tc<2, 8>(P, a);
+        case 3: return launch_tc<3, 8>(P, a);
+        case 4: return launch_tc<4, 8>(P, a);
+        case 6: return launch_tc<6, 4>(P, a);
+        case 7: return launch_tc<7, 2>(P, a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace nfl

@@ -77,6 +77,7 @@ struct Plan {
     void *mult = nullptr;       // fused multiplier M_eff (real, FFT type)
     void *twiddle = nullptr;    // e^{-2 pi i q / ngrid}, q < ngrid/2 (complex, FFT type)
     double *scratch = nullptr;  // small device scalars (reductions, fixed-point scale)
+    int *error_flag = nullptr;  // set by a kernel whose bounded wait ran out
     int num_sms = 0;
 
     // stage timing: 5 events per timed column (before prep, spread, fft, gather, after)
@@ -102,6 +103,10 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y);
 // 3-D atomic-free spreading (spread3.cu): tile edge it needs for cut-off m (0: not available)
 int column_tile_edge(int m);
 cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool scale_dinv);
+
+// 3-D interpolation on the tensor cores (gather_tc.cu)
+bool gather_tc_available(const Plan &P);
+cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y);
 
 // number of kernels one column launches
 int kernels_per_column(const Plan &P);

@@ -447,6 +447,7 @@ static void free_plan(Plan *P) {
     cudaFree(P->mult);
     cudaFree(P->twiddle);
     cudaFree(P->scratch);
+    cudaFree(P->error_flag);
     delete P;
 }
 
@@ -461,6 +462,8 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     NFL_STATUS_TRY(cudaGetDevice(&dev));
     NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
     NFL_STATUS_TRY(cudaMalloc(&P->scratch, 64 * sizeof(double)));
+    NFL_STATUS_TRY(cudaMalloc(&P->error_flag, sizeof(int)));
+    NFL_STATUS_TRY(cudaMemsetAsync(P->error_flag, 0, sizeof(int), stream));
 
     const int rblocks = 1024;
     double *part = nullptr;
@@ -705,6 +708,13 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->min_degree = P->min_deg;
     info->max_degree = P->max_deg;
     info->degree_ok = P->degree_ok ? 1 : 0;
+    int flag = 0;
+    if (P->error_flag) {
+        if (cudaMemcpyAsync(&flag, P->error_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+            cudaStreamSynchronize(P->stream) != cudaSuccess)
+            return NFL_ERR_CUDA;
+    }
+    info->device_error = flag;
     return NFL_OK;
 }
 

@@ -41,7 +41,7 @@ class Info(ctypes.Structure):
         ("eps_B", ctypes.c_double), ("rho", ctypes.c_double), ("sigma_tilde", ctypes.c_double),
         ("center", ctypes.c_double * 3), ("box", ctypes.c_int * 3), ("tiles", ctypes.c_int64),
         ("work_items", ctypes.c_int64), ("min_degree", ctypes.c_double), ("max_degree", ctypes.c_double),
-        ("degree_ok", ctypes.c_int),
+        ("degree_ok", ctypes.c_int), ("device_error", ctypes.c_int),
     ]
 
 

@@ -100,6 +100,21 @@ def test_mixed_precision_forms(prec, tol):
     plan = Plan(gpu(v), 0.3, 32, 4, 4, -1.0, prec)
     assert rel(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x)) < tol
     assert rel(plan.apply_A(gpu(x)).cpu().numpy(), ref.apply_A(x)) < tol
+    assert plan.info()["device_error"] == 0
+
+
+# every 3-D tile shape of the column spread and the tensor-core interpolation
+@pytest.mark.parametrize("m,N", [(2, 16), (3, 16), (4, 32), (6, 32), (7, 32), (5, 32), (8, 32)])
+def test_fp32c_each_window_size(m, N):
+    n = 2600
+    v = _cloud("clusters", n, 3, seed=30 + m)
+    x = workloads.rhs(n, seed=31 + m)
+    ref = fastsum.NormalizedFastsum(v, 0.4, N, m, m)
+    plan = Plan(gpu(v), 0.4, N, m, m, -1.0, "fp32c")
+    y = plan.apply_W(gpu(x)).cpu().numpy()
+    assert rel(y, ref.apply_W(x)) < 2e-6
+    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=2e-6)
+    assert plan.info()["device_error"] == 0
 
 
 def test_block_of_right_hand_sides_equals_columns():

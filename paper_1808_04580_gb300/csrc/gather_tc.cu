@@ -19,7 +19,9 @@
 // Operands use the canonical K-major layout without swizzle: core matrices
 // of 8 rows x 16 bytes (8 x 4 TF32 values), k-blocks of one 8-row group
 // 128 B apart (leading-dimension offset), 8-row groups 512 B apart (stride
-// offset).  One thread issues the MMAs; tcgen05.commit arrives on an mbarrier
+// offset).  The (b, c) columns are processed in halves of N = 128 so that a
+// CTA needs 128 TMEM columns and four CTAs fit an SM.  One thread issues the
+// MMAs; tcgen05.commit arrives on an mbarrier
 // that the CTA waits on with a bounded spin (a wait that runs out sets an
 // error flag and the kernel skips ahead rather than hang).
 #include <stdint.h>
@@ -75,18 +77,19 @@ template <int M, int TE>
 struct TCGeom {
     static constexpr int PA = TE + 2 * M - 1;             // <= 16
     static constexpr int NCOL = PA * PA;                  // (b, c) columns used
-    static constexpr int N = (NCOL + 15) / 16 * 16;       // MMA N (multiple of 16, <= 256)
-    static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    static constexpr int N = 128;                         // MMA N per half
+    static constexpr int NH = (NCOL + N - 1) / N;         // halves of the column range
+    static constexpr int TMEM_COLS = 128;
     static constexpr int A_BYTES = 128 * 64;              // 128 rows x 16 TF32
-    static constexpr int B_BYTES = N * 64;
+    static constexpr int B_BYTES = NH * N * 64;           // all halves
 };
 
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 template <int M, int TE>
-__global__ void __launch_bounds__(128, 1) gather3_tc(GatherTCArgs a) {
+__global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     using G = TCGeom<M, TE>;
-    constexpr int PA = G::PA, N = G::N, NCOL = G::NCOL, TAPS = 2 * M;
+    constexpr int PA = G::PA, N = G::N, NH = G::NH, NCOL = G::NCOL, TAPS = 2 * M;
     static_assert(PA <= 16, "K is padded to 16");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sA_hi = smem_raw;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(128, 1) gather3_tc(GatherTCArgs a) {
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
         // B operand: G[a][(b, c)] as rows n = b PA + c, k = a; hi/lo TF32 parts; zero padding
-        for (int e = tid; e < N * 16; e += 128) {
+        for (int e = tid; e < NH * N * 16; e += 128) {
             const int n = e >> 4, k = e & 15;
             float v = 0.f;
             if (n < NCOL && k < PA) {
@@ -150,33 +153,37 @@ __global__ void __launch_bounds__(128, 1) gather3_tc(GatherTCArgs a) {
             float w1p[PA], w2p[PA];
             int kq = 0;
             {
-                float w0p[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) w0p[q] = 0.f;
-#pragma unroll
-                for (int q = 0; q < PA; ++q) { w1p[q] = 0.f; w2p[q] = 0.f; }
+                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+                int s0 = 0, s1 = 0, s2 = 0;
                 if (live) {
                     kq = base + tid;
                     const PointF p = a.pts[kq];
-                    const int s0 = cell_axis(p.cell, 0) - tc[0] * TE;
-                    const int s1 = cell_axis(p.cell, 1) - tc[1] * TE;
-                    const int s2 = cell_axis(p.cell, 2) - tc[2] * TE;
-#pragma unroll
-                    for (int q = 0; q < PA; ++q) {
-                        const int j0 = q - s0, j1 = q - s1, j2 = q - s2;
-                        if ((unsigned)j0 < (unsigned)TAPS) w0p[q] = kb_weight<float>(p.f[0] + float(M - 1 - j0), tm, tb, tden);
-                        if ((unsigned)j1 < (unsigned)TAPS) w1p[q] = kb_weight<float>(p.f[1] + float(M - 1 - j1), tm, tb, tden);
-                        if ((unsigned)j2 < (unsigned)TAPS) w2p[q] = kb_weight<float>(p.f[2] + float(M - 1 - j2), tm, tb, tden);
-                    }
+                    s0 = cell_axis(p.cell, 0) - tc[0] * TE;
+                    s1 = cell_axis(p.cell, 1) - tc[1] * TE;
+                    s2 = cell_axis(p.cell, 2) - tc[2] * TE;
+                    f0 = p.f[0]; f1 = p.f[1]; f2 = p.f[2];
                 }
-                // A operand row tid: hi/lo TF32 parts, four 16-byte k-blocks
+#pragma unroll
+                for (int q = 0; q < PA; ++q) {
+                    const int j1 = q - s1, j2 = q - s2;
+                    w1p[q] = (live && (unsigned)j1 < (unsigned)TAPS) ? kb_weight<float>(f1 + float(M - 1 - j1), tm, tb, tden) : 0.f;
+                    w2p[q] = (live && (unsigned)j2 < (unsigned)TAPS) ? kb_weight<float>(f2 + float(M - 1 - j2), tm, tb, tden) : 0.f;
+                }
+                // A operand row tid: axis-0 window, hi/lo TF32 parts, written four values at a time
 #pragma unroll
                 for (int kb = 0; kb < 4; ++kb) {
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = 4 * kb + u, j0 = q - s0;
+                        v[u] = (live && q < PA && (unsigned)j0 < (unsigned)TAPS)
+                                   ? kb_weight<float>(f0 + float(M - 1 - j0), tm, tb, tden) : 0.f;
+                    }
                     float4 h, l;
-                    h.x = to_tf32(w0p[4 * kb + 0]); l.x = to_tf32(w0p[4 * kb + 0] - h.x);
-                    h.y = to_tf32(w0p[4 * kb + 1]); l.y = to_tf32(w0p[4 * kb + 1] - h.y);
-                    h.z = to_tf32(w0p[4 * kb + 2]); l.z = to_tf32(w0p[4 * kb + 2] - h.z);
-                    h.w = to_tf32(w0p[4 * kb + 3]); l.w = to_tf32(w0p[4 * kb + 3] - h.w);
+                    h.x = to_tf32(v[0]); l.x = to_tf32(v[0] - h.x);
+                    h.y = to_tf32(v[1]); l.y = to_tf32(v[1] - h.y);
+                    h.z = to_tf32(v[2]); l.z = to_tf32(v[2] - h.z);
+                    h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
                     const uint32_t off = kmajor_off(tid, 4 * kb);
                     *reinterpret_cast<float4 *>(sA_hi + off) = h;
                     *reinterpret_cast<float4 *>(sA_lo + off) = l;
@@ -187,70 +194,79 @@ __global__ void __launch_bounds__(128, 1) gather3_tc(GatherTCArgs a) {
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;");
-            if (tid == 0) {
-                const uint32_t aH = smem_u32(sA_hi), aL = smem_u32(sA_lo);
-                const uint32_t bH = smem_u32(sB_hi), bL = smem_u32(sB_lo);
-                int issued = 0;
+            float accb[PA];
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {          // K = 16 in two steps of 8
-                    const uint32_t koff = ks * 256;        // two 128-byte k-blocks per step
-                    const uint64_t dAh = smem_desc(aH + koff, 128, 512), dAl = smem_desc(aL + koff, 128, 512);
-                    const uint64_t dBh = smem_desc(bH + koff, 128, 512), dBl = smem_desc(bL + koff, 128, 512);
-                    const uint64_t As[3] = {dAh, dAh, dAl};
-                    const uint64_t Bs[3] = {dBh, dBl, dBh};
+            for (int q = 0; q < PA; ++q) accb[q] = 0.f;
 #pragma unroll
-                    for (int t = 0; t < 3; ++t) {
-                        const uint32_t acc = issued > 0 ? 1u : 0u;
+            for (int h = 0; h < NH; ++h) {
+                if (failed) break;   // uniform: decided by __syncthreads_or below
+                if (tid == 0) {
+                    const uint32_t aH = smem_u32(sA_hi), aL = smem_u32(sA_lo);
+                    const uint32_t bH = smem_u32(sB_hi) + h * (N * 64), bL = smem_u32(sB_lo) + h * (N * 64);
+                    int issued = 0;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {          // K = 16 in two steps of 8
+                        const uint32_t koff = ks * 256;        // two 128-byte k-blocks per step
+                        const uint64_t dAh = smem_desc(aH + koff, 128, 512), dAl = smem_desc(aL + koff, 128, 512);
+                        const uint64_t dBh = smem_desc(bH + koff, 128, 512), dBl = smem_desc(bL + koff, 128, 512);
+                        const uint64_t As[3] = {dAh, dAh, dAl};
+                        const uint64_t Bs[3] = {dBh, dBl, dBh};
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            const uint32_t acc = issued > 0 ? 1u : 0u;
+                            asm volatile(
+                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                "l"(As[t]), "l"(Bs[t]), "r"(idesc), "r"(acc));
+                            ++issued;
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&mbar)));
+                }
+                // bounded wait for the MMAs
+                {
+                    uint32_t done = 0, spins = 0;
+                    while (!done) {
                         asm volatile(
-                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                            "l"(As[t]), "l"(Bs[t]), "r"(idesc), "r"(acc));
-                        ++issued;
+                            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                            : "=r"(done)
+                            : "r"(smem_u32(&mbar)), "r"(phase));
+                        if (!done && ++spins > kSpinLimit) break;
+                    }
+                    // every thread takes the same decision (barriers below stay matched)
+                    if (__syncthreads_or(!done)) {
+                        failed = true;
+                        if (tid == 0) atomicExch(a.error_flag, 1);
                     }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar)));
-            }
-            // bounded wait for the MMAs
-            {
-                uint32_t done = 0, spins = 0;
-                while (!done) {
-                    asm volatile(
-                        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                        : "=r"(done)
-                        : "r"(smem_u32(&mbar)), "r"(phase));
-                    if (!done && ++spins > kSpinLimit) break;
+                phase ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (!failed) {
+                    // thread tid owns TMEM lane tid: contract this half of its row of T with w1 w2
+                    const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+                    for (int ch = 0; ch < N / 8; ++ch) {
+                        if (h * N + ch * 8 >= NCOL) break;
+                        uint32_t r[8];
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                            : "r"(row_addr + ch * 8));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int n = h * N + ch * 8 + e;
+                            if (n < NCOL) accb[n / PA] += w2p[n % PA] * __uint_as_float(r[e]);
+                        }
+                    }
                 }
-                // every thread takes the same decision (barriers below stay matched)
-                if (__syncthreads_or(!done)) {
-                    failed = true;
-                    if (tid == 0) atomicExch(a.error_flag, 1);
-                }
+                // the next half's MMA overwrites the accumulator: order it after these loads
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+                asm volatile("tcgen05.fence::after_thread_sync;");
             }
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;");
             if (!failed) {
-                // thread tid owns TMEM lane tid: contract its row of T with w1 w2
-                float accb[PA];
-#pragma unroll
-                for (int q = 0; q < PA; ++q) accb[q] = 0.f;
-                const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-                for (int ch = 0; ch < N / 16; ++ch) {
-                    uint32_t r[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                          "=r"(r[15])
-                        : "r"(row_addr + ch * 16));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int n = ch * 16 + e;
-                        if (n < NCOL) accb[n / PA] += w2p[n % PA] * __uint_as_float(r[e]);
-                    }
-                }
                 float f = 0.f;
 #pragma unroll
                 for (int q = 0; q < PA; ++q) f += w1p[q] * accb[q];
@@ -295,11 +311,12 @@ template <int M, int TE>
 static cudaError_t launch_tc(Plan &P, const GatherTCArgs &a) {
     using G = TCGeom<M, TE>;
     auto kern = gather3_tc<M, TE>;
-    // 100 KB of dynamic shared memory keeps at most two CTAs (2 x TMEM_COLS <= 512 columns) per SM
-    const int smem = 100 * 1024;
-    static_assert(2 * G::A_BYTES + 2 * G::B_BYTES + 1024 <= 100 * 1024, "operands fit");
+    // 52 KB of dynamic shared memory (and <= 128 registers from the launch bounds)
+    // keep at most four CTAs, 4 x TMEM_COLS = 512 columns, per SM
+    const int smem = 52 * 1024;
+    static_assert(2 * G::A_BYTES + 2 * G::B_BYTES + 1024 <= 52 * 1024, "operands fit");
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int64_t grid = 2LL * P.num_sms;
+    int64_t grid = 4LL * P.num_sms;
     if (grid > P.nitems) grid = P.nitems;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, 128, smem, P.stream>>>(a);

@@ -4,8 +4,9 @@
 //
 // A CTA takes one chunk of one tile of TE^3 cells.  The tile with its halo
 // spans PA = TE + 2M - 1 grid positions per axis.  Thread (b, c) owns the
-// grid column t_1 = b, t_2 = c (PA^2 columns) and keeps the PA values along
-// t_0 in registers.  Nodes are handled in batches of 32: the CTA stages each
+// two grid columns t_1 = b, t_2 = c, c + 1 (c even) and keeps their 2 PA
+// values along t_0 in registers (the checks, coefficients and row loads of a
+// node are shared by both columns).  Nodes are handled in batches of 32: the CTA stages each
 // node's 3 x 2M window weights in shared memory (axis-0 weights placed at
 // their offset in a zero-padded row of length PA), then every thread whose
 // column lies under a node's support adds
@@ -16,8 +17,9 @@
 //
 // FP32C: after every batch the FP32 partial sums are converted to 64-bit
 // fixed point (scale 2^k from sum |x~|, as in the generic kernel) and added to
-// int64 registers, so everything beyond a 32-node partial sum is exact and the
-// result does not depend on the order of the global atomics.
+// thread-private int64 slots in shared memory, so everything beyond a 32-node
+// partial sum is exact and the result does not depend on the order of the
+// global atomics.
 #include <type_traits>
 
 #include "device.cuh"
@@ -75,6 +77,38 @@ __device__ __forceinline__ void fma_row(T *acc, T coef, const T *row) {
     }
 }
 
+// acc0[q] += k0 * row[q], acc1[q] += k1 * row[q]: one pass over the row for two columns.
+template <typename T, int PA>
+__device__ __forceinline__ void fma_row2(T *acc0, T *acc1, T k0, T k1, const T *row) {
+    if (sizeof(T) == 4) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int q = 0; q < (PA + 3) / 4; ++q) {
+            const float4 w = r4[q];
+            const T v[4] = {T(w.x), T(w.y), T(w.z), T(w.w)};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (4 * q + u < PA) {
+                    acc0[4 * q + u] += k0 * v[u];
+                    acc1[4 * q + u] += k1 * v[u];
+                }
+        }
+    } else {
+        const double2 *r2 = reinterpret_cast<const double2 *>(row);
+#pragma unroll
+        for (int q = 0; q < (PA + 1) / 2; ++q) {
+            const double2 w = r2[q];
+            const T v[2] = {T(w.x), T(w.y)};
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (2 * q + u < PA) {
+                    acc0[2 * q + u] += k0 * v[u];
+                    acc1[2 * q + u] += k1 * v[u];
+                }
+        }
+    }
+}
+
 // FP32 value (already scaled by 2^k, |v| < 2^62) -> nearest int64 with 32-bit
 // conversions only.  |v| = h 2^32 + l with h = floor(|v| 2^-32) and
 // 0 <= l < 2^32: both parts are exact in FP32 (power-of-two scaling; l keeps
@@ -92,47 +126,49 @@ template <int M, int TE>
 struct ColGeom {
     static constexpr int PA = TE + 2 * M - 1;
     static constexpr int PA4 = (PA + 3) / 4 * 4;
-    static constexpr int COLS = PA * PA;
-    static constexpr int NT = (COLS + 31) / 32 * 32;
+    static constexpr int CP = (PA + 1) / 2;              // column pairs per row b
+    static constexpr int OWN = PA * CP;                  // threads owning a pair (b, c0..c0+1)
+    static constexpr int NT = (OWN + 31) / 32 * 32;
     static constexpr int B = 32;
 };
 
 template <typename T, int M, int TE, bool FIXED>
 __global__ void __launch_bounds__(ColGeom<M, TE>::NT) spread3_columns(Spread3Args a) {
     using G = ColGeom<M, TE>;
-    constexpr int PA = G::PA, PA4 = G::PA4, B = G::B, TAPS = 2 * M;
+    constexpr int PA = G::PA, PA4 = G::PA4, CP = G::CP, B = G::B, TAPS = 2 * M, NT = G::NT;
     using Pt = typename PointOf<T>::type;
     __shared__ __align__(16) T w0row[B][PA4];
     __shared__ T w1s[B][TAPS], w2s[B][TAPS];
     __shared__ T frs[B][3];
     __shared__ T xs[B];
     __shared__ int ss[B][3];
+    // FP32C: exact int64 partial sums per owned cell, [q][half][thread] (thread-private slots)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    long long *iacc = reinterpret_cast<long long *>(smem_raw);
 
     const int tid = threadIdx.x;
-    const bool owner = tid < G::COLS;
-    const int cb = owner ? tid / PA : 0;
-    const int cc = owner ? tid % PA : 0;
+    const bool owner = tid < G::OWN;
+    const int cb = owner ? tid / CP : 0;
+    const int c0 = owner ? 2 * (tid % CP) : 0;
+    const bool has1 = owner && c0 + 1 < PA;
     const T tm = T(M), tb = T(a.b), tden = T(a.inv_den);
     const Pt *pts = reinterpret_cast<const Pt *>(a.pts);
     T fscale = T(1);
     if (FIXED) fscale = T(fixed_scale_of(*a.abs_sum));
+    if (FIXED)
+        for (int e = tid; e < PA * 2 * NT; e += NT) iacc[e] = 0;
 
     for (int64_t it = blockIdx.x; it < a.nitems; it += gridDim.x) {
         const WorkItem w = a.items[it];
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
-        T acc[PA];
-        long long iacc[FIXED ? PA : 1];
+        T acc0[PA], acc1[PA];
 #pragma unroll
-        for (int q = 0; q < PA; ++q) acc[q] = T(0);
-        if (FIXED) {
-#pragma unroll
-            for (int q = 0; q < PA; ++q) iacc[q] = 0;
-        }
+        for (int q = 0; q < PA; ++q) { acc0[q] = T(0); acc1[q] = T(0); }
 
         for (int base = w.start; base < w.start + w.count; base += B) {
             const int nb = min(B, w.start + w.count - base);
-            for (int e = tid; e < B * PA4; e += blockDim.x) (&w0row[0][0])[e] = T(0);
+            for (int e = tid; e < B * PA4; e += NT) (&w0row[0][0])[e] = T(0);
             if (tid < nb) {
                 const int k = base + tid;
                 const Pt p = pts[k];
@@ -146,31 +182,37 @@ __global__ void __launch_bounds__(ColGeom<M, TE>::NT) spread3_columns(Spread3Arg
                 }
             }
             __syncthreads();
-            for (int e = tid; e < nb * 3 * TAPS; e += blockDim.x) {
+            for (int e = tid; e < nb * 3 * TAPS; e += NT) {
                 const int pt = e / (3 * TAPS);
                 const int r = e - pt * 3 * TAPS;
                 const int ax = r / TAPS;
                 const int j = r - ax * TAPS;
                 const T wv = kb_weight<T>(frs[pt][ax] + T(M - 1) - T(j), tm, tb, tden);
                 if (ax == 0) w0row[pt][ss[pt][0] + j] = wv;
-                else if (ax == 1) w1s[pt][j] = wv;
+                else if (ax == 1) w1s[pt][j] = wv * xs[pt];   // x~ folded into the axis-1 window
                 else w2s[pt][j] = wv;
             }
             __syncthreads();
             if (owner) {
                 for (int pt = 0; pt < nb; ++pt) {
                     const int jb = cb - ss[pt][1];
-                    const int jc = cc - ss[pt][2];
-                    if ((unsigned)jb < (unsigned)TAPS && (unsigned)jc < (unsigned)TAPS) {
-                        const T coef = xs[pt] * w1s[pt][jb] * w2s[pt][jc];
-                        fma_row<T, PA>(acc, coef, w0row[pt]);
-                    }
+                    if ((unsigned)jb >= (unsigned)TAPS) continue;
+                    const int jc = c0 - ss[pt][2];
+                    const bool in0 = (unsigned)jc < (unsigned)TAPS;
+                    const bool in1 = has1 && (unsigned)(jc + 1) < (unsigned)TAPS;
+                    if (!in0 && !in1) continue;
+                    const T w1v = w1s[pt][jb];
+                    const T k0 = in0 ? w1v * w2s[pt][jc] : T(0);
+                    const T k1 = in1 ? w1v * w2s[pt][jc + 1] : T(0);
+                    fma_row2<T, PA>(acc0, acc1, k0, k1, w0row[pt]);
                 }
                 if (FIXED) {
 #pragma unroll
                     for (int q = 0; q < PA; ++q) {
-                        iacc[q] += to_fixed(acc[q] * fscale);
-                        acc[q] = T(0);
+                        iacc[(q * 2 + 0) * NT + tid] += to_fixed(acc0[q] * fscale);
+                        iacc[(q * 2 + 1) * NT + tid] += to_fixed(acc1[q] * fscale);
+                        acc0[q] = T(0);
+                        acc1[q] = T(0);
                     }
                 }
             }
@@ -180,21 +222,28 @@ __global__ void __launch_bounds__(ColGeom<M, TE>::NT) spread3_columns(Spread3Arg
         if (owner) {
             const int b0 = tc[0] * TE - (M - 1);
             int p1 = tc[1] * TE - (M - 1) + cb;
-            int p2 = tc[2] * TE - (M - 1) + cc;
             if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-            if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-            const bool ok12 = p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2];
 #pragma unroll
-            for (int q = 0; q < PA; ++q) {
-                int p0 = b0 + q;
-                if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-                if (!ok12 || p0 < 0 || p0 >= a.L[0]) continue;
-                const int64_t idx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
-                if (FIXED) {
-                    if (iacc[q] != 0)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + idx, (unsigned long long)iacc[q]);
-                } else {
-                    if (acc[q] != T(0)) atomicAdd(reinterpret_cast<T *>(a.grid) + idx, acc[q]);
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && !has1) break;
+                int p2 = tc[2] * TE - (M - 1) + c0 + half;
+                if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+                const bool ok12 = p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2];
+#pragma unroll
+                for (int q = 0; q < PA; ++q) {
+                    int p0 = b0 + q;
+                    if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                    const bool ok = ok12 && p0 >= 0 && p0 < a.L[0];
+                    const int64_t idx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+                    if (FIXED) {
+                        long long &slot = iacc[(q * 2 + half) * NT + tid];
+                        if (ok && slot != 0)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + idx, (unsigned long long)slot);
+                        slot = 0;
+                    } else {
+                        const T v = half == 0 ? acc0[q] : acc1[q];
+                        if (ok && v != T(0)) atomicAdd(reinterpret_cast<T *>(a.grid) + idx, v);
+                    }
                 }
             }
         }
@@ -205,13 +254,15 @@ template <typename T, int M, int TE, bool FIXED>
 static cudaError_t launch_cols(Plan &P, const Spread3Args &a) {
     using G = ColGeom<M, TE>;
     auto kern = spread3_columns<T, M, TE, FIXED>;
+    const int smem = FIXED ? G::PA * 2 * G::NT * (int)sizeof(long long) : 0;
+    NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, 0));
+    NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * P.num_sms;
     if (grid > P.nitems) grid = P.nitems;
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, G::NT, 0, P.stream>>>(a);
+    kern<<<(unsigned)grid, G::NT, smem, P.stream>>>(a);
     return cudaGetLastError();
 }
 

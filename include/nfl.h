@@ -139,6 +139,19 @@ nfl_status nfl_apply_Ls(nfl_plan *plan, const double *x, int64_t ldx,
                         double *y, int64_t ldy, int nrhs);
 
 /*
+ * Products for many independent graphs in one call (a batch of plans):
+ * y_g = op(x_g) for g < G with op 0 = W, 1 = A, 2 = L_s, each x_g / y_g a
+ * device block of nrhs columns with leading dimension ld[g] >= n_g.  All
+ * work is issued on the stream of plans[0] (every plan is moved to it), in
+ * plan order, without host synchronization, so the whole batch can be
+ * captured into one CUDA graph and replayed as a single launch.
+ *   plans, x, y, ld: host arrays of G entries; plans must be distinct.
+ * Returns the first failing plan's status (earlier products are issued).
+ */
+nfl_status nfl_apply_batched(nfl_plan *const *plans, int G, int op, const double *const *x,
+                             double *const *y, const int64_t *ld, int nrhs);
+
+/*
  * k smallest eigenpairs of L_s, i.e. the k largest of A (Sec. 2), by the
  * Lanczos process with full reorthogonalization (Sec. 4, eq. (krylov1)).
  * Ritz pair (theta, Q_k w) is accepted when |beta_{k+1} w_k| <= tol (Sec. 4).

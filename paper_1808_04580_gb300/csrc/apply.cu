@@ -65,6 +65,22 @@ nfl_status nfl_apply_Ls(nfl_plan *plan, const double *x, int64_t ldx, double *y,
     return nfl::apply(plan, nfl::OP_LS, x, ldx, y, ldy, nrhs);
 }
 
+nfl_status nfl_apply_batched(nfl_plan *const *plans, int G, int op, const double *const *x, double *const *y,
+                             const int64_t *ld, int nrhs) {
+    if (!plans || !x || !y || !ld || G < 0 || op < 0 || op > 2) return NFL_ERR_INVALID_ARG;
+    if (G == 0) return NFL_OK;
+    if (!plans[0]) return NFL_ERR_INVALID_ARG;
+    const cudaStream_t s = reinterpret_cast<nfl::Plan *>(plans[0])->stream;
+    const int ops[3] = {nfl::OP_W, nfl::OP_A, nfl::OP_LS};
+    for (int g = 0; g < G; ++g) {
+        if (!plans[g]) return NFL_ERR_INVALID_ARG;
+        reinterpret_cast<nfl::Plan *>(plans[g])->stream = s;
+        const nfl_status st = nfl::apply(plans[g], ops[op], x[g], ld[g], y[g], ld[g], nrhs);
+        if (st != NFL_OK) return st;
+    }
+    return NFL_OK;
+}
+
 nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable) {
     if (!plan) return NFL_ERR_INVALID_ARG;
     nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plan);

@@ -62,6 +62,8 @@ SIGNATURES = {
     "nfl_apply_Ls": (_I, [_P, _P, _L, _P, _L, _I]),
     "nfl_lanczos_k_smallest": (_I, [_P, _I, _D, _I, ctypes.c_uint64, _P, _P, ctypes.POINTER(_I)]),
     "nfl_cg_solve": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nfl_apply_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                               ctypes.POINTER(_L), _I]),
     "nfl_cg_solve_noalloc": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_plan_set_profiling": (_I, [_P, _I]),
     "nfl_plan_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
@@ -235,3 +237,37 @@ class Plan:
         if check:
             _check(st, "nfl_cg_solve_noalloc" if noalloc else "nfl_cg_solve")
         return u, it.value, rel.value, st
+
+
+_OPS = {"W": 0, "A": 1, "Ls": 2}
+
+
+def apply_batched(plans, xs, op="Ls", outs=None):
+    """op(x_g) for a batch of plans in one library call on the current stream.
+
+    xs: list of (n_g,) or (n_g, r) CUDA float64 tensors (same r for all);
+    returns the list of outputs.  The call issues no host synchronization, so
+    it can be captured into a torch.cuda.CUDAGraph and replayed as one launch.
+    """
+    G = len(plans)
+    if len(xs) != G:
+        raise ValueError("one right-hand side block per plan")
+    cols, ys, vecs, nrhs = [], [], [], None
+    for g, (plan, x) in enumerate(zip(plans, xs)):
+        xc, r, vec = _as_columns(x, plan.n)
+        if nrhs is None:
+            nrhs = r
+        elif r != nrhs:
+            raise ValueError("every block needs the same number of columns")
+        cols.append(xc)
+        ys.append(torch.empty_like(xc) if outs is None else outs[g])
+        vecs.append(vec)
+    for plan in plans:
+        plan._sync_stream()
+    arr_p = (_P * G)(*[p._h for p in plans])
+    arr_x = (_P * G)(*[c.data_ptr() for c in cols])
+    arr_y = (_P * G)(*[y.data_ptr() for y in ys])
+    arr_l = (_L * G)(*[p.n for p in plans])
+    _check(_lib().nfl_apply_batched(arr_p, G, _OPS[op], arr_x, arr_y, arr_l, int(nrhs or 1)), "nfl_apply_batched")
+    return [y if v else y.t() for y, v in zip(ys, vecs)]
+

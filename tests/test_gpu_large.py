@@ -1,0 +1,110 @@
+"""Full-size workloads through the C ABI, checked on sampled rows or by properties.
+
+At n = 10^6 .. 10^7 the oracle cannot form the whole product, so the GPU
+result is compared with the direct FP64 sum (O1, plain C over all n sources)
+on sampled rows, and the mixed forms with the FP64 form of the same plan on
+every row.  Tolerances: the method's own error at these parameters plus the
+mixed-precision budget of 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import direct
+from paper_1808_04580_gb300 import Plan, workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def ball10m():
+    v = workloads.ball_plus_clusters(10_000_000, seed=0)
+    x = workloads.rhs(10_000_000, seed=1)
+    return v, x
+
+
+def test_ball10m_products_against_direct_sum(ball10m):
+    """n = 10^7, sigma 0.08, N 128, m 6: W x in every form against O1 on 256 rows."""
+    v, x = ball10m
+    rows = np.random.default_rng(5).choice(v.shape[0], 256, replace=False)
+    ref = direct.rows_W(v, 0.08, x, rows)
+    vg, xg = gpu(v), gpu(x)
+    out = {}
+    for prec in ("fp64", "fp32c", "fp32"):
+        plan = Plan(vg, 0.08, 128, 6, 6, -1.0, prec)
+        out[prec] = plan.apply_W(xg).cpu().numpy()
+        assert plan.info()["device_error"] == 0
+        plan.close()
+        assert rel(out[prec][rows], ref) < 1e-6, prec
+    assert rel(out["fp32c"], out["fp64"]) < 1e-6
+    assert rel(out["fp32"], out["fp64"]) < 1e-6
+
+
+def test_ball10m_normalized_identity(ball10m):
+    """L_s,E D_E^{1/2} 1 = 0 holds for the fast operator at any size (Alg. 2 step 4)."""
+    v, _ = ball10m
+    plan = Plan(gpu(v), 0.08, 128, 6, 6, -1.0, "fp32c")
+    d = plan.degree()
+    r = plan.apply_Ls(torch.sqrt(d)).cpu().numpy()
+    assert np.abs(r).max() < 1e-5 * float(torch.sqrt(d).max())
+
+
+def test_image1m_mixed_against_fp64():
+    """1000 x 1000 Voronoi image, sigma 0.1, N 64, m 4: FP32C against FP64 on every row."""
+    v, _ = workloads.voronoi_image(seed=0)
+    x = workloads.rhs(v.shape[0], seed=2)
+    vg, xg = gpu(v), gpu(x)
+    p64 = Plan(vg, 0.1, 64, 4, 4, -1.0, "fp64")
+    p32 = Plan(vg, 0.1, 64, 4, 4, -1.0, "fp32c")
+    y64 = p64.apply_Ls(xg).cpu().numpy()
+    y32 = p32.apply_Ls(xg).cpu().numpy()
+    # L_s x = x - A x: measure the error relative to ||A x||, which x would hide
+    assert rel(x - y32, x - y64) < 1e-6
+    w64 = p64.apply_W(xg).cpu().numpy()
+    rows = np.random.default_rng(7).choice(v.shape[0], 128, replace=False)
+    ref = direct.rows_W(v, 0.1, x, rows)
+    assert rel(w64[rows], ref) < 1e-4   # N = 64 kernel approximation error
+
+
+def test_lanczos_200k_fp32c_against_fp64():
+    n = 200_000
+    v = workloads.two_arm_spiral(n, seed=8)
+    vg = gpu(v)
+    p64 = Plan(vg, 0.5, 32, 4, 4, -1.0, "fp64")
+    p32 = Plan(vg, 0.5, 32, 4, 4, -1.0, "fp32c")
+    e64, V64, it64, st64 = p64.lanczos_k_smallest(10, tol=1e-9, maxit=300, seed=3)
+    e32, V32, it32, st32 = p32.lanczos_k_smallest(10, tol=1e-7, maxit=300, seed=3)
+    assert st64 == 0 and st32 == 0
+    assert np.abs(e32 - e64).max() < 1e-6
+    # residuals of the FP64 pairs under the FP64 operator
+    R = p64.apply_A(V64).cpu().numpy() - V64.cpu().numpy() * (1.0 - e64)[None, :]
+    assert np.linalg.norm(R, axis=0).max() < 1e-8
+
+
+def test_cg_moons500k():
+    """(L_s + 10 diag(mask)) u = f on a two-moon cloud, 1% labelled (SSL system of Sec. 6.2.2)."""
+    v, lab = workloads.two_moons(500_000, seed=1)
+    n = v.shape[0]
+    rng = np.random.default_rng(4)
+    mask = (rng.uniform(size=n) < 0.01).astype(np.float64)
+    f = mask * lab
+    vg = gpu(v)
+    sols = {}
+    for prec in ("fp64", "fp32c"):
+        plan = Plan(vg, 0.2, 128, 4, 4, -1.0, prec)
+        u, iters, relres, st = plan.cg_solve(gpu(f), beta=1.0, shift=gpu(10.0 * mask), tol=1e-6, maxit=3000)
+        assert st == 0 and relres <= 1e-6, (prec, iters, relres)
+        sols[prec] = u.cpu().numpy()
+    assert rel(sols["fp32c"], sols["fp64"]) < 1e-3
+    # the labelled signs are reproduced on the labelled nodes
+    lab_idx = np.nonzero(mask)[0]
+    assert np.mean(np.sign(sols["fp64"][lab_idx]) == lab[lab_idx]) > 0.99

@@ -120,25 +120,40 @@ __device__ __forceinline__ int tile_of(const int *cell, const Geometry &G) {
     return t;
 }
 
-__global__ void count_tiles(const double *v, int64_t n, Geometry G, int32_t *tile_id, int32_t *rank, int32_t *count) {
+// Sort key of a node: its tile, then (when cells_per_tile > 1) its cell inside
+// the tile, so that the nodes of one cell are contiguous.
+__global__ void count_keys(const double *v, int64_t n, Geometry G, int cells_per_tile, int32_t *key_of,
+                           int32_t *rank, int32_t *count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int cell[3];
         double frac[3];
         node_cell(v, i, G, cell, frac);
-        const int t = tile_of(cell, G);
-        tile_id[i] = t;
-        rank[i] = atomicAdd(&count[t], 1);
+        int local = 0;
+        if (cells_per_tile > 1)
+            for (int a = 0; a < G.d; ++a) local = local * G.tile_edge + cell[a] % G.tile_edge;
+        const int key = tile_of(cell, G) * cells_per_tile + local;
+        key_of[i] = key;
+        rank[i] = atomicAdd(&count[key], 1);
+    }
+}
+
+// Per-tile node counts and starts from the per-key offsets.
+__global__ void tiles_from_keys(const int64_t *kstart, int64_t ntiles, int cells_per_tile, int32_t *count,
+                                int64_t *start) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        start[t] = kstart[t * cells_per_tile];
+        count[t] = (int32_t)(kstart[(t + 1) * cells_per_tile] - kstart[t * cells_per_tile]);
     }
 }
 
 template <typename PT, typename T>
-__global__ void scatter_nodes(const double *v, int64_t n, Geometry G, const int32_t *tile_id, const int32_t *rank,
+__global__ void scatter_nodes(const double *v, int64_t n, Geometry G, const int32_t *key_of, const int32_t *rank,
                               const int64_t *start, PT *pts, int32_t *perm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int cell[3] = {0, 0, 0};
         double frac[3] = {0, 0, 0};
         node_cell(v, i, G, cell, frac);
-        const int64_t pos = start[tile_id[i]] + rank[i];
+        const int64_t pos = start[key_of[i]] + rank[i];
         PT p;
         for (int a = 0; a < 3; ++a) p.f[a] = T(a < G.d ? frac[a] : 0.0);
         p.cell = cell[0] | (cell[1] << 10) | (cell[2] << 20);
@@ -527,16 +542,21 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     P->tiles_total = 1;
     for (int a = 0; a < d; ++a) P->tiles_total *= P->ntile[a];
 
-    // counting sort of the nodes by tile
-    int32_t *tile_id = nullptr, *rank = nullptr, *count = nullptr, *chunks = nullptr;
-    int64_t *start = nullptr, *item_off = nullptr;
+    // counting sort of the nodes by tile and, inside a tile, by cell
+    const int64_t nt = P->tiles_total;
+    int cpt = 1;
+    for (int a = 0; a < d; ++a) cpt *= P->tile_edge;
+    if (nt * cpt > (int64_t)1 << 26) cpt = 1;   // very large grids: sort by tile only
+    const int64_t nkeys = nt * cpt;
+    int32_t *key_of = nullptr, *rank = nullptr, *kcount = nullptr, *count = nullptr, *chunks = nullptr;
+    int64_t *kstart = nullptr, *start = nullptr, *item_off = nullptr;
     unsigned long long *nonempty = nullptr;
     auto cleanup = [&]() {
-        cudaFree(tile_id); cudaFree(rank); cudaFree(count); cudaFree(chunks);
-        cudaFree(start); cudaFree(item_off); cudaFree(nonempty);
+        cudaFree(key_of); cudaFree(rank); cudaFree(kcount); cudaFree(count); cudaFree(chunks);
+        cudaFree(kstart); cudaFree(start); cudaFree(item_off); cudaFree(nonempty);
     };
-    const int64_t nt = P->tiles_total;
-    if (cudaMalloc(&tile_id, n * 4) != cudaSuccess || cudaMalloc(&rank, n * 4) != cudaSuccess ||
+    if (cudaMalloc(&key_of, n * 4) != cudaSuccess || cudaMalloc(&rank, n * 4) != cudaSuccess ||
+        cudaMalloc(&kcount, nkeys * 4) != cudaSuccess || cudaMalloc(&kstart, (nkeys + 1) * 8) != cudaSuccess ||
         cudaMalloc(&count, nt * 4) != cudaSuccess || cudaMalloc(&chunks, nt * 4) != cudaSuccess ||
         cudaMalloc(&start, (nt + 1) * 8) != cudaSuccess || cudaMalloc(&item_off, (nt + 1) * 8) != cudaSuccess ||
         cudaMalloc(&nonempty, 8) != cudaSuccess) {
@@ -551,13 +571,14 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
         return NFL_ERR_OUT_OF_MEMORY;
     }
     const int blocks = P->num_sms * 8;
-    ce = cudaMemsetAsync(count, 0, nt * 4, stream);
+    ce = cudaMemsetAsync(kcount, 0, nkeys * 4, stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(nonempty, 0, 8, stream);
     if (ce != cudaSuccess) { cleanup(); return NFL_ERR_CUDA; }
-    count_tiles<<<blocks, 256, 0, stream>>>(v, n, G, tile_id, rank, count);
-    exclusive_scan<<<1, 1024, 0, stream>>>(count, nt, start);
-    if (dbl) scatter_nodes<PointD, double><<<blocks, 256, 0, stream>>>(v, n, G, tile_id, rank, start, (PointD *)P->pts, P->perm);
-    else scatter_nodes<PointF, float><<<blocks, 256, 0, stream>>>(v, n, G, tile_id, rank, start, (PointF *)P->pts, P->perm);
+    count_keys<<<blocks, 256, 0, stream>>>(v, n, G, cpt, key_of, rank, kcount);
+    exclusive_scan<<<1, 1024, 0, stream>>>(kcount, nkeys, kstart);
+    tiles_from_keys<<<blocks, 256, 0, stream>>>(kstart, nt, cpt, count, start);
+    if (dbl) scatter_nodes<PointD, double><<<blocks, 256, 0, stream>>>(v, n, G, key_of, rank, kstart, (PointD *)P->pts, P->perm);
+    else scatter_nodes<PointF, float><<<blocks, 256, 0, stream>>>(v, n, G, key_of, rank, kstart, (PointF *)P->pts, P->perm);
     chunks_per_tile<<<blocks, 256, 0, stream>>>(count, nt, chunks, nonempty);
     exclusive_scan<<<1, 1024, 0, stream>>>(chunks, nt, item_off);
     unsigned long long h_nonempty = 0;

@@ -1,25 +1,23 @@
-// Window spreading in 3-D without atomics in the inner loop (Alg. 1 step 1,
-// spreading half of the adjoint NFFT):
+// Window spreading in 3-D (Alg. 1 step 1, the window half of the adjoint NFFT):
 //   h_t = sum_i x~_i phi(n v~_i0 - t_0) phi(n v~_i1 - t_1) phi(n v~_i2 - t_2).
 //
-// A CTA takes one chunk of one tile of TE^3 cells.  The tile with its halo
-// spans PA = TE + 2M - 1 grid positions per axis.  Thread (b, c) owns the
-// two grid columns t_1 = b, t_2 = c, c + 1 (c even) and keeps their 2 PA
-// values along t_0 in registers (the checks, coefficients and row loads of a
-// node are shared by both columns).  Nodes are handled in batches of 32: the CTA stages each
-// node's 3 x 2M window weights in shared memory (axis-0 weights placed at
-// their offset in a zero-padded row of length PA), then every thread whose
-// column lies under a node's support adds
-//   coef * w0row[a],  coef = x~ * w1[b - s1] * w2[c - s2],   a = 0..PA-1,
-// to its registers: PA fused multiply-adds per node and column, in node
-// order, with no shared-memory atomics.  At the end of the chunk each column
-// adds its PA values to the global grid (one atomic per non-zero cell).
+// The plan sorts the nodes of every tile by cell, so the nodes of one cell
+// are contiguous; they share the whole (2M)^3 support.  A CTA takes one chunk
+// of one tile (TE^3 cells) and keeps the tile plus halo (PA = TE + 2M - 1 per
+// axis) in shared memory.  Thread (jb, jc) owns one support-relative column of
+// the current cell and 2M registers along axis 0; each node adds
+// coef * w0[ja], coef = x~ w1[jb] w2[jc], for ja = 0..2M-1: every fused
+// multiply-add lands in the support, with no range tests.  When the cell
+// changes (and before every fixed-point carry for FP32C) each thread adds
+// its 2M values to the shared tile with shared-memory atomics (supports of
+// neighbouring cells overlap); at the end of the chunk the non-zero tile
+// cells go to the global grid with one atomic each.
 //
-// FP32C: after every batch the FP32 partial sums are converted to 64-bit
-// fixed point (scale 2^k from sum |x~|, as in the generic kernel) and added to
-// thread-private int64 slots in shared memory, so everything beyond a 32-node
-// partial sum is exact and the result does not depend on the order of the
-// global atomics.
+// FP32C: the shared FP32 tile only ever holds the sums of 8 batches (256
+// nodes); then it is carried into a 64-bit fixed-point tile (scale 2^k from
+// sum |x~|, so no partial sum can overflow).  Everything after that is
+// exact integer addition, so the result does not depend on the order of the
+// atomics.
 #include <type_traits>
 
 #include "device.cuh"
@@ -122,64 +120,81 @@ __device__ __forceinline__ long long to_fixed(float v) {
 }
 __device__ __forceinline__ long long to_fixed(double v) { return __double2ll_rn(v); }
 
+constexpr int kCarry = 8;   // FP32C: batches (of 32 nodes) per fixed-point carry
+
 template <int M, int TE>
-struct ColGeom {
-    static constexpr int PA = TE + 2 * M - 1;
-    static constexpr int PA4 = (PA + 3) / 4 * 4;
-    static constexpr int CP = (PA + 1) / 2;              // column pairs per row b
-    static constexpr int OWN = PA * CP;                  // threads owning a pair (b, c0..c0+1)
+struct CellGeom {
+    static constexpr int PA = TE + 2 * M - 1;     // tile + halo per axis
+    static constexpr int TAPS = 2 * M;
+    static constexpr int TAPS4 = (TAPS + 3) / 4 * 4;
+    static constexpr int OWN = TAPS * TAPS;       // threads owning a support column (jb, jc)
     static constexpr int NT = (OWN + 31) / 32 * 32;
-    static constexpr int B = 32;
+    static constexpr int B = 32;                  // nodes staged per batch
 };
 
 template <typename T, int M, int TE, bool FIXED>
-__global__ void __launch_bounds__(ColGeom<M, TE>::NT) spread3_columns(Spread3Args a) {
-    using G = ColGeom<M, TE>;
-    constexpr int PA = G::PA, PA4 = G::PA4, CP = G::CP, B = G::B, TAPS = 2 * M, NT = G::NT;
+__global__ void __launch_bounds__(CellGeom<M, TE>::NT) spread3_cells(Spread3Args a) {
+    using G = CellGeom<M, TE>;
+    constexpr int PA = G::PA, PA3 = PA * PA * PA, TAPS = G::TAPS, TAPS4 = G::TAPS4, B = G::B, NT = G::NT;
     using Pt = typename PointOf<T>::type;
-    __shared__ __align__(16) T w0row[B][PA4];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);                                        // PA^3, [a][b][c]
+    unsigned long long *itile = reinterpret_cast<unsigned long long *>(smem_raw + ((PA3 * sizeof(T) + 15) / 16) * 16);
+    __shared__ __align__(16) T w0s[B][TAPS4];
     __shared__ T w1s[B][TAPS], w2s[B][TAPS];
     __shared__ T frs[B][3];
     __shared__ T xs[B];
-    __shared__ int ss[B][3];
-    // FP32C: exact int64 partial sums per owned cell, [q][half][thread] (thread-private slots)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    long long *iacc = reinterpret_cast<long long *>(smem_raw);
+    __shared__ int org[B];                                // tile-local base cell, 8 bits per axis
 
     const int tid = threadIdx.x;
     const bool owner = tid < G::OWN;
-    const int cb = owner ? tid / CP : 0;
-    const int c0 = owner ? 2 * (tid % CP) : 0;
-    const bool has1 = owner && c0 + 1 < PA;
+    const int jb = owner ? tid / TAPS : 0;
+    const int jc = owner ? tid % TAPS : 0;
     const T tm = T(M), tb = T(a.b), tden = T(a.inv_den);
     const Pt *pts = reinterpret_cast<const Pt *>(a.pts);
     T fscale = T(1);
     if (FIXED) fscale = T(fixed_scale_of(*a.abs_sum));
-    if (FIXED)
-        for (int e = tid; e < PA * 2 * NT; e += NT) iacc[e] = 0;
+    for (int e = tid; e < PA3; e += NT) {
+        tile[e] = T(0);
+        if (FIXED) itile[e] = 0ull;
+    }
+
+    // add this thread's 2M values along a for the support column (jb, jc) of cell o
+    auto flush = [&](int o, T *acc) {
+        const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
+        T *col = tile + (s0 * PA + s1 + jb) * PA + s2 + jc;
+#pragma unroll
+        for (int ja = 0; ja < TAPS; ++ja) {
+            if (acc[ja] != T(0)) atomicAdd(col + ja * PA * PA, acc[ja]);
+            acc[ja] = T(0);
+        }
+    };
 
     for (int64_t it = blockIdx.x; it < a.nitems; it += gridDim.x) {
         const WorkItem w = a.items[it];
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
-        T acc0[PA], acc1[PA];
+        T acc[TAPS];
 #pragma unroll
-        for (int q = 0; q < PA; ++q) { acc0[q] = T(0); acc1[q] = T(0); }
+        for (int q = 0; q < TAPS; ++q) acc[q] = T(0);
+        int cur = -1;
+        int bcount = 0;
 
         for (int base = w.start; base < w.start + w.count; base += B) {
             const int nb = min(B, w.start + w.count - base);
-            for (int e = tid; e < B * PA4; e += NT) (&w0row[0][0])[e] = T(0);
             if (tid < nb) {
                 const int k = base + tid;
                 const Pt p = pts[k];
                 double xv = a.ones ? 1.0 : a.x[a.perm[k]];
                 if (a.dinv) xv *= a.dinv[k];
                 xs[tid] = T(xv);
+                int o = 0;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
-                    ss[tid][ax] = cell_axis(p.cell, ax) - tc[ax] * TE;
+                    o |= (cell_axis(p.cell, ax) - tc[ax] * TE) << (8 * ax);
                     frs[tid][ax] = T(p.f[ax]);
                 }
+                org[tid] = o;
             }
             __syncthreads();
             for (int e = tid; e < nb * 3 * TAPS; e += NT) {
@@ -188,73 +203,76 @@ __global__ void __launch_bounds__(ColGeom<M, TE>::NT) spread3_columns(Spread3Arg
                 const int ax = r / TAPS;
                 const int j = r - ax * TAPS;
                 const T wv = kb_weight<T>(frs[pt][ax] + T(M - 1) - T(j), tm, tb, tden);
-                if (ax == 0) w0row[pt][ss[pt][0] + j] = wv;
+                if (ax == 0) w0s[pt][j] = wv;
                 else if (ax == 1) w1s[pt][j] = wv * xs[pt];   // x~ folded into the axis-1 window
                 else w2s[pt][j] = wv;
             }
             __syncthreads();
             if (owner) {
                 for (int pt = 0; pt < nb; ++pt) {
-                    const int jb = cb - ss[pt][1];
-                    if ((unsigned)jb >= (unsigned)TAPS) continue;
-                    const int jc = c0 - ss[pt][2];
-                    const bool in0 = (unsigned)jc < (unsigned)TAPS;
-                    const bool in1 = has1 && (unsigned)(jc + 1) < (unsigned)TAPS;
-                    if (!in0 && !in1) continue;
-                    const T w1v = w1s[pt][jb];
-                    const T k0 = in0 ? w1v * w2s[pt][jc] : T(0);
-                    const T k1 = in1 ? w1v * w2s[pt][jc + 1] : T(0);
-                    fma_row2<T, PA>(acc0, acc1, k0, k1, w0row[pt]);
-                }
-                if (FIXED) {
-#pragma unroll
-                    for (int q = 0; q < PA; ++q) {
-                        iacc[(q * 2 + 0) * NT + tid] += to_fixed(acc0[q] * fscale);
-                        iacc[(q * 2 + 1) * NT + tid] += to_fixed(acc1[q] * fscale);
-                        acc0[q] = T(0);
-                        acc1[q] = T(0);
+                    const int o = org[pt];
+                    if (o != cur) {
+                        if (cur >= 0) flush(cur, acc);
+                        cur = o;
                     }
+                    const T coef = w1s[pt][jb] * w2s[pt][jc];
+                    fma_row<T, TAPS>(acc, coef, w0s[pt]);
                 }
             }
+            // FP32C carries the FP32 sums into fixed point every kCarry batches and at the chunk end
+            const bool carry = FIXED && ((++bcount % kCarry) == 0 || base + B >= w.start + w.count);
+            if (carry && owner && cur >= 0) flush(cur, acc);
             __syncthreads();
-        }
-
-        if (owner) {
-            const int b0 = tc[0] * TE - (M - 1);
-            int p1 = tc[1] * TE - (M - 1) + cb;
-            if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                if (half == 1 && !has1) break;
-                int p2 = tc[2] * TE - (M - 1) + c0 + half;
-                if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-                const bool ok12 = p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2];
-#pragma unroll
-                for (int q = 0; q < PA; ++q) {
-                    int p0 = b0 + q;
-                    if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-                    const bool ok = ok12 && p0 >= 0 && p0 < a.L[0];
-                    const int64_t idx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
-                    if (FIXED) {
-                        long long &slot = iacc[(q * 2 + half) * NT + tid];
-                        if (ok && slot != 0)
-                            atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + idx, (unsigned long long)slot);
-                        slot = 0;
-                    } else {
-                        const T v = half == 0 ? acc0[q] : acc1[q];
-                        if (ok && v != T(0)) atomicAdd(reinterpret_cast<T *>(a.grid) + idx, v);
+            if (carry) {
+                // FP32C: carry the FP32 tile into fixed point and clear it
+                for (int e = tid; e < PA3; e += NT) {
+                    const T v = tile[e];
+                    if (v != T(0)) {
+                        itile[e] += (unsigned long long)to_fixed(v * fscale);
+                        tile[e] = T(0);
                     }
+                }
+                __syncthreads();
+            }
+        }
+        if (owner && cur >= 0 && !FIXED) flush(cur, acc);
+        __syncthreads();
+
+        // tile -> global grid (c fastest, matching the grid's x2 axis), then clear it
+        for (int e = tid; e < PA3; e += NT) {
+            const int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
+            int p0 = tc[0] * TE - (M - 1) + q0;
+            int p1 = tc[1] * TE - (M - 1) + q1;
+            int p2 = tc[2] * TE - (M - 1) + q2;
+            if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+            if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+            if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+            const bool ok = p0 >= 0 && p0 < a.L[0] && p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2];
+            const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+            if (FIXED) {
+                const unsigned long long val = itile[e];
+                if (val != 0ull) {
+                    itile[e] = 0ull;
+                    if (ok) atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx, val);
+                }
+            } else {
+                const T val = tile[e];
+                if (val != T(0)) {
+                    tile[e] = T(0);
+                    if (ok) atomicAdd(reinterpret_cast<T *>(a.grid) + gidx, val);
                 }
             }
         }
+        __syncthreads();
     }
 }
 
 template <typename T, int M, int TE, bool FIXED>
 static cudaError_t launch_cols(Plan &P, const Spread3Args &a) {
-    using G = ColGeom<M, TE>;
-    auto kern = spread3_columns<T, M, TE, FIXED>;
-    const int smem = FIXED ? G::PA * 2 * G::NT * (int)sizeof(long long) : 0;
+    using G = CellGeom<M, TE>;
+    auto kern = spread3_cells<T, M, TE, FIXED>;
+    const int pa3 = G::PA * G::PA * G::PA;
+    const int smem = ((pa3 * (int)sizeof(T) + 15) / 16) * 16 + (FIXED ? pa3 * 8 : 0);
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem));

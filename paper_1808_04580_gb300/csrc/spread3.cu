@@ -4,8 +4,9 @@
 // The plan sorts the nodes of every tile by cell, so the nodes of one cell
 // are contiguous; they share the whole (2M)^3 support.  A CTA takes one chunk
 // of one tile (TE^3 cells) and keeps the tile plus halo (PA = TE + 2M - 1 per
-// axis) in shared memory.  Thread (jb, jc) owns one support-relative column of
-// the current cell and 2M registers along axis 0; each node adds
+// axis) in shared memory.  One or two thread groups take alternate nodes; in
+// each, thread (jb, jc) owns one support-relative column of its current cell
+// and 2M registers along axis 0; each node adds
 // coef * w0[ja], coef = x~ w1[jb] w2[jc], for ja = 0..2M-1: every fused
 // multiply-add lands in the support, with no range tests.  When the cell
 // changes (and before every fixed-point carry for FP32C) each thread adds
@@ -16,8 +17,8 @@
 // FP32C: the shared FP32 tile only ever holds the sums of 8 batches (256
 // nodes); then it is carried into a 64-bit fixed-point tile (scale 2^k from
 // sum |x~|, so no partial sum can overflow).  Everything after that is
-// exact integer addition, so the result does not depend on the order of the
-// atomics.
+// exact integer addition; only the order in which the FP32 partial sums of a
+// carry interval meet in the shared tile varies from run to run.
 #include <type_traits>
 
 #include "device.cuh"
@@ -122,19 +123,23 @@ __device__ __forceinline__ long long to_fixed(double v) { return __double2ll_rn(
 
 constexpr int kCarry = 8;   // FP32C: batches (of 32 nodes) per fixed-point carry
 
-template <int M, int TE>
+// GROUPS thread groups per CTA take alternate nodes: two for FP32C, whose
+// larger shared footprint (FP32 + int64 tiles) leaves fewer CTAs per SM.
+template <int M, int TE, int GROUPS_>
 struct CellGeom {
     static constexpr int PA = TE + 2 * M - 1;     // tile + halo per axis
     static constexpr int TAPS = 2 * M;
     static constexpr int TAPS4 = (TAPS + 3) / 4 * 4;
-    static constexpr int OWN = TAPS * TAPS;       // threads owning a support column (jb, jc)
-    static constexpr int NT = (OWN + 31) / 32 * 32;
-    static constexpr int B = 32;                  // nodes staged per batch
+    static constexpr int OWN = TAPS * TAPS;       // threads of a group owning a support column (jb, jc)
+    static constexpr int NTG = (OWN + 31) / 32 * 32;
+    static constexpr int GROUPS = GROUPS_;
+    static constexpr int NT = GROUPS * NTG;
+    static constexpr int B = 32 * GROUPS;         // nodes staged per batch
 };
 
 template <typename T, int M, int TE, bool FIXED>
-__global__ void __launch_bounds__(CellGeom<M, TE>::NT) spread3_cells(Spread3Args a) {
-    using G = CellGeom<M, TE>;
+__global__ void __launch_bounds__(CellGeom<M, TE, FIXED ? 2 : 1>::NT) spread3_cells(Spread3Args a) {
+    using G = CellGeom<M, TE, FIXED ? 2 : 1>;
     constexpr int PA = G::PA, PA3 = PA * PA * PA, TAPS = G::TAPS, TAPS4 = G::TAPS4, B = G::B, NT = G::NT;
     using Pt = typename PointOf<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -147,9 +152,10 @@ __global__ void __launch_bounds__(CellGeom<M, TE>::NT) spread3_cells(Spread3Args
     __shared__ int org[B];                                // tile-local base cell, 8 bits per axis
 
     const int tid = threadIdx.x;
-    const bool owner = tid < G::OWN;
-    const int jb = owner ? tid / TAPS : 0;
-    const int jc = owner ? tid % TAPS : 0;
+    const int grp = tid / G::NTG, gtid = tid - grp * G::NTG;
+    const bool owner = gtid < G::OWN;
+    const int jb = owner ? gtid / TAPS : 0;
+    const int jc = owner ? gtid % TAPS : 0;
     const T tm = T(M), tb = T(a.b), tden = T(a.inv_den);
     const Pt *pts = reinterpret_cast<const Pt *>(a.pts);
     T fscale = T(1);
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(CellGeom<M, TE>::NT) spread3_cells(Spread3Args
             }
             __syncthreads();
             if (owner) {
-                for (int pt = 0; pt < nb; ++pt) {
+                for (int pt = grp; pt < nb; pt += G::GROUPS) {
                     const int o = org[pt];
                     if (o != cur) {
                         if (cur >= 0) flush(cur, acc);
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(CellGeom<M, TE>::NT) spread3_cells(Spread3Args
 
 template <typename T, int M, int TE, bool FIXED>
 static cudaError_t launch_cols(Plan &P, const Spread3Args &a) {
-    using G = CellGeom<M, TE>;
+    using G = CellGeom<M, TE, FIXED ? 2 : 1>;
     auto kern = spread3_cells<T, M, TE, FIXED>;
     const int pa3 = G::PA * G::PA * G::PA;
     const int smem = ((pa3 * (int)sizeof(T) + 15) / 16) * 16 + (FIXED ? pa3 * 8 : 0);

@@ -2,9 +2,9 @@
 
 nfl_apply_batched issues every plan's products on one stream without host
 synchronization; captured into a CUDA graph, the whole batch replays as a
-single launch.  FP32C products are deterministic (exact fixed-point
-spreading, fixed reduction order), so batched, per-plan and replayed results
-must agree exactly; one graph is also checked against the oracle's Alg. 2.
+single launch.  Batched, per-plan and replayed FP32C results agree to the
+FP32C budget (the order in which FP32 partial sums meet in shared memory is
+not fixed); one graph is also checked against the oracle's Alg. 2.
 """
 import numpy as np
 import pytest
@@ -28,9 +28,13 @@ def test_batched_equals_per_plan_and_graph_replay():
     xs = [gpu(workloads.rhs(n, nrhs=8, seed=40 + g)) for g, n in enumerate(sizes)]
     ys = apply_batched(plans, xs, "Ls")
     torch.cuda.synchronize()
+    def close(a, b):
+        # L_s x = x - A x: compare the A x parts, which x would otherwise hide
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) < 1e-6
+
     for plan, x, y in zip(plans, xs, ys):
         ref = plan.apply_Ls(x)
-        assert torch.equal(ref, y)
+        assert close(x - y, x - ref)
         assert plan.info()["device_error"] == 0
 
     outs = [torch.empty((8, n), dtype=torch.float64, device=DEV) for n in sizes]
@@ -43,8 +47,8 @@ def test_batched_equals_per_plan_and_graph_replay():
         o.zero_()
     graph.replay()
     torch.cuda.synchronize()
-    for o, y in zip(outs, ys):
-        assert torch.equal(o.t(), y)
+    for o, x, y in zip(outs, xs, ys):
+        assert close(x - o.t(), x - y)
 
     # one member against the oracle's Alg. 2 (FP32C tolerance)
     v, x = clouds[0], xs[0][:, 3].cpu().numpy()

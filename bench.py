@@ -149,9 +149,9 @@ def source_sha(path):
     return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
 
 
-def profiled_traffic(kernel_file):
+def profiled_traffic(summary, kernel_file):
     """dram bytes per launch from the committed ncu summary, if it matches the current source."""
-    summ = os.path.join(ROOT, "profiles", "spread3_columns_ball10M.md")
+    summ = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(summ):
         return None
     vals = {}
@@ -269,12 +269,13 @@ def main():
     flops = 2.0 * taps * n
     achieved = flops / (dom_ms / 1000.0) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    kernel_file = os.path.join(ROOT, "paper_1808_04580_gb300", "csrc",
-                               "spread3.cu" if dom == "spread" else "gather.cu")
-    traffic = profiled_traffic(kernel_file) if dom == "spread" else None
+    kname, src, summary = (("spread3_cells", "spread3.cu", "spread3_cells_ball10M.md") if dom == "spread"
+                           else ("gather3_tc", "gather_tc.cu", "gather3_tc_ball10M.md"))
+    kernel_file = os.path.join(ROOT, "paper_1808_04580_gb300", "csrc", src)
+    traffic = profiled_traffic(summary, kernel_file) if n == 10_000_000 else None
     hbm_bytes = n * (16 + 8 + 4 + 8)  # node record, x, perm, dinv read once per column
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "spread3_columns" if dom == "spread" else "gather_kernel",
+                "traffic": traffic, "kernel": kname,
                 "flops_per_launch": flops, "ms_per_launch": dom_ms,
                 "hbm_achieved_gbs": hbm_bytes / (dom_ms / 1000.0) / 1e9,
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no measured FP32 peak)"}

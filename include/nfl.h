@@ -57,9 +57,12 @@ enum { NFL_KERNEL_GAUSSIAN = 0 };
  * D^{-1/2} scaling, x - A x) and all solver scalars are FP64 in every mode.
  *   FP64  : everything in FP64.
  *   FP32  : window weights, spreading grid, FFT and interpolation in FP32.
- *   FP32C : FP32 window weights and products; spreading sums are carried
- *           into 64-bit fixed point every 32 nodes and accumulated exactly;
- *           FFT and interpolation in FP32.                                  */
+ *   FP32C : FP32 window weights and products; FP32 partial sums over at
+ *           most 256 nodes are carried into 64-bit fixed point and
+ *           accumulated exactly from there on; FFT in FP32; interpolation
+ *           on the tensor cores with FP32-accurate (three-term TF32) products.
+ *           Results vary in the last FP32 bits from run to run (the order
+ *           in which the partial sums meet is not fixed).                   */
 enum { NFL_PREC_FP64 = 0, NFL_PREC_FP32 = 1, NFL_PREC_FP32C = 2 };
 
 typedef struct {

@@ -6,7 +6,8 @@ namespace nfl {
 
 int kernels_per_column(const Plan &P) {
     const int passes = P.d == 1 ? 1 : (P.d == 2 ? 3 : 5);
-    return (P.prec == NFL_PREC_FP32C ? 1 : 0) + 1 + passes + 1;
+    const bool staged = P.d == 3 && column_tile_edge(P.m) == P.tile_edge;
+    return (staged || P.prec == NFL_PREC_FP32C ? 1 : 0) + 1 + passes + 1;
 }
 
 static cudaError_t mark(Plan &P, int stage) {

@@ -33,6 +33,7 @@ struct WorkItem {
 };
 
 constexpr int kMaxM = 12;
+constexpr int kPolyCoef = 10;   // window polynomial degree 9
 
 struct Plan {
     // problem
@@ -60,6 +61,7 @@ struct Plan {
     void *pts = nullptr;        // PointF or PointD
     int32_t *perm = nullptr;    // sorted position -> input index
     double *dinv_sorted = nullptr;  // D_E^{-1/2} in sorted order
+    void *xsort = nullptr;      // x~ of the current column in sorted order (spread type; 3-D cell kernels)
     double *degree = nullptr;   // d_E in input order
     double min_deg = 0, max_deg = 0;
     bool degree_ok = false;
@@ -67,6 +69,10 @@ struct Plan {
     // window phi(delta)/phi(0) = (m / s) sinh(b s) / sinh(b m), s = sqrt(m^2 - delta^2);
     // kb_inv_sinh_bm holds 1 / (1 - e^{-2 b m}) for the cancellation-free form
     double kb_b = 0, kb_inv_sinh_bm = 0;
+    // FP32 window by taps: for tap j of a node at fractional offset f in [0, 1),
+    // phi(f + m - 1 - j) / phi(0) = sum_k kb_poly[j][k] t^k, t = 2 f - 1, to
+    // within FP32 rounding of the peak (Chebyshev interpolation in FP64).
+    float kb_poly[2 * kMaxM][kPolyCoef] = {};
 
     // FFT data
     int K[3] = {1, 1, 1};       // kept frequencies per axis (R2C axis N/2+1, others N+1)
@@ -103,6 +109,7 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y);
 // 3-D atomic-free spreading (spread3.cu): tile edge it needs for cut-off m (0: not available)
 int column_tile_edge(int m);
 cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool scale_dinv);
+cudaError_t stage_spread3_values(Plan &P, const double *x, bool ones, bool scale_dinv);
 
 // 3-D interpolation on the tensor cores (gather_tc.cu)
 bool gather_tc_available(const Plan &P);

@@ -454,6 +454,7 @@ static void free_plan(Plan *P) {
     cudaFree(P->pts);
     cudaFree(P->perm);
     cudaFree(P->dinv_sorted);
+    cudaFree(P->xsort);
     cudaFree(P->degree);
     cudaFree(P->grid);
     cudaFree(P->bufA);
@@ -466,6 +467,52 @@ static void free_plan(Plan *P) {
     delete P;
 }
 
+// phi(delta) / phi(0) for the normalized Kaiser-Bessel window, in FP64 on the host.
+static double host_window(double delta, double m, double b, double inv_den) {
+    const double s2 = std::max(m * m - delta * delta, 0.0);
+    const double s = std::sqrt(s2);
+    const double head = std::exp(-b * delta * delta / (s + m));
+    const double tail = s > 0.0 ? -std::expm1(-2.0 * b * s) / s : 2.0 * b;
+    return head * m * tail * inv_den;
+}
+
+// Per-tap polynomials of the window for the FP32 kernels: tap j of a node at
+// fractional offset f sees phi(f + m - 1 - j); on f in [0, 1) this is
+// interpolated at the kPolyCoef Chebyshev points of t = 2 f - 1 and the
+// Chebyshev series is re-expanded in powers of t.  The window is an entire
+// function of delta, so degree 9 reaches FP32 rounding of the peak for
+// every m here (about 7e-8 of phi(0), measured on a dense grid of f).
+static void window_poly(Plan &P) {
+    constexpr int NC = kPolyCoef;
+    const double m = P.m;
+    for (int j = 0; j < 2 * P.m && j < 2 * kMaxM; ++j) {
+        double fv[NC], c[NC], mono[NC] = {0}, tkm1[NC] = {0}, tk[NC] = {0}, tn[NC];
+        for (int i = 0; i < NC; ++i) {
+            const double t = std::cos(M_PI * (i + 0.5) / NC);
+            fv[i] = host_window(0.5 * (t + 1.0) + m - 1.0 - j, m, P.kb_b, P.kb_inv_sinh_bm);
+        }
+        for (int k = 0; k < NC; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < NC; ++i) acc += fv[i] * std::cos(M_PI * k * (i + 0.5) / NC);
+            c[k] = (k == 0 ? 1.0 : 2.0) * acc / NC;
+        }
+        // sum_k c_k T_k(t) with T_0 = 1, T_1 = t, T_{k+1} = 2 t T_k - T_{k-1}
+        tkm1[0] = 1.0;
+        tk[1] = 1.0;
+        mono[0] = c[0];
+        for (int q = 0; q < NC; ++q) mono[q] += c[1] * tk[q];
+        for (int k = 2; k < NC; ++k) {
+            for (int q = 0; q < NC; ++q) tn[q] = (q > 0 ? 2.0 * tk[q - 1] : 0.0) - tkm1[q];
+            for (int q = 0; q < NC; ++q) {
+                tkm1[q] = tk[q];
+                tk[q] = tn[q];
+                mono[q] += c[k] * tn[q];
+            }
+        }
+        for (int q = 0; q < NC; ++q) P.kb_poly[j][q] = static_cast<float>(mono[q]);
+    }
+}
+
 static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sigma, int N, int m, int p,
                                    double eps_B, int prec, cudaStream_t stream, Plan *P) {
     P->n = n; P->d = d; P->N = N; P->m = m; P->p = p; P->prec = prec;
@@ -473,6 +520,7 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     P->ngrid = 2 * N;
     P->kb_b = M_PI * (2.0 - 1.0 / 2.0);
     P->kb_inv_sinh_bm = 1.0 / -std::expm1(-2.0 * P->kb_b * m);   // 1 / (1 - e^{-2 b m})
+    window_poly(*P);
     int dev = 0;
     NFL_STATUS_TRY(cudaGetDevice(&dev));
     NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -566,7 +614,7 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     const bool dbl = points_are_double(prec);
     if (cudaMalloc(&P->pts, n * (dbl ? sizeof(PointD) : sizeof(PointF))) != cudaSuccess ||
         cudaMalloc(&P->perm, n * 4) != cudaSuccess || cudaMalloc(&P->dinv_sorted, n * 8) != cudaSuccess ||
-        cudaMalloc(&P->degree, n * 8) != cudaSuccess) {
+        cudaMalloc(&P->degree, n * 8) != cudaSuccess || cudaMalloc(&P->xsort, n * 8) != cudaSuccess) {
         cleanup();
         return NFL_ERR_OUT_OF_MEMORY;
     }

@@ -1,24 +1,33 @@
 // Window spreading in 3-D (Alg. 1 step 1, the window half of the adjoint NFFT):
 //   h_t = sum_i x~_i phi(n v~_i0 - t_0) phi(n v~_i1 - t_1) phi(n v~_i2 - t_2).
 //
+// A first kernel writes x~ = D_E^{-1/2} x (Alg. 2 step 5) in the plan's
+// tile-sorted node order, so the spread reads node records and values with
+// coalesced loads, one batch ahead of use.
+//
 // The plan sorts the nodes of every tile by cell, so the nodes of one cell
 // are contiguous; they share the whole (2M)^3 support.  A CTA takes one chunk
 // of one tile (TE^3 cells) and keeps the tile plus halo (PA = TE + 2M - 1 per
-// axis) in shared memory.  One or two thread groups take alternate nodes; in
-// each, thread (jb, jc) owns one support-relative column of its current cell
-// and 2M registers along axis 0; each node adds
-// coef * w0[ja], coef = x~ w1[jb] w2[jc], for ja = 0..2M-1: every fused
-// multiply-add lands in the support, with no range tests.  When the cell
-// changes (and before every fixed-point carry for FP32C) each thread adds
-// its 2M values to the shared tile with shared-memory atomics (supports of
-// neighbouring cells overlap); at the end of the chunk the non-zero tile
-// cells go to the global grid with one atomic each.
+// axis) in shared memory, one copy per thread group.  Nodes are staged in
+// batches of 32 per group; group g takes the g-th slice of 32 consecutive
+// nodes, whose cell runs the staging warp marks in a bit mask.  In a group,
+// thread (jb, jc) owns one support-relative column of the current cell and
+// 2M registers along axis 0; each node of a run adds coef * w0[ja],
+// coef = x~ w1[jb] w2[jc], for ja = 0..2M-1 (FP32: two lanes per
+// fma.rn.f32x2).  Every multiply-add lands in the support, with no range
+// tests.  When the cell changes, the group meets at a named barrier and each
+// thread adds its 2M values to the group's tile with plain read-modify-write:
+// in one flush the threads of a group touch distinct positions, and the
+// barrier orders flushes of different cells.  At the end of the chunk the
+// non-zero tile cells go to the global grid with one atomic each.
 //
-// FP32C: the shared FP32 tile only ever holds the sums of 8 batches (256
-// nodes); then it is carried into a 64-bit fixed-point tile (scale 2^k from
-// sum |x~|, so no partial sum can overflow).  Everything after that is
-// exact integer addition; only the order in which the FP32 partial sums of a
-// carry interval meet in the shared tile varies from run to run.
+// FP32 window weights come from the plan's per-tap polynomials (Horner in
+// t = 2f - 1, two taps per fma.rn.f32x2); FP64 evaluates the window itself.
+//
+// FP32C: each group's FP32 tile only ever holds the sums of 8 slices (256 of
+// its nodes); then both tiles are carried into a 64-bit fixed-point tile
+// (scale 2^k from sum |x~|, so no partial sum can overflow).  Everything
+// after that is exact integer addition.
 #include <type_traits>
 
 #include "device.cuh"
@@ -28,9 +37,7 @@ namespace nfl {
 
 struct Spread3Args {
     const void *pts;
-    const int32_t *perm;
-    const double *x;
-    const double *dinv;
+    const void *xs;                 // x~ in sorted order (spread type)
     const WorkItem *items;
     int64_t nitems;
     int ntile[3];
@@ -39,9 +46,32 @@ struct Spread3Args {
     int ngrid;
     void *grid;
     const double *abs_sum;
-    int ones;
     double b, inv_den;
+    float poly[2 * kMaxM][kPolyCoef];
 };
+
+// x~_k = x[perm[k]] * dinv[k] (or dinv[k] / 1 for the all-ones vector) in sorted
+// order; with abs_sum, also sum_k |x~_k| (the fixed-point scale of FP32C).
+template <typename T>
+__global__ void __launch_bounds__(256) stage_values(const double *x, const int32_t *perm, const double *dinv,
+                                                    int64_t n, int ones, T *out, double *abs_sum) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double v = ones ? 1.0 : x[perm[k]];
+        if (dinv) v *= dinv[k];
+        out[k] = T(v);
+        acc += fabs(v);
+    }
+    if (!abs_sum) return;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(abs_sum, red[0]);
+}
 
 __device__ __forceinline__ double fixed_scale_of(double abs_sum) {
     if (!(abs_sum > 0.0)) return 1.0;
@@ -52,60 +82,25 @@ __device__ __forceinline__ double fixed_scale_of(double abs_sum) {
     return ldexp(1.0, k);
 }
 
-// acc[q] += coef * row[q], q < PA, with 16-byte shared loads of the row.
-template <typename T, int PA>
-__device__ __forceinline__ void fma_row(T *acc, T coef, const T *row) {
-    if (sizeof(T) == 4) {
-        const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-        for (int q = 0; q < (PA + 3) / 4; ++q) {
-            const float4 w = r4[q];
-            if (4 * q + 0 < PA) acc[4 * q + 0] += coef * T(w.x);
-            if (4 * q + 1 < PA) acc[4 * q + 1] += coef * T(w.y);
-            if (4 * q + 2 < PA) acc[4 * q + 2] += coef * T(w.z);
-            if (4 * q + 3 < PA) acc[4 * q + 3] += coef * T(w.w);
-        }
-    } else {
-        const double2 *r2 = reinterpret_cast<const double2 *>(row);
-#pragma unroll
-        for (int q = 0; q < (PA + 1) / 2; ++q) {
-            const double2 w = r2[q];
-            if (2 * q + 0 < PA) acc[2 * q + 0] += coef * T(w.x);
-            if (2 * q + 1 < PA) acc[2 * q + 1] += coef * T(w.y);
-        }
-    }
+// Two FP32 lanes in one 64-bit register: lane 0 in the low half.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lane_of(unsigned long long v, int hi) {
+    return __uint_as_float(static_cast<unsigned>(hi ? (v >> 32) : v));
+}
+// a * b + c on both lanes.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
-// acc0[q] += k0 * row[q], acc1[q] += k1 * row[q]: one pass over the row for two columns.
-template <typename T, int PA>
-__device__ __forceinline__ void fma_row2(T *acc0, T *acc1, T k0, T k1, const T *row) {
-    if (sizeof(T) == 4) {
-        const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-        for (int q = 0; q < (PA + 3) / 4; ++q) {
-            const float4 w = r4[q];
-            const T v[4] = {T(w.x), T(w.y), T(w.z), T(w.w)};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (4 * q + u < PA) {
-                    acc0[4 * q + u] += k0 * v[u];
-                    acc1[4 * q + u] += k1 * v[u];
-                }
-        }
-    } else {
-        const double2 *r2 = reinterpret_cast<const double2 *>(row);
-#pragma unroll
-        for (int q = 0; q < (PA + 1) / 2; ++q) {
-            const double2 w = r2[q];
-            const T v[2] = {T(w.x), T(w.y)};
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-                if (2 * q + u < PA) {
-                    acc0[2 * q + u] += k0 * v[u];
-                    acc1[2 * q + u] += k1 * v[u];
-                }
-        }
-    }
+__device__ __forceinline__ void group_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // FP32 value (already scaled by 2^k, |v| < 2^62) -> nearest int64 with 32-bit
@@ -121,127 +116,240 @@ __device__ __forceinline__ long long to_fixed(float v) {
 }
 __device__ __forceinline__ long long to_fixed(double v) { return __double2ll_rn(v); }
 
-constexpr int kCarry = 8;   // FP32C: batches (of 32 nodes) per fixed-point carry
+constexpr int kCarry = 8;   // FP32C: slices (of 32 nodes per group) per fixed-point carry
 
-// GROUPS thread groups per CTA take alternate nodes: two for FP32C, whose
-// larger shared footprint (FP32 + int64 tiles) leaves fewer CTAs per SM.
-template <int M, int TE, int GROUPS_>
+template <int M, int TE>
 struct CellGeom {
     static constexpr int PA = TE + 2 * M - 1;     // tile + halo per axis
+    static constexpr int PA3 = PA * PA * PA;
     static constexpr int TAPS = 2 * M;
     static constexpr int TAPS4 = (TAPS + 3) / 4 * 4;
+    static constexpr int PAIRS = TAPS / 2;
     static constexpr int OWN = TAPS * TAPS;       // threads of a group owning a support column (jb, jc)
     static constexpr int NTG = (OWN + 31) / 32 * 32;
-    static constexpr int GROUPS = GROUPS_;
+    static constexpr int GROUPS = 2;
     static constexpr int NT = GROUPS * NTG;
-    static constexpr int B = 32 * GROUPS;         // nodes staged per batch
+    static constexpr int S = 32;                  // nodes per group per batch (one staging warp)
+    static constexpr int B = S * GROUPS;          // nodes staged per batch
+};
+
+// CTAs per SM that shared memory admits (at most 3, and no fewer than 64
+// registers per thread): the register budget is set to match, so registers
+// do not limit occupancy below shared memory.
+template <typename T, int M, int TE, bool FIXED>
+constexpr int cells_min_blocks() {
+    using G = CellGeom<M, TE>;
+    constexpr int dyn = G::GROUPS * ((G::PA3 * (int)sizeof(T) + 15) / 16) * 16 + (FIXED ? G::PA3 * 8 : 0);
+    constexpr int stat = G::B * (G::TAPS4 + 2 * G::TAPS + 4) * (int)sizeof(T) + G::B * 4 + G::PAIRS * kPolyCoef * 8 + 64;
+    constexpr int by_smem = 232448 / (dyn + stat + 1024);
+    constexpr int by_threads = 65536 / (G::NT * 64);    // keep 64 registers per thread
+    constexpr int b = by_smem < by_threads ? by_smem : by_threads;
+    return b < 1 ? 1 : (b > 3 ? 3 : b);
+}
+
+// Register accumulator of one support column: 2M values along axis 0.
+template <typename T, int TAPS> struct ColumnAcc {
+    T v[TAPS];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int q = 0; q < TAPS; ++q) v[q] = T(0);
+    }
+    __device__ __forceinline__ void add(T coef, const T *row) {
+        const double2 *r2 = reinterpret_cast<const double2 *>(row);
+#pragma unroll
+        for (int q = 0; q < TAPS / 2; ++q) {
+            const double2 w = r2[q];
+            v[2 * q] += coef * w.x;
+            v[2 * q + 1] += coef * w.y;
+        }
+    }
+    __device__ __forceinline__ T get(int q) const { return v[q]; }
+};
+template <int TAPS> struct ColumnAcc<float, TAPS> {
+    unsigned long long v[TAPS / 2];               // taps (2q, 2q + 1)
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int q = 0; q < TAPS / 2; ++q) v[q] = 0ull;
+    }
+    __device__ __forceinline__ void add(float coef, const float *row) {
+        const ulonglong2 *r = reinterpret_cast<const ulonglong2 *>(row);
+        const unsigned long long c2 = pack2(coef, coef);
+#pragma unroll
+        for (int q = 0; q < (TAPS + 3) / 4; ++q) {
+            const ulonglong2 w = r[q];
+            v[2 * q] = ffma2(c2, w.x, v[2 * q]);
+            if (2 * q + 1 < TAPS / 2) v[2 * q + 1] = ffma2(c2, w.y, v[2 * q + 1]);
+        }
+    }
+    __device__ __forceinline__ float get(int q) const { return lane_of(v[q >> 1], q & 1); }
 };
 
 template <typename T, int M, int TE, bool FIXED>
-__global__ void __launch_bounds__(CellGeom<M, TE, FIXED ? 2 : 1>::NT) spread3_cells(Spread3Args a) {
-    using G = CellGeom<M, TE, FIXED ? 2 : 1>;
-    constexpr int PA = G::PA, PA3 = PA * PA * PA, TAPS = G::TAPS, TAPS4 = G::TAPS4, B = G::B, NT = G::NT;
+__global__ void __launch_bounds__(CellGeom<M, TE>::NT, (cells_min_blocks<T, M, TE, FIXED>()))
+    spread3_cells(Spread3Args a) {
+    using G = CellGeom<M, TE>;
+    constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, TAPS4 = G::TAPS4, S = G::S, B = G::B, NT = G::NT;
+    constexpr int TILE_STRIDE = ((PA3 * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T);
     using Pt = typename PointOf<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw);                                        // PA^3, [a][b][c]
-    unsigned long long *itile = reinterpret_cast<unsigned long long *>(smem_raw + ((PA3 * sizeof(T) + 15) / 16) * 16);
+    T *tiles = reinterpret_cast<T *>(smem_raw);                                       // GROUPS x PA^3, [a][b][c]
+    unsigned long long *itile =
+        reinterpret_cast<unsigned long long *>(smem_raw + G::GROUPS * TILE_STRIDE * sizeof(T));
     __shared__ __align__(16) T w0s[B][TAPS4];
     __shared__ T w1s[B][TAPS], w2s[B][TAPS];
     __shared__ T frs[B][3];
     __shared__ T xs[B];
     __shared__ int org[B];                                // tile-local base cell, 8 bits per axis
+    __shared__ unsigned runs[G::GROUPS];                  // bit i: slice node i starts a cell run
+    __shared__ __align__(16) float2 polys[G::PAIRS][kPolyCoef];   // (tap 2q, tap 2q+1) coefficients
 
     const int tid = threadIdx.x;
     const int grp = tid / G::NTG, gtid = tid - grp * G::NTG;
     const bool owner = gtid < G::OWN;
     const int jb = owner ? gtid / TAPS : 0;
     const int jc = owner ? gtid % TAPS : 0;
-    const T tm = T(M), tb = T(a.b), tden = T(a.inv_den);
+    T *tile = tiles + grp * TILE_STRIDE;
     const Pt *pts = reinterpret_cast<const Pt *>(a.pts);
+    const T *xsrc = reinterpret_cast<const T *>(a.xs);
     T fscale = T(1);
     if (FIXED) fscale = T(fixed_scale_of(*a.abs_sum));
-    for (int e = tid; e < PA3; e += NT) {
-        tile[e] = T(0);
-        if (FIXED) itile[e] = 0ull;
+    for (int e = tid; e < G::GROUPS * TILE_STRIDE; e += NT) tiles[e] = T(0);
+    if (FIXED)
+        for (int e = tid; e < PA3; e += NT) itile[e] = 0ull;
+    for (int e = tid; e < G::PAIRS * kPolyCoef; e += NT) {
+        const int q = e / kPolyCoef, k = e - q * kPolyCoef;
+        polys[q][k] = make_float2(a.poly[2 * q][k], a.poly[2 * q + 1][k]);
     }
 
-    // add this thread's 2M values along a for the support column (jb, jc) of cell o
-    auto flush = [&](int o, T *acc) {
-        const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
-        T *col = tile + (s0 * PA + s1 + jb) * PA + s2 + jc;
+    ColumnAcc<T, TAPS> acc;
+    // group barrier, then add this thread's 2M values of cell o to the group's tile
+    auto flush = [&](int o) {
+        group_barrier(1 + grp, G::NTG);
+        if (owner) {
+            const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
+            T *col = tile + (s0 * PA + s1 + jb) * PA + s2 + jc;
 #pragma unroll
-        for (int ja = 0; ja < TAPS; ++ja) {
-            if (acc[ja] != T(0)) atomicAdd(col + ja * PA * PA, acc[ja]);
-            acc[ja] = T(0);
+            for (int ja = 0; ja < TAPS; ++ja) col[ja * PA * PA] += acc.get(ja);
         }
+        acc.clear();
     };
 
     for (int64_t it = blockIdx.x; it < a.nitems; it += gridDim.x) {
         const WorkItem w = a.items[it];
+        const int wend = w.start + w.count;
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
-        T acc[TAPS];
-#pragma unroll
-        for (int q = 0; q < TAPS; ++q) acc[q] = T(0);
+        acc.clear();
         int cur = -1;
         int bcount = 0;
+        // node record and value of this thread's slot, one batch ahead
+        Pt pn;
+        T xn = T(0);
+        if (tid < B && w.start + tid < wend) {
+            pn = pts[w.start + tid];
+            xn = xsrc[w.start + tid];
+        }
 
-        for (int base = w.start; base < w.start + w.count; base += B) {
-            const int nb = min(B, w.start + w.count - base);
-            if (tid < nb) {
-                const int k = base + tid;
-                const Pt p = pts[k];
-                double xv = a.ones ? 1.0 : a.x[a.perm[k]];
-                if (a.dinv) xv *= a.dinv[k];
-                xs[tid] = T(xv);
-                int o = 0;
+        for (int base = w.start; base < wend; base += B) {
+            const int nb = min(B, wend - base);
+            if (tid < B) {                                // warps 0 .. GROUPS-1: one slice each
+                const bool valid = tid < nb;
+                int o = -1;
+                if (valid) {
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    o |= (cell_axis(p.cell, ax) - tc[ax] * TE) << (8 * ax);
-                    frs[tid][ax] = T(p.f[ax]);
+                    for (int ax = 0; ax < 3; ++ax) {
+                        o = (ax == 0 ? 0 : o) | ((cell_axis(pn.cell, ax) - tc[ax] * TE) << (8 * ax));
+                        frs[tid][ax] = T(pn.f[ax]);
+                    }
+                    xs[tid] = xn;
+                    org[tid] = o;
                 }
-                org[tid] = o;
+                const int lane = tid & 31;
+                const int prev = __shfl_up_sync(0xffffffffu, o, 1);
+                const unsigned m = __ballot_sync(0xffffffffu, valid && (lane == 0 || o != prev));
+                if (lane == 0) runs[tid >> 5] = m;
+                const int kn = base + B + tid;
+                if (kn < wend) {
+                    pn = pts[kn];
+                    xn = xsrc[kn];
+                }
             }
             __syncthreads();
-            for (int e = tid; e < nb * 3 * TAPS; e += NT) {
-                const int pt = e / (3 * TAPS);
-                const int r = e - pt * 3 * TAPS;
-                const int ax = r / TAPS;
-                const int j = r - ax * TAPS;
-                const T wv = kb_weight<T>(frs[pt][ax] + T(M - 1) - T(j), tm, tb, tden);
-                if (ax == 0) w0s[pt][j] = wv;
-                else if (ax == 1) w1s[pt][j] = wv * xs[pt];   // x~ folded into the axis-1 window
-                else w2s[pt][j] = wv;
+            if constexpr (std::is_same<T, float>::value) {
+                // one (axis, node) per item; the lanes of a warp read the same coefficients
+                for (int e = tid; e < 3 * B; e += NT) {
+                    const int ax = e / B, pt = e - ax * B;
+                    if (pt >= nb) continue;
+                    const float t = fmaf(2.f, frs[pt][ax], -1.f);
+                    const unsigned long long t2 = pack2(t, t);
+                    const float sc = ax == 1 ? xs[pt] : 1.f;    // x~ folded into the axis-1 window
+                    float *dst = ax == 0 ? w0s[pt] : (ax == 1 ? w1s[pt] : w2s[pt]);
+                    const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
+#pragma unroll 1
+                    for (int q = 0; q < G::PAIRS; ++q) {
+                        unsigned long long h = pc[q * kPolyCoef + kPolyCoef - 1];
+#pragma unroll
+                        for (int k = kPolyCoef - 2; k >= 0; --k) h = ffma2(h, t2, pc[q * kPolyCoef + k]);
+                        dst[2 * q] = lane_of(h, 0) * sc;
+                        dst[2 * q + 1] = lane_of(h, 1) * sc;
+                    }
+                }
+            } else {
+                const T tm = T(M), tb = T(a.b), tden = T(a.inv_den);
+                for (int e = tid; e < nb * 3 * TAPS; e += NT) {
+                    const int pt = e / (3 * TAPS);
+                    const int r = e - pt * 3 * TAPS;
+                    const int ax = r / TAPS;
+                    const int j = r - ax * TAPS;
+                    const T wv = kb_weight<T>(frs[pt][ax] + T(M - 1) - T(j), tm, tb, tden);
+                    if (ax == 0) w0s[pt][j] = wv;
+                    else if (ax == 1) w1s[pt][j] = wv * xs[pt];
+                    else w2s[pt][j] = wv;
+                }
             }
             __syncthreads();
-            if (owner) {
-                for (int pt = grp; pt < nb; pt += G::GROUPS) {
-                    const int o = org[pt];
+            {
+                // this group's slice, one cell run at a time
+                const unsigned rm = runs[grp];
+                const int s0 = grp * S;
+                const int cnt = max(0, min(S, nb - s0));
+                int i = 0;
+                while (i < cnt) {
+                    const unsigned rest = i + 1 < 32 ? (rm >> (i + 1)) : 0u;
+                    const int j = rest ? min(cnt, i + __ffs(rest)) : cnt;
+                    const int o = org[s0 + i];
                     if (o != cur) {
-                        if (cur >= 0) flush(cur, acc);
+                        if (cur >= 0) flush(cur);
                         cur = o;
                     }
-                    const T coef = w1s[pt][jb] * w2s[pt][jc];
-                    fma_row<T, TAPS>(acc, coef, w0s[pt]);
+                    if (owner) {
+#pragma unroll 2
+                        for (int q = s0 + i; q < s0 + j; ++q) acc.add(w1s[q][jb] * w2s[q][jc], w0s[q]);
+                    }
+                    i = j;
                 }
             }
             // FP32C carries the FP32 sums into fixed point every kCarry batches and at the chunk end
-            const bool carry = FIXED && ((++bcount % kCarry) == 0 || base + B >= w.start + w.count);
-            if (carry && owner && cur >= 0) flush(cur, acc);
+            const bool carry = FIXED && ((++bcount % kCarry) == 0 || base + B >= wend);
+            if (carry && cur >= 0) flush(cur);
             __syncthreads();
             if (carry) {
-                // FP32C: carry the FP32 tile into fixed point and clear it
                 for (int e = tid; e < PA3; e += NT) {
-                    const T v = tile[e];
-                    if (v != T(0)) {
-                        itile[e] += (unsigned long long)to_fixed(v * fscale);
-                        tile[e] = T(0);
+                    long long add = 0;
+#pragma unroll
+                    for (int g = 0; g < G::GROUPS; ++g) {
+                        T &tv = tiles[g * TILE_STRIDE + e];
+                        if (tv != T(0)) {
+                            add += to_fixed(tv * fscale);
+                            tv = T(0);
+                        }
                     }
+                    if (add != 0) itile[e] += (unsigned long long)add;
                 }
                 __syncthreads();
             }
         }
-        if (owner && cur >= 0 && !FIXED) flush(cur, acc);
+        if (!FIXED && cur >= 0) flush(cur);
         __syncthreads();
 
         // tile -> global grid (c fastest, matching the grid's x2 axis), then clear it
@@ -262,11 +370,13 @@ __global__ void __launch_bounds__(CellGeom<M, TE, FIXED ? 2 : 1>::NT) spread3_ce
                     if (ok) atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx, val);
                 }
             } else {
-                const T val = tile[e];
-                if (val != T(0)) {
-                    tile[e] = T(0);
-                    if (ok) atomicAdd(reinterpret_cast<T *>(a.grid) + gidx, val);
+                T val = T(0);
+#pragma unroll
+                for (int g = 0; g < G::GROUPS; ++g) {
+                    val += tiles[g * TILE_STRIDE + e];
+                    tiles[g * TILE_STRIDE + e] = T(0);
                 }
+                if (val != T(0) && ok) atomicAdd(reinterpret_cast<T *>(a.grid) + gidx, val);
             }
         }
         __syncthreads();
@@ -275,10 +385,9 @@ __global__ void __launch_bounds__(CellGeom<M, TE, FIXED ? 2 : 1>::NT) spread3_ce
 
 template <typename T, int M, int TE, bool FIXED>
 static cudaError_t launch_cols(Plan &P, const Spread3Args &a) {
-    using G = CellGeom<M, TE, FIXED ? 2 : 1>;
+    using G = CellGeom<M, TE>;
     auto kern = spread3_cells<T, M, TE, FIXED>;
-    const int pa3 = G::PA * G::PA * G::PA;
-    const int smem = ((pa3 * (int)sizeof(T) + 15) / 16) * 16 + (FIXED ? pa3 * 8 : 0);
+    const int smem = G::GROUPS * ((G::PA3 * (int)sizeof(T) + 15) / 16) * 16 + (FIXED ? G::PA3 * 8 : 0);
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NT, smem));
@@ -313,12 +422,27 @@ static cudaError_t dispatch_cols(Plan &P, const Spread3Args &a) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool scale_dinv) {
+cudaError_t stage_spread3_values(Plan &P, const double *x, bool ones, bool scale_dinv) {
+    const double *dinv = scale_dinv ? P.dinv_sorted : nullptr;
+    double *abs_sum = nullptr;
+    if (P.prec == NFL_PREC_FP32C) {
+        NFL_CUDA_TRY(cudaMemsetAsync(P.scratch, 0, sizeof(double), P.stream));
+        abs_sum = P.scratch;
+    }
+    const int blocks = P.num_sms * 4;
+    if (P.prec == NFL_PREC_FP64)
+        stage_values<double><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
+                                                           static_cast<double *>(P.xsort), abs_sum);
+    else
+        stage_values<float><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
+                                                          static_cast<float *>(P.xsort), abs_sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spread3_columns(Plan &P, const double *, bool, bool) {
     Spread3Args a;
     a.pts = P.pts;
-    a.perm = P.perm;
-    a.x = x;
-    a.dinv = scale_dinv ? P.dinv_sorted : nullptr;
+    a.xs = P.xsort;
     a.items = P.items;
     a.nitems = P.nitems;
     for (int i = 0; i < 3; ++i) {
@@ -329,9 +453,10 @@ cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool sca
     a.ngrid = P.ngrid;
     a.grid = P.grid;
     a.abs_sum = P.scratch;
-    a.ones = ones ? 1 : 0;
     a.b = P.kb_b;
     a.inv_den = P.kb_inv_sinh_bm;
+    for (int j = 0; j < 2 * kMaxM; ++j)
+        for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
     if (P.prec == NFL_PREC_FP64) return dispatch_cols<double, false>(P, a);
     if (P.prec == NFL_PREC_FP32C) return dispatch_cols<float, true>(P, a);
     return dispatch_cols<float, false>(P, a);

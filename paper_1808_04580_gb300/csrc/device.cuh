@@ -43,6 +43,23 @@ __device__ __forceinline__ float kb_weight<float>(float delta, float m, float b,
     return head * m * tail * inv_den;
 }
 
+// Two FP32 lanes in one 64-bit register: lane 0 in the low half.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lane_of(unsigned long long v, int hi) {
+    return __uint_as_float(static_cast<unsigned>(hi ? (v >> 32) : v));
+}
+// a * b + c on both lanes.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 __device__ __forceinline__ int cell_axis(int32_t packed, int a) { return (packed >> (10 * a)) & 1023; }
 __device__ __forceinline__ int cell_axis(int64_t packed, int a) { return (int)((packed >> (10 * a)) & 1023); }
 

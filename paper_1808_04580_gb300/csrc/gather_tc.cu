@@ -47,9 +47,25 @@ struct GatherTCArgs {
     int ngrid;
     const float *g;   // layout [x2][x1][x0]
     int op;
-    float b, inv_den;
     int *error_flag;
+    float poly[2 * kMaxM][kPolyCoef];   // window by taps, as in the plan
 };
+
+// out[q] = tap[q - s] for 0 <= q - s < TAPS, else 0, with s in [0, TE): the
+// node's taps placed at its tile-local cell offset (selects, no indexing).
+template <int TAPS, int PAD, int TE>
+__device__ __forceinline__ void place_taps(const float (&tap)[TAPS], int s, float (&out)[PAD]) {
+#pragma unroll
+    for (int q = 0; q < PAD; ++q) {
+        float v = 0.f;
+#pragma unroll
+        for (int d = 0; d < TE; ++d) {
+            const int j = q - d;
+            if (j >= 0 && j < TAPS) v = (s == d) ? tap[j] : v;
+        }
+        out[q] = v;
+    }
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -98,9 +114,13 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     unsigned char *sB_lo = sB_hi + G::B_BYTES;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
+    __shared__ __align__(16) float2 polys[M][kPolyCoef];   // (tap 2q, tap 2q+1) coefficients
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const float tm = float(M), tb = a.b, tden = a.inv_den;
+    for (int e = tid; e < M * kPolyCoef; e += 128) {
+        const int q = e / kPolyCoef, k = e - q * kPolyCoef;
+        polys[q][k] = make_float2(a.poly[2 * q][k], a.poly[2 * q + 1][k]);
+    }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -151,42 +171,72 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
             const int nb = min(128, w.start + w.count - base);
             const bool live = tid < nb;
             float w1p[PA], w2p[PA];
-            int kq = 0;
+            int kq = 0, iq = 0;
+            double xq = 0.0, dq = 0.0;
             {
                 float f0 = 0.f, f1 = 0.f, f2 = 0.f;
                 int s0 = 0, s1 = 0, s2 = 0;
                 if (live) {
                     kq = base + tid;
                     const PointF p = a.pts[kq];
+                    // epilogue operands, loaded now and used after the contraction
+                    iq = a.perm[kq];
+                    if (a.op != OP_DEGREE) xq = a.x[iq];
+                    if (a.op == OP_A || a.op == OP_LS) dq = a.dinv[kq];
                     s0 = cell_axis(p.cell, 0) - tc[0] * TE;
                     s1 = cell_axis(p.cell, 1) - tc[1] * TE;
                     s2 = cell_axis(p.cell, 2) - tc[2] * TE;
                     f0 = p.f[0]; f1 = p.f[1]; f2 = p.f[2];
                 }
+                // window taps: Horner in t = 2f - 1, two taps per fma.rn.f32x2; axes 1 and 2
+                // first (kept for the contraction), then axis 0 (the A operand)
+                const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
+                {
+                    float tap1[TAPS], tap2[TAPS];
+                    const unsigned long long T1 = pack2(fmaf(2.f, f1, -1.f), fmaf(2.f, f1, -1.f));
+                    const unsigned long long T2 = pack2(fmaf(2.f, f2, -1.f), fmaf(2.f, f2, -1.f));
 #pragma unroll
-                for (int q = 0; q < PA; ++q) {
-                    const int j1 = q - s1, j2 = q - s2;
-                    w1p[q] = (live && (unsigned)j1 < (unsigned)TAPS) ? kb_weight<float>(f1 + float(M - 1 - j1), tm, tb, tden) : 0.f;
-                    w2p[q] = (live && (unsigned)j2 < (unsigned)TAPS) ? kb_weight<float>(f2 + float(M - 1 - j2), tm, tb, tden) : 0.f;
-                }
-                // A operand row tid: axis-0 window, hi/lo TF32 parts, written four values at a time
+                    for (int q = 0; q < M; ++q) {
+                        unsigned long long h1 = pc[q * kPolyCoef + kPolyCoef - 1], h2 = h1;
 #pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    float v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int q = 4 * kb + u, j0 = q - s0;
-                        v[u] = (live && q < PA && (unsigned)j0 < (unsigned)TAPS)
-                                   ? kb_weight<float>(f0 + float(M - 1 - j0), tm, tb, tden) : 0.f;
+                        for (int k = kPolyCoef - 2; k >= 0; --k) {
+                            const unsigned long long c = pc[q * kPolyCoef + k];
+                            h1 = ffma2(h1, T1, c);
+                            h2 = ffma2(h2, T2, c);
+                        }
+                        tap1[2 * q] = lane_of(h1, 0);
+                        tap1[2 * q + 1] = lane_of(h1, 1);
+                        tap2[2 * q] = lane_of(h2, 0);
+                        tap2[2 * q + 1] = lane_of(h2, 1);
                     }
-                    float4 h, l;
-                    h.x = to_tf32(v[0]); l.x = to_tf32(v[0] - h.x);
-                    h.y = to_tf32(v[1]); l.y = to_tf32(v[1] - h.y);
-                    h.z = to_tf32(v[2]); l.z = to_tf32(v[2] - h.z);
-                    h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
-                    const uint32_t off = kmajor_off(tid, 4 * kb);
-                    *reinterpret_cast<float4 *>(sA_hi + off) = h;
-                    *reinterpret_cast<float4 *>(sA_lo + off) = l;
+                    place_taps<TAPS, PA, TE>(tap1, s1, w1p);
+                    place_taps<TAPS, PA, TE>(tap2, s2, w2p);
+                }
+                {
+                    // A operand row tid: axis-0 window, hi/lo TF32 parts, written four values at a time
+                    float tap0[TAPS];
+                    const unsigned long long T0 = pack2(fmaf(2.f, f0, -1.f), fmaf(2.f, f0, -1.f));
+#pragma unroll
+                    for (int q = 0; q < M; ++q) {
+                        unsigned long long h0 = pc[q * kPolyCoef + kPolyCoef - 1];
+#pragma unroll
+                        for (int k = kPolyCoef - 2; k >= 0; --k) h0 = ffma2(h0, T0, pc[q * kPolyCoef + k]);
+                        tap0[2 * q] = live ? lane_of(h0, 0) : 0.f;
+                        tap0[2 * q + 1] = live ? lane_of(h0, 1) : 0.f;
+                    }
+                    float v0[16];
+                    place_taps<TAPS, 16, TE>(tap0, s0, v0);
+#pragma unroll
+                    for (int kb = 0; kb < 4; ++kb) {
+                        float4 h, l;
+                        h.x = to_tf32(v0[4 * kb + 0]); l.x = to_tf32(v0[4 * kb + 0] - h.x);
+                        h.y = to_tf32(v0[4 * kb + 1]); l.y = to_tf32(v0[4 * kb + 1] - h.y);
+                        h.z = to_tf32(v0[4 * kb + 2]); l.z = to_tf32(v0[4 * kb + 2] - h.z);
+                        h.w = to_tf32(v0[4 * kb + 3]); l.w = to_tf32(v0[4 * kb + 3] - h.w);
+                        const uint32_t off = kmajor_off(tid, 4 * kb);
+                        *reinterpret_cast<float4 *>(sA_hi + off) = h;
+                        *reinterpret_cast<float4 *>(sA_lo + off) = l;
+                    }
                 }
             }
             // make the generic-proxy stores visible to the tensor core
@@ -194,9 +244,8 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;");
-            float accb[PA];
-#pragma unroll
-            for (int q = 0; q < PA; ++q) accb[q] = 0.f;
+            // f = sum_b w1[b] sum_c w2[c] T[b, c], one row b at a time
+            float f = 0.f, rowsum = 0.f;
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
                 if (failed) break;   // uniform: decided by __syncthreads_or below
@@ -257,7 +306,13 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             const int n = h * N + ch * 8 + e;
-                            if (n < NCOL) accb[n / PA] += w2p[n % PA] * __uint_as_float(r[e]);
+                            if (n < NCOL) {
+                                rowsum = fmaf(w2p[n % PA], __uint_as_float(r[e]), rowsum);
+                                if (n % PA == PA - 1) {
+                                    f = fmaf(w1p[n / PA], rowsum, f);
+                                    rowsum = 0.f;
+                                }
+                            }
                         }
                     }
                 }
@@ -267,23 +322,17 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
             }
             if (!failed) {
-                float f = 0.f;
-#pragma unroll
-                for (int q = 0; q < PA; ++q) f += w1p[q] * accb[q];
                 if (live) {
-                    const int i = a.perm[kq];
                     const double fd = double(f);
                     if (a.op == OP_DEGREE) {
                         const double dd = fd - 1.0;
-                        a.degree_out[i] = dd;
+                        a.degree_out[iq] = dd;
                         a.dinv_out[kq] = dd > 0.0 ? 1.0 / sqrt(dd) : 0.0;
                     } else if (a.op == OP_W) {
-                        a.y[i] = fd - a.x[i];
+                        a.y[iq] = fd - xq;
                     } else {
-                        const double di = a.dinv[kq];
-                        const double xi = a.x[i];
-                        const double ax = di * (fd - di * xi);
-                        a.y[i] = a.op == OP_A ? ax : xi - ax;
+                        const double ax = dq * (fd - dq * xq);
+                        a.y[iq] = a.op == OP_A ? ax : xq - ax;
                     }
                 }
             }
@@ -347,9 +396,9 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
     a.ngrid = P.ngrid;
     a.g = reinterpret_cast<const float *>(P.g);
     a.op = op;
-    a.b = float(P.kb_b);
-    a.inv_den = float(P.kb_inv_sinh_bm);
     a.error_flag = P.error_flag;
+    for (int j = 0; j < 2 * kMaxM; ++j)
+        for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
     switch (P.m) {
         case 2: return launch_tc<2, 8>(P, a);
         case 3: return launch_tc<3, 8>(P, a);

@@ -82,23 +82,6 @@ __device__ __forceinline__ double fixed_scale_of(double abs_sum) {
     return ldexp(1.0, k);
 }
 
-// Two FP32 lanes in one 64-bit register: lane 0 in the low half.
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float lane_of(unsigned long long v, int hi) {
-    return __uint_as_float(static_cast<unsigned>(hi ? (v >> 32) : v));
-}
-// a * b + c on both lanes.
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 __device__ __forceinline__ void group_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }

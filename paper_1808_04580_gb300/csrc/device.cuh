@@ -60,6 +60,29 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
+// 2^k with k the largest integer such that sum|x~| * 2^k < 2^62 (FP32C fixed point).
+__device__ __forceinline__ double fixed_scale_of(double abs_sum) {
+    if (!(abs_sum > 0.0)) return 1.0;
+    int e;
+    frexp(abs_sum, &e);
+    int k = 62 - e;
+    k = k > 120 ? 120 : (k < -120 ? -120 : k);     // 2^k stays a normal FP32 number
+    return ldexp(1.0, k);
+}
+
+// FP32 value (already scaled by 2^k, |v| < 2^62) -> nearest int64 with 32-bit
+// conversions only.  |v| = h 2^32 + l with h = floor(|v| 2^-32) and
+// 0 <= l < 2^32: both parts are exact in FP32 (power-of-two scaling; l keeps
+// a subset of the bits of |v|), and the sign is applied to the integer.
+__device__ __forceinline__ long long to_fixed(float v) {
+    const float av = fabsf(v);
+    const float hf = floorf(av * 2.3283064365386963e-10f);
+    const float lf = fmaf(hf, -4294967296.0f, av);
+    const unsigned long long mag = ((unsigned long long)__float2uint_rn(hf) << 32) + __float2uint_rn(lf);
+    return v < 0.f ? -(long long)mag : (long long)mag;
+}
+__device__ __forceinline__ long long to_fixed(double v) { return __double2ll_rn(v); }
+
 __device__ __forceinline__ int cell_axis(int32_t packed, int a) { return (packed >> (10 * a)) & 1023; }
 __device__ __forceinline__ int cell_axis(int64_t packed, int a) { return (int)((packed >> (10 * a)) & 1023); }
 

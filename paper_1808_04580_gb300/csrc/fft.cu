@@ -58,7 +58,7 @@ __device__ __forceinline__ double fixed_point_unscale(double abs_sum) {
     int e;
     frexp(abs_sum, &e);
     int k = 62 - e;
-    k = k > 1000 ? 1000 : (k < -1000 ? -1000 : k);
+    k = k > 120 ? 120 : (k < -120 ? -120 : k);     // 2^k stays a normal FP32 number
     return ldexp(1.0, -k);
 }
 

@@ -28,6 +28,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace nfl {
 
@@ -67,28 +68,6 @@ __device__ __forceinline__ void place_taps(const float (&tap)[TAPS], int s, floa
     }
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ float to_tf32(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor: start, leading (K) and stride (M/N)
-// byte offsets in 16-byte units, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
-}
-
-// Byte offset of element (row, k) in a K-major, no-swizzle operand of K = 16.
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
-    return (uint32_t)((((row >> 3) * 4 + (k >> 2)) * 128) + ((row & 7) * 16) + ((k & 3) * 4));
-}
-
 template <int M, int TE>
 struct TCGeom {
     static constexpr int PA = TE + 2 * M - 1;             // <= 16
@@ -99,8 +78,6 @@ struct TCGeom {
     static constexpr int A_BYTES = 128 * 64;              // 128 rows x 16 TF32
     static constexpr int B_BYTES = NH * N * 64;           // all halves
 };
-
-constexpr uint32_t kSpinLimit = 1u << 26;
 
 template <int M, int TE>
 __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {

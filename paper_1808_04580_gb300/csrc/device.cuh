@@ -60,6 +60,13 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
+// a * b on both lanes.
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // 2^k with k the largest integer such that sum|x~| * 2^k < 2^62 (FP32C fixed point).
 __device__ __forceinline__ double fixed_scale_of(double abs_sum) {
     if (!(abs_sum > 0.0)) return 1.0;

@@ -110,6 +110,8 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y);
 int column_tile_edge(int m);
 cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool scale_dinv);
 cudaError_t stage_spread3_values(Plan &P, const double *x, bool ones, bool scale_dinv);
+bool spread_warp_available(const Plan &P);
+cudaError_t launch_spread3_warp(Plan &P);
 
 // 3-D interpolation on the tensor cores (gather_tc.cu)
 bool gather_tc_available(const Plan &P);

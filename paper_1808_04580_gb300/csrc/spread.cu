@@ -223,7 +223,10 @@ cudaError_t prepare_spread(Plan &P, const double *x, bool ones, bool scale_dinv)
 }
 
 cudaError_t launch_spread(Plan &P, const double *x, int64_t, bool ones, bool scale_dinv) {
-    if (P.d == 3 && column_tile_edge(P.m) == P.tile_edge) return launch_spread3_columns(P, x, ones, scale_dinv);
+    if (P.d == 3 && column_tile_edge(P.m) == P.tile_edge) {
+        if (spread_warp_available(P)) return launch_spread3_warp(P);
+        return launch_spread3_columns(P, x, ones, scale_dinv);
+    }
     SpreadArgs a;
     a.pts = P.pts;
     a.perm = P.perm;

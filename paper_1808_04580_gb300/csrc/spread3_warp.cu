@@ -1,0 +1,297 @@
+// Window spreading in 3-D, FP32 / FP32C, one warp per node slice
+// (Alg. 1 step 1, the window half of the adjoint NFFT):
+//   h_t = sum_i x~_i phi(n v~_i0 - t_0) phi(n v~_i1 - t_1) phi(n v~_i2 - t_2).
+//
+// The plan sorts the nodes of every tile by cell, so the nodes of one cell
+// are contiguous; they share the whole (2M)^3 support.  A CTA of NG warps
+// takes one chunk of one tile (TE^3 cells); warp g takes the chunk's slices
+// of 32 nodes g, g + NG, ...  and owns a copy of the tile plus halo
+// (PA = TE + 2M - 1 per axis) in shared memory.
+//
+// Per slice, lane i stages node i: its tile-local cell, the 3 x 2M window
+// taps (the plan's per-tap polynomials, Horner in t = 2f - 1 with two taps
+// per fma.rn.f32x2; x~ folded into the axis-1 taps), written once per node.
+// A warp ballot marks the cell runs.  For the accumulation, LPB lanes share
+// a support row jb of axis 1 and each owns CPL support columns jc of axis 2;
+// a lane keeps 2M x CPL accumulators as pairs of adjacent columns and adds,
+// per node, (w1[jb] w2[jc], w1[jb] w2[jc + 1]) * (w0[ja], w0[ja]) with one
+// fma.rn.f32x2 per pair and ja.  Every multiply-add lands in the support,
+// with no range tests and no shared-memory traffic besides the staged taps.
+// When the cell changes, the lanes add their accumulators to the warp's
+// tile copy with plain read-modify-write: in one flush the lanes touch
+// distinct positions, and __syncwarp orders consecutive flushes.
+//
+// At the end of the chunk the CTA sums the NG tile copies; FP32 adds each
+// non-zero sum to the global grid with an FP32 atomic, FP32C converts it to
+// 64-bit fixed point (scale 2^k from sum |x~|, so nothing can overflow) and
+// adds it with an integer atomic.  So FP32C sums at most 2048 / NG nodes of a
+// tile position in FP32 (512 for NG = 4) before the exact integer part.
+#include "device.cuh"
+#include "internal.h"
+
+namespace nfl {
+
+struct SpreadWarpArgs {
+    const PointF *pts;
+    const float *xs;                // x~ in sorted order
+    const WorkItem *items;
+    int64_t nitems;
+    int ntile[3];
+    int L[3];
+    int wrap[3];
+    int ngrid;
+    void *grid;
+    const double *abs_sum;
+    float poly[2 * kMaxM][kPolyCoef];
+};
+
+template <int M, int TE>
+struct WarpGeom {
+    static constexpr int PA = TE + 2 * M - 1;
+    static constexpr int PA3 = PA * PA * PA;
+    static constexpr int TAPS = 2 * M;
+    static constexpr int LPB = M == 6 ? 2 : (M == 4 ? 4 : (M == 3 ? 3 : 2));   // lanes per support row jb
+    static constexpr int CPL = TAPS / LPB;        // support columns per lane (even)
+    static constexpr int CP = CPL / 2;            // column pairs per lane
+    static constexpr int LANES = TAPS * LPB;      // lanes that accumulate
+    static constexpr int SEG = (CPL + 3) / 4 * 4; // axis-2 taps of one lane, padded to 16 bytes
+    static constexpr int NG = 4;                  // warps (tile copies) per CTA
+    static constexpr int S = 32;                  // nodes per slice
+    static constexpr int TILE = (PA3 + 3) / 4 * 4;
+    // per warp: tile copy, then per node the duplicated axis-0 taps (TAPS x 8 B),
+    // the axis-1 taps and the padded axis-2 taps
+    static constexpr int W0_BYTES = S * TAPS * 8;
+    static constexpr int W1_BYTES = S * TAPS * 4;
+    static constexpr int W2_BYTES = S * LPB * SEG * 4;
+    static constexpr int WARP_BYTES = TILE * 4 + W0_BYTES + W1_BYTES + W2_BYTES;
+    static constexpr int SMEM = NG * WARP_BYTES;
+    static_assert(CPL % 2 == 0 && LANES <= 32, "lane layout");
+    static_assert(WARP_BYTES % 16 == 0, "16-byte aligned per-warp areas");
+};
+
+template <int M, int TE, bool FIXED>
+__global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadWarpArgs a) {
+    using G = WarpGeom<M, TE>;
+    constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, CP = G::CP, CPL = G::CPL, SEG = G::SEG, S = G::S,
+                  NG = G::NG;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    unsigned char *mine = smem_raw + g * G::WARP_BYTES;
+    float *tile = reinterpret_cast<float *>(mine);
+    unsigned long long *w0d = reinterpret_cast<unsigned long long *>(mine + G::TILE * 4);      // [S][TAPS]
+    float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES);                   // [S][TAPS]
+    float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES + G::W1_BYTES);     // [S][LPB * SEG]
+    __shared__ __align__(16) float2 polys[M][kPolyCoef];
+
+    const bool acc_lane = lane < G::LANES;
+    const int jb = acc_lane ? lane / G::LPB : 0;
+    const int hseg = acc_lane ? lane - jb * G::LPB : 0;          // which CPL columns: jc = hseg * CPL + c
+    for (int e = threadIdx.x; e < M * kPolyCoef; e += NG * 32) {
+        const int q = e / kPolyCoef, k = e - q * kPolyCoef;
+        polys[q][k] = make_float2(a.poly[2 * q][k], a.poly[2 * q + 1][k]);
+    }
+    for (int e = lane; e < G::TILE; e += 32) tile[e] = 0.f;
+    float fscale = 1.f;
+    if (FIXED) fscale = float(fixed_scale_of(*a.abs_sum));
+    __syncthreads();
+
+    unsigned long long acc[TAPS][CP];             // (jc, jc + 1) pairs for each ja
+#pragma unroll
+    for (int ja = 0; ja < TAPS; ++ja)
+#pragma unroll
+        for (int c = 0; c < CP; ++c) acc[ja][c] = 0ull;
+
+    // add the accumulators of cell o to this warp's tile copy
+    auto flush = [&](int o) {
+        __syncwarp();
+        if (acc_lane) {
+            const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
+            float *col = tile + (s0 * PA + s1 + jb) * PA + s2 + hseg * CPL;
+#pragma unroll
+            for (int ja = 0; ja < TAPS; ++ja)
+#pragma unroll
+                for (int c = 0; c < CP; ++c) {
+                    col[ja * PA * PA + 2 * c] += lane_of(acc[ja][c], 0);
+                    col[ja * PA * PA + 2 * c + 1] += lane_of(acc[ja][c], 1);
+                    acc[ja][c] = 0ull;
+                }
+        }
+    };
+
+    for (int64_t it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const WorkItem w = a.items[it];
+        const int wend = w.start + w.count;
+        int tc[3];
+        tile_coords<3>(w.tile, a.ntile, tc);
+        int cur = -1;
+        // this lane's node of the warp's next slice, loaded one slice ahead
+        int base = w.start + g * S;
+        PointF pn = {{0.f, 0.f, 0.f}, 0};
+        float xn = 0.f;
+        if (base + lane < wend) {
+            pn = a.pts[base + lane];
+            xn = a.xs[base + lane];
+        }
+        for (; base < wend; base += NG * S) {
+            const int cnt = min(S, wend - base);
+            const bool valid = lane < cnt;
+            int o = 0;
+            {
+                // stage node `lane` of the slice
+                float f[3];
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    o |= (valid ? cell_axis(pn.cell, ax) - tc[ax] * TE : 0) << (8 * ax);
+                    f[ax] = valid ? pn.f[ax] : 0.f;
+                }
+                const float xv = xn;
+                const int kn = base + NG * S + lane;
+                if (kn < wend) {
+                    pn = a.pts[kn];
+                    xn = a.xs[kn];
+                }
+                const unsigned long long T0 = pack2(fmaf(2.f, f[0], -1.f), fmaf(2.f, f[0], -1.f));
+                const unsigned long long T1 = pack2(fmaf(2.f, f[1], -1.f), fmaf(2.f, f[1], -1.f));
+                const unsigned long long T2 = pack2(fmaf(2.f, f[2], -1.f), fmaf(2.f, f[2], -1.f));
+                const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
+                unsigned long long *r0 = w0d + lane * TAPS;
+                float *r1 = w1s + lane * TAPS;
+                float *r2 = w2s + lane * (G::LPB * SEG);
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    unsigned long long h0 = pc[q * kPolyCoef + kPolyCoef - 1], h1 = h0, h2 = h0;
+#pragma unroll
+                    for (int k = kPolyCoef - 2; k >= 0; --k) {
+                        const unsigned long long c = pc[q * kPolyCoef + k];
+                        h0 = ffma2(h0, T0, c);
+                        h1 = ffma2(h1, T1, c);
+                        h2 = ffma2(h2, T2, c);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int j = 2 * q + u;
+                        const float v0 = lane_of(h0, u);
+                        r0[j] = pack2(v0, v0);
+                        r1[j] = lane_of(h1, u) * xv;
+                        r2[(j / CPL) * SEG + j % CPL] = lane_of(h2, u);
+                    }
+                }
+            }
+            const int prev = __shfl_up_sync(0xffffffffu, o, 1);
+            const unsigned runs = __ballot_sync(0xffffffffu, valid && (lane == 0 || o != prev));
+            __syncwarp();
+            int i = 0;
+            while (i < cnt) {
+                const unsigned rest = i + 1 < 32 ? (runs >> (i + 1)) : 0u;
+                const int j = rest ? min(cnt, i + __ffs(rest)) : cnt;
+                const int oi = __shfl_sync(0xffffffffu, o, i);
+                if (oi != cur) {
+                    if (cur >= 0) flush(cur);
+                    cur = oi;
+                }
+                if (acc_lane) {
+#pragma unroll 2
+                    for (int q = i; q < j; ++q) {
+                        const float w1v = w1s[q * TAPS + jb];
+                        const unsigned long long w1p = pack2(w1v, w1v);
+                        const float *r2 = w2s + q * (G::LPB * SEG) + hseg * SEG;
+                        unsigned long long coef[CP];
+#pragma unroll
+                        for (int c = 0; c < CP; ++c)
+                            coef[c] = fmul2(w1p, *reinterpret_cast<const unsigned long long *>(r2 + 2 * c));
+                        const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(w0d + q * TAPS);
+#pragma unroll
+                        for (int ja2 = 0; ja2 < TAPS / 2; ++ja2) {
+                            const ulonglong2 wv = r0[ja2];
+#pragma unroll
+                            for (int c = 0; c < CP; ++c) {
+                                acc[2 * ja2][c] = ffma2(coef[c], wv.x, acc[2 * ja2][c]);
+                                acc[2 * ja2 + 1][c] = ffma2(coef[c], wv.y, acc[2 * ja2 + 1][c]);
+                            }
+                        }
+                    }
+                }
+                i = j;
+            }
+            __syncwarp();                         // the next slice overwrites the staged taps
+        }
+        if (cur >= 0) flush(cur);
+        __syncthreads();
+
+        // sum the tile copies -> global grid (c fastest, matching the grid's x2 axis), clear them
+        for (int e = threadIdx.x; e < PA3; e += NG * 32) {
+            float v = 0.f;
+#pragma unroll
+            for (int gg = 0; gg < NG; ++gg) {
+                float *t = reinterpret_cast<float *>(smem_raw + gg * G::WARP_BYTES);
+                v += t[e];
+                t[e] = 0.f;
+            }
+            if (v == 0.f) continue;
+            const int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
+            int p0 = tc[0] * TE - (M - 1) + q0;
+            int p1 = tc[1] * TE - (M - 1) + q1;
+            int p2 = tc[2] * TE - (M - 1) + q2;
+            if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+            if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+            if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+            if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
+            const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+            if (FIXED)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
+                          (unsigned long long)to_fixed(v * fscale));
+            else
+                atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
+        }
+        __syncthreads();
+    }
+}
+
+template <int M, int TE, bool FIXED>
+static cudaError_t launch_warp(Plan &P, const SpreadWarpArgs &a) {
+    using G = WarpGeom<M, TE>;
+    auto kern = spread3_warp<M, TE, FIXED>;
+    NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
+    NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int per_sm = 0;
+    NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NG * 32, G::SMEM));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * P.num_sms;
+    if (grid > P.nitems) grid = P.nitems;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, G::NG * 32, G::SMEM, P.stream>>>(a);
+    return cudaGetLastError();
+}
+
+bool spread_warp_available(const Plan &P) {
+    if (P.d != 3 || P.prec == NFL_PREC_FP64 || P.tile_edge != column_tile_edge(P.m)) return false;
+    return P.m == 2 || P.m == 3 || P.m == 4 || P.m == 6;
+}
+
+cudaError_t launch_spread3_warp(Plan &P) {
+    SpreadWarpArgs a;
+    a.pts = reinterpret_cast<const PointF *>(P.pts);
+    a.xs = static_cast<const float *>(P.xsort);
+    a.items = P.items;
+    a.nitems = P.nitems;
+    for (int i = 0; i < 3; ++i) {
+        a.ntile[i] = P.ntile[i];
+        a.L[i] = P.L[i];
+        a.wrap[i] = P.wrap[i];
+    }
+    a.ngrid = P.ngrid;
+    a.grid = P.grid;
+    a.abs_sum = P.scratch;
+    for (int j = 0; j < 2 * kMaxM; ++j)
+        for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
+    const bool fixed = P.prec == NFL_PREC_FP32C;
+    switch (P.m) {
+        case 2: return fixed ? launch_warp<2, 8, true>(P, a) : launch_warp<2, 8, false>(P, a);
+        case 3: return fixed ? launch_warp<3, 8, true>(P, a) : launch_warp<3, 8, false>(P, a);
+        case 4: return fixed ? launch_warp<4, 8, true>(P, a) : launch_warp<4, 8, false>(P, a);
+        case 6: return fixed ? launch_warp<6, 4, true>(P, a) : launch_warp<6, 4, false>(P, a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace nfl

@@ -54,16 +54,17 @@ struct WarpGeom {
     static constexpr int CPL = TAPS / LPB;        // support columns per lane (even)
     static constexpr int CP = CPL / 2;            // column pairs per lane
     static constexpr int LANES = TAPS * LPB;      // lanes that accumulate
-    static constexpr int SEG = (CPL + 3) / 4 * 4; // axis-2 taps of one lane, padded to 16 bytes
     static constexpr int NG = 4;                  // warps (tile copies) per CTA
     static constexpr int S = 32;                  // nodes per slice
     static constexpr int TILE = (PA3 + 3) / 4 * 4;
-    // per warp: tile copy, then per node the duplicated axis-0 taps (TAPS x 8 B),
-    // the axis-1 taps and the padded axis-2 taps
-    static constexpr int W0_BYTES = S * TAPS * 8;
-    static constexpr int W1_BYTES = S * TAPS * 4;
-    static constexpr int W2_BYTES = S * LPB * SEG * 4;
-    static constexpr int WARP_BYTES = TILE * 4 + W0_BYTES + W1_BYTES + W2_BYTES;
+    // per node, rows of staged taps whose strides are odd multiples of 16 bytes
+    // (the 16-byte stores of the 32 lanes then fall in distinct bank groups):
+    // the duplicated axis-0 taps (TAPS x 8 B), the axis-1 and the axis-2 taps
+    static constexpr int R0 = (TAPS / 2) % 2 ? TAPS : TAPS + 2;                 // u64 per row
+    static constexpr int R1 = ((TAPS + 3) / 4) % 2 ? (TAPS + 3) / 4 * 4 : (TAPS + 3) / 4 * 4 + 4;   // floats per row
+    static constexpr int W0_BYTES = S * R0 * 8;
+    static constexpr int W1_BYTES = S * R1 * 4;
+    static constexpr int WARP_BYTES = TILE * 4 + W0_BYTES + 2 * W1_BYTES;
     static constexpr int SMEM = NG * WARP_BYTES;
     static_assert(CPL % 2 == 0 && LANES <= 32, "lane layout");
     static_assert(WARP_BYTES % 16 == 0, "16-byte aligned per-warp areas");
@@ -72,15 +73,15 @@ struct WarpGeom {
 template <int M, int TE, bool FIXED>
 __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadWarpArgs a) {
     using G = WarpGeom<M, TE>;
-    constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, CP = G::CP, CPL = G::CPL, SEG = G::SEG, S = G::S,
-                  NG = G::NG;
+    constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, CP = G::CP, CPL = G::CPL, S = G::S, NG = G::NG,
+                  R0 = G::R0, R1 = G::R1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     unsigned char *mine = smem_raw + g * G::WARP_BYTES;
     float *tile = reinterpret_cast<float *>(mine);
-    unsigned long long *w0d = reinterpret_cast<unsigned long long *>(mine + G::TILE * 4);      // [S][TAPS]
-    float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES);                   // [S][TAPS]
-    float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES + G::W1_BYTES);     // [S][LPB * SEG]
+    unsigned long long *w0d = reinterpret_cast<unsigned long long *>(mine + G::TILE * 4);      // [S][R0]
+    float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES);                   // [S][R1]
+    float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES + G::W1_BYTES);     // [S][R1]
     __shared__ __align__(16) float2 polys[M][kPolyCoef];
 
     const bool acc_lane = lane < G::LANES;
@@ -154,9 +155,8 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
                 const unsigned long long T1 = pack2(fmaf(2.f, f[1], -1.f), fmaf(2.f, f[1], -1.f));
                 const unsigned long long T2 = pack2(fmaf(2.f, f[2], -1.f), fmaf(2.f, f[2], -1.f));
                 const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
-                unsigned long long *r0 = w0d + lane * TAPS;
-                float *r1 = w1s + lane * TAPS;
-                float *r2 = w2s + lane * (G::LPB * SEG);
+                unsigned long long t0[TAPS];
+                float t1[TAPS], t2[TAPS];
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
                     unsigned long long h0 = pc[q * kPolyCoef + kPolyCoef - 1], h1 = h0, h2 = h0;
@@ -169,12 +169,28 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
                     }
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        const int j = 2 * q + u;
                         const float v0 = lane_of(h0, u);
-                        r0[j] = pack2(v0, v0);
-                        r1[j] = lane_of(h1, u) * xv;
-                        r2[(j / CPL) * SEG + j % CPL] = lane_of(h2, u);
+                        t0[2 * q + u] = pack2(v0, v0);
+                        t1[2 * q + u] = lane_of(h1, u) * xv;
+                        t2[2 * q + u] = lane_of(h2, u);
                     }
+                }
+                // 16-byte stores of this lane's rows
+                ulonglong2 *r0 = reinterpret_cast<ulonglong2 *>(w0d + lane * R0);
+#pragma unroll
+                for (int j = 0; j < TAPS / 2; ++j) r0[j] = make_ulonglong2(t0[2 * j], t0[2 * j + 1]);
+                float4 *r1 = reinterpret_cast<float4 *>(w1s + lane * R1);
+                float4 *r2 = reinterpret_cast<float4 *>(w2s + lane * R1);
+#pragma unroll
+                for (int j = 0; j < (TAPS + 3) / 4; ++j) {
+                    float v1[4], v2[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v1[u] = 4 * j + u < TAPS ? t1[(4 * j + u) % TAPS] : 0.f;
+                        v2[u] = 4 * j + u < TAPS ? t2[(4 * j + u) % TAPS] : 0.f;
+                    }
+                    r1[j] = make_float4(v1[0], v1[1], v1[2], v1[3]);
+                    r2[j] = make_float4(v2[0], v2[1], v2[2], v2[3]);
                 }
             }
             const int prev = __shfl_up_sync(0xffffffffu, o, 1);
@@ -192,14 +208,14 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
                 if (acc_lane) {
 #pragma unroll 2
                     for (int q = i; q < j; ++q) {
-                        const float w1v = w1s[q * TAPS + jb];
+                        const float w1v = w1s[q * R1 + jb];
                         const unsigned long long w1p = pack2(w1v, w1v);
-                        const float *r2 = w2s + q * (G::LPB * SEG) + hseg * SEG;
+                        const float *r2 = w2s + q * R1 + hseg * CPL;
                         unsigned long long coef[CP];
 #pragma unroll
                         for (int c = 0; c < CP; ++c)
                             coef[c] = fmul2(w1p, *reinterpret_cast<const unsigned long long *>(r2 + 2 * c));
-                        const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(w0d + q * TAPS);
+                        const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(w0d + q * R0);
 #pragma unroll
                         for (int ja2 = 0; ja2 < TAPS / 2; ++ja2) {
                             const ulonglong2 wv = r0[ja2];

@@ -35,7 +35,7 @@ namespace nfl {
 struct GatherTCArgs {
     const PointF *pts;
     const int32_t *perm;
-    const double *x;
+    const double *xd;     // x in sorted order
     double *y;
     const double *dinv;
     double *degree_out;
@@ -122,26 +122,35 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
         const WorkItem w = a.items[it];
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
-        // B operand: G[a][(b, c)] as rows n = b PA + c, k = a; hi/lo TF32 parts; zero padding
-        for (int e = tid; e < NH * N * 16; e += 128) {
-            const int n = e >> 4, k = e & 15;
-            float v = 0.f;
-            if (n < NCOL && k < PA) {
-                const int bq = n / PA, cq = n - (n / PA) * PA;
+        // B operand: row n = b PA + c holds G[a][(b, c)] for k = a = 0..15, split into TF32
+        // hi/lo parts; zero beyond PA^2 rows, beyond PA along a and outside the box
+        for (int n = tid; n < NH * N; n += 128) {
+            const bool used = n < NCOL;
+            const int bq = used ? n / PA : 0, cq = used ? n - bq * PA : 0;
+            int p1 = tc[1] * TE - (M - 1) + bq;
+            int p2 = tc[2] * TE - (M - 1) + cq;
+            if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+            if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+            const bool ok12 = used && p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2];
+            const float *src = a.g + ((int64_t)(ok12 ? p2 : 0) * a.L[1] + (ok12 ? p1 : 0)) * a.L[0];
+            float v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
                 int p0 = tc[0] * TE - (M - 1) + k;
-                int p1 = tc[1] * TE - (M - 1) + bq;
-                int p2 = tc[2] * TE - (M - 1) + cq;
                 if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-                if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-                if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-                if (p0 >= 0 && p0 < a.L[0] && p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2])
-                    v = a.g[((int64_t)p2 * a.L[1] + p1) * a.L[0] + p0];
+                v[k] = (ok12 && k < PA && p0 >= 0 && p0 < a.L[0]) ? src[p0] : 0.f;
             }
-            const float hi = to_tf32(v);
-            const float lo = to_tf32(v - hi);
-            const uint32_t off = kmajor_off(n, k);
-            *reinterpret_cast<float *>(sB_hi + off) = hi;
-            *reinterpret_cast<float *>(sB_lo + off) = lo;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                float4 h, l;
+                h.x = to_tf32(v[4 * kb + 0]); l.x = to_tf32(v[4 * kb + 0] - h.x);
+                h.y = to_tf32(v[4 * kb + 1]); l.y = to_tf32(v[4 * kb + 1] - h.y);
+                h.z = to_tf32(v[4 * kb + 2]); l.z = to_tf32(v[4 * kb + 2] - h.z);
+                h.w = to_tf32(v[4 * kb + 3]); l.w = to_tf32(v[4 * kb + 3] - h.w);
+                const uint32_t off = kmajor_off(n, 4 * kb);
+                *reinterpret_cast<float4 *>(sB_hi + off) = h;
+                *reinterpret_cast<float4 *>(sB_lo + off) = l;
+            }
         }
 
         for (int base = w.start; base < w.start + w.count && !failed; base += 128) {
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                     const PointF p = a.pts[kq];
                     // epilogue operands, loaded now and used after the contraction
                     iq = a.perm[kq];
-                    if (a.op != OP_DEGREE) xq = a.x[iq];
+                    if (a.op != OP_DEGREE) xq = a.xd[kq];
                     if (a.op == OP_A || a.op == OP_LS) dq = a.dinv[kq];
                     s0 = cell_axis(p.cell, 0) - tc[0] * TE;
                     s1 = cell_axis(p.cell, 1) - tc[1] * TE;
@@ -358,7 +367,7 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
     GatherTCArgs a;
     a.pts = reinterpret_cast<const PointF *>(P.pts);
     a.perm = P.perm;
-    a.x = x;
+    a.xd = P.xsorted;
     a.y = y;
     a.dinv = P.dinv_sorted;
     a.degree_out = P.degree;

@@ -62,6 +62,7 @@ struct Plan {
     int32_t *perm = nullptr;    // sorted position -> input index
     double *dinv_sorted = nullptr;  // D_E^{-1/2} in sorted order
     void *xsort = nullptr;      // x~ of the current column in sorted order (spread type; 3-D cell kernels)
+    double *xsorted = nullptr;  // x of the current column in sorted order (interpolation epilogue)
     double *degree = nullptr;   // d_E in input order
     double min_deg = 0, max_deg = 0;
     bool degree_ok = false;

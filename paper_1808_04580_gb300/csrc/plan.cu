@@ -455,6 +455,7 @@ static void free_plan(Plan *P) {
     cudaFree(P->perm);
     cudaFree(P->dinv_sorted);
     cudaFree(P->xsort);
+    cudaFree(P->xsorted);
     cudaFree(P->degree);
     cudaFree(P->grid);
     cudaFree(P->bufA);
@@ -614,7 +615,8 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     const bool dbl = points_are_double(prec);
     if (cudaMalloc(&P->pts, n * (dbl ? sizeof(PointD) : sizeof(PointF))) != cudaSuccess ||
         cudaMalloc(&P->perm, n * 4) != cudaSuccess || cudaMalloc(&P->dinv_sorted, n * 8) != cudaSuccess ||
-        cudaMalloc(&P->degree, n * 8) != cudaSuccess || cudaMalloc(&P->xsort, n * 8) != cudaSuccess) {
+        cudaMalloc(&P->degree, n * 8) != cudaSuccess || cudaMalloc(&P->xsort, n * 8) != cudaSuccess ||
+        cudaMalloc(&P->xsorted, n * 8) != cudaSuccess) {
         cleanup();
         return NFL_ERR_OUT_OF_MEMORY;
     }

@@ -51,16 +51,18 @@ struct Spread3Args {
 };
 
 // x~_k = x[perm[k]] * dinv[k] (or dinv[k] / 1 for the all-ones vector) in sorted
-// order; with abs_sum, also sum_k |x~_k| (the fixed-point scale of FP32C).
+// order, and x[perm[k]] itself (for the interpolation epilogue); with
+// abs_sum, also sum_k |x~_k| (the fixed-point scale of FP32C).
 template <typename T>
 __global__ void __launch_bounds__(256) stage_values(const double *x, const int32_t *perm, const double *dinv,
-                                                    int64_t n, int ones, T *out, double *abs_sum) {
+                                                    int64_t n, int ones, T *out, double *xs_out, double *abs_sum) {
     __shared__ double red[256];
     double acc = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        double v = ones ? 1.0 : x[perm[k]];
-        if (dinv) v *= dinv[k];
+        const double xv = ones ? 1.0 : x[perm[k]];
+        const double v = dinv ? xv * dinv[k] : xv;
         out[k] = T(v);
+        xs_out[k] = xv;
         acc += fabs(v);
     }
     if (!abs_sum) return;
@@ -72,7 +74,6 @@ __global__ void __launch_bounds__(256) stage_values(const double *x, const int32
     }
     if (threadIdx.x == 0) atomicAdd(abs_sum, red[0]);
 }
-
 
 __device__ __forceinline__ void group_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -395,10 +396,10 @@ cudaError_t stage_spread3_values(Plan &P, const double *x, bool ones, bool scale
     const int blocks = P.num_sms * 4;
     if (P.prec == NFL_PREC_FP64)
         stage_values<double><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
-                                                           static_cast<double *>(P.xsort), abs_sum);
+                                                           static_cast<double *>(P.xsort), P.xsorted, abs_sum);
     else
         stage_values<float><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
-                                                          static_cast<float *>(P.xsort), abs_sum);
+                                                          static_cast<float *>(P.xsort), P.xsorted, abs_sum);
     return cudaGetLastError();
 }
 

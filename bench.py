@@ -7,7 +7,8 @@ Workload (one "step" = one pass of the whole hot path over one batch):
   sigma = 0.08; fast summation N = 128, m = 6, p = 6, eps_B = 6/128.
   A step applies L_s to a block of ``--nrhs`` right-hand sides x ~ N(0, 1)
   (spread, FFT with the fused multiplier, gather with the fused D^{-1/2}
-  epilogue, per column), with the FP32-compensated arithmetic.
+  epilogue, per column), in the FP32C form (FP32 window arithmetic, spreading
+  sums carried into 64-bit fixed point).
 
 Reported: L_s matvecs/s (columns per second, all ranks), the same through
 host buffers (e2e), the plain FP64 single-vector form on the same data, the
@@ -50,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=4)
-    ap.add_argument("--n", type=int, default=N_NODES)
+    ap.add_argument("--points", type=int, default=N_NODES)
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp32", "fp64"])
     ap.add_argument("--baseline-rows", type=int, default=1024)
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -60,14 +61,18 @@ def parse():
 
 
 def dist_setup():
+    """Process group from the torchrun environment: NCCL with one GPU per rank, or gloo on a host without GPUs."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -76,7 +81,8 @@ def max_over_ranks(value, world):
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -180,20 +186,20 @@ def run_reference(args, world, rank):
         return
     import numpy as np
     from paper_1808_04580_gb300 import workloads
-    v = workloads.ball_plus_clusters(args.n, seed=0)
-    x = workloads.rhs(args.n, seed=1)
+    v = workloads.ball_plus_clusters(args.points, seed=0)
+    x = workloads.rhs(args.points, seed=1)
     rng = np.random.default_rng(2)
     rows_per_step = 64
     for _ in range(args.warmup):
-        oracle_rows(v, x, rng.choice(args.n, 8, replace=False))
+        oracle_rows(v, x, rng.choice(args.points, 8, replace=False))
     total = 0.0
     cores = 1
     for _ in range(args.steps):
-        _, dt, cores = oracle_rows(v, x, rng.choice(args.n, rows_per_step, replace=False))
+        _, dt, cores = oracle_rows(v, x, rng.choice(args.points, rows_per_step, replace=False))
         total += dt
-    value = rows_per_step * args.steps / total / args.n
+    value = rows_per_step * args.steps / total / args.points
     sample = "%d steps x %d of %d target rows, each summed over all %d sources; matvecs/s extrapolated as rows/s / n" % (
-        args.steps, rows_per_step, args.n, args.n)
+        args.steps, rows_per_step, args.points, args.points)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
@@ -216,7 +222,7 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    n, nrhs = args.n, args.nrhs
+    n, nrhs = args.points, args.nrhs
     v = workloads.ball_plus_clusters(n, seed=rank)
     X = workloads.rhs(n, nrhs=nrhs, seed=rank + 1)
     X = X.reshape(n, nrhs)
@@ -269,7 +275,7 @@ def main():
     flops = 2.0 * taps * n
     achieved = flops / (dom_ms / 1000.0) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    kname, src, summary = (("spread3_cells", "spread3.cu", "spread3_cells_ball10M.md") if dom == "spread"
+    kname, src, summary = (("spread3_warp", "spread3_warp.cu", "spread3_warp_ball10M.md") if dom == "spread"
                            else ("gather3_tc", "gather_tc.cu", "gather3_tc_ball10M.md"))
     kernel_file = os.path.join(ROOT, "paper_1808_04580_gb300", "csrc", src)
     traffic = profiled_traffic(summary, kernel_file) if n == 10_000_000 else None

@@ -68,14 +68,14 @@ __device__ __forceinline__ double fixed_point_unscale(double abs_sum) {
 //   Y[k + 2 j s + s] = (X[k + j s] - X[k + j s + n/2]) w^{j s},  w = e^{-+2 pi i / n}.
 template <typename C>
 __device__ C *stockham(C *x, C *y, int nl, int n, int logn, const C *tw, bool inverse) {
-    const int half = n >> 1;
+    const int half = n >> 1;                 // n is a power of two: index math by shifts and masks
     int s = 1;
     for (int stage = 0; stage < logn; ++stage) {
         for (int e = threadIdx.x; e < nl * half; e += blockDim.x) {
-            const int line = e / half;
-            const int bidx = e - line * half;
-            const int j = bidx / s;
-            const int k = bidx - j * s;
+            const int line = e >> (logn - 1);
+            const int bidx = e & (half - 1);
+            const int j = bidx >> stage;
+            const int k = bidx & (s - 1);
             const C *X = x + line * n;
             C *Y = y + line * n;
             const C c0 = X[k + j * s];

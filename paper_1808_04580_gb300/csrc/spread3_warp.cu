@@ -13,10 +13,11 @@
 // per fma.rn.f32x2; x~ folded into the axis-1 taps), written once per node.
 // A warp ballot marks the cell runs.  For the accumulation, LPB lanes share
 // a support row jb of axis 1 and each owns CPL support columns jc of axis 2;
-// a lane keeps 2M x CPL accumulators as pairs of adjacent columns and adds,
-// per node, (w1[jb] w2[jc], w1[jb] w2[jc + 1]) * (w0[ja], w0[ja]) with one
-// fma.rn.f32x2 per pair and ja.  Every multiply-add lands in the support,
-// with no range tests and no shared-memory traffic besides the staged taps.
+// a lane keeps 2M x CPL accumulators as pairs of adjacent rows ja and adds,
+// per node, (c, c) * (w0[ja], w0[ja + 1]) with c = w1[jb] w2[jc], one
+// fma.rn.f32x2 per pair and column.  Every multiply-add lands in the
+// support, with no range tests and no shared-memory traffic besides the
+// staged taps.
 // When the cell changes, the lanes add their accumulators to the warp's
 // tile copy with plain read-modify-write: in one flush the lanes touch
 // distinct positions, and __syncwarp orders consecutive flushes.
@@ -51,37 +52,34 @@ struct WarpGeom {
     static constexpr int PA3 = PA * PA * PA;
     static constexpr int TAPS = 2 * M;
     static constexpr int LPB = M == 6 ? 2 : (M == 4 ? 4 : (M == 3 ? 3 : 2));   // lanes per support row jb
-    static constexpr int CPL = TAPS / LPB;        // support columns per lane (even)
-    static constexpr int CP = CPL / 2;            // column pairs per lane
+    static constexpr int CPL = TAPS / LPB;        // support columns per lane
+    static constexpr int RP = TAPS / 2;           // row pairs (ja, ja + 1)
     static constexpr int LANES = TAPS * LPB;      // lanes that accumulate
     static constexpr int NG = 4;                  // warps (tile copies) per CTA
     static constexpr int S = 32;                  // nodes per slice
     static constexpr int TILE = (PA3 + 3) / 4 * 4;
-    // per node, rows of staged taps whose strides are odd multiples of 16 bytes
-    // (the 16-byte stores of the 32 lanes then fall in distinct bank groups):
-    // the duplicated axis-0 taps (TAPS x 8 B), the axis-1 and the axis-2 taps
-    static constexpr int R0 = (TAPS / 2) % 2 ? TAPS : TAPS + 2;                 // u64 per row
+    // per node, rows of staged taps (axes 0, 1, 2) whose strides are odd multiples
+    // of 16 bytes, so the 16-byte stores of the 32 lanes fall in distinct bank groups
     static constexpr int R1 = ((TAPS + 3) / 4) % 2 ? (TAPS + 3) / 4 * 4 : (TAPS + 3) / 4 * 4 + 4;   // floats per row
-    static constexpr int W0_BYTES = S * R0 * 8;
-    static constexpr int W1_BYTES = S * R1 * 4;
-    static constexpr int WARP_BYTES = TILE * 4 + W0_BYTES + 2 * W1_BYTES;
+    static constexpr int W_BYTES = S * R1 * 4;
+    static constexpr int WARP_BYTES = TILE * 4 + 3 * W_BYTES;
     static constexpr int SMEM = NG * WARP_BYTES;
-    static_assert(CPL % 2 == 0 && LANES <= 32, "lane layout");
+    static_assert(TAPS * LPB == LANES && LANES <= 32, "lane layout");
     static_assert(WARP_BYTES % 16 == 0, "16-byte aligned per-warp areas");
 };
 
 template <int M, int TE, bool FIXED>
-__global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadWarpArgs a) {
+__global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(SpreadWarpArgs a) {
     using G = WarpGeom<M, TE>;
-    constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, CP = G::CP, CPL = G::CPL, S = G::S, NG = G::NG,
-                  R0 = G::R0, R1 = G::R1;
+    constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, RP = G::RP, CPL = G::CPL, S = G::S, NG = G::NG,
+                  R1 = G::R1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     unsigned char *mine = smem_raw + g * G::WARP_BYTES;
     float *tile = reinterpret_cast<float *>(mine);
-    unsigned long long *w0d = reinterpret_cast<unsigned long long *>(mine + G::TILE * 4);      // [S][R0]
-    float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES);                   // [S][R1]
-    float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W0_BYTES + G::W1_BYTES);     // [S][R1]
+    float *w0s = reinterpret_cast<float *>(mine + G::TILE * 4);                     // [S][R1]
+    float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W_BYTES);       // [S][R1]
+    float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + 2 * G::W_BYTES);   // [S][R1]
     __shared__ __align__(16) float2 polys[M][kPolyCoef];
 
     const bool acc_lane = lane < G::LANES;
@@ -96,11 +94,11 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
     if (FIXED) fscale = float(fixed_scale_of(*a.abs_sum));
     __syncthreads();
 
-    unsigned long long acc[TAPS][CP];             // (jc, jc + 1) pairs for each ja
+    unsigned long long acc[RP][CPL];              // (ja, ja + 1) pairs for each column jc
 #pragma unroll
-    for (int ja = 0; ja < TAPS; ++ja)
+    for (int p = 0; p < RP; ++p)
 #pragma unroll
-        for (int c = 0; c < CP; ++c) acc[ja][c] = 0ull;
+        for (int c = 0; c < CPL; ++c) acc[p][c] = 0ull;
 
     // add the accumulators of cell o to this warp's tile copy
     auto flush = [&](int o) {
@@ -109,12 +107,12 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
             const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
             float *col = tile + (s0 * PA + s1 + jb) * PA + s2 + hseg * CPL;
 #pragma unroll
-            for (int ja = 0; ja < TAPS; ++ja)
+            for (int p = 0; p < RP; ++p)
 #pragma unroll
-                for (int c = 0; c < CP; ++c) {
-                    col[ja * PA * PA + 2 * c] += lane_of(acc[ja][c], 0);
-                    col[ja * PA * PA + 2 * c + 1] += lane_of(acc[ja][c], 1);
-                    acc[ja][c] = 0ull;
+                for (int c = 0; c < CPL; ++c) {
+                    col[(2 * p) * PA * PA + c] += lane_of(acc[p][c], 0);
+                    col[(2 * p + 1) * PA * PA + c] += lane_of(acc[p][c], 1);
+                    acc[p][c] = 0ull;
                 }
         }
     };
@@ -155,8 +153,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
                 const unsigned long long T1 = pack2(fmaf(2.f, f[1], -1.f), fmaf(2.f, f[1], -1.f));
                 const unsigned long long T2 = pack2(fmaf(2.f, f[2], -1.f), fmaf(2.f, f[2], -1.f));
                 const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
-                unsigned long long t0[TAPS];
-                float t1[TAPS], t2[TAPS];
+                float t0[TAPS], t1[TAPS], t2[TAPS];
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
                     unsigned long long h0 = pc[q * kPolyCoef + kPolyCoef - 1], h1 = h0, h2 = h0;
@@ -169,26 +166,26 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
                     }
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        const float v0 = lane_of(h0, u);
-                        t0[2 * q + u] = pack2(v0, v0);
+                        t0[2 * q + u] = lane_of(h0, u);
                         t1[2 * q + u] = lane_of(h1, u) * xv;
                         t2[2 * q + u] = lane_of(h2, u);
                     }
                 }
                 // 16-byte stores of this lane's rows
-                ulonglong2 *r0 = reinterpret_cast<ulonglong2 *>(w0d + lane * R0);
-#pragma unroll
-                for (int j = 0; j < TAPS / 2; ++j) r0[j] = make_ulonglong2(t0[2 * j], t0[2 * j + 1]);
+                float4 *r0 = reinterpret_cast<float4 *>(w0s + lane * R1);
                 float4 *r1 = reinterpret_cast<float4 *>(w1s + lane * R1);
                 float4 *r2 = reinterpret_cast<float4 *>(w2s + lane * R1);
 #pragma unroll
                 for (int j = 0; j < (TAPS + 3) / 4; ++j) {
-                    float v1[4], v2[4];
+                    float v0[4], v1[4], v2[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        v1[u] = 4 * j + u < TAPS ? t1[(4 * j + u) % TAPS] : 0.f;
-                        v2[u] = 4 * j + u < TAPS ? t2[(4 * j + u) % TAPS] : 0.f;
+                        const bool in = 4 * j + u < TAPS;
+                        v0[u] = in ? t0[(4 * j + u) % TAPS] : 0.f;
+                        v1[u] = in ? t1[(4 * j + u) % TAPS] : 0.f;
+                        v2[u] = in ? t2[(4 * j + u) % TAPS] : 0.f;
                     }
+                    r0[j] = make_float4(v0[0], v0[1], v0[2], v0[3]);
                     r1[j] = make_float4(v1[0], v1[1], v1[2], v1[3]);
                     r2[j] = make_float4(v2[0], v2[1], v2[2], v2[3]);
                 }
@@ -209,21 +206,27 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32) spread3_warp(SpreadW
 #pragma unroll 2
                     for (int q = i; q < j; ++q) {
                         const float w1v = w1s[q * R1 + jb];
-                        const unsigned long long w1p = pack2(w1v, w1v);
                         const float *r2 = w2s + q * R1 + hseg * CPL;
-                        unsigned long long coef[CP];
+                        unsigned long long coef[CPL];
 #pragma unroll
-                        for (int c = 0; c < CP; ++c)
-                            coef[c] = fmul2(w1p, *reinterpret_cast<const unsigned long long *>(r2 + 2 * c));
-                        const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(w0d + q * R0);
+                        for (int c = 0; c < CPL; ++c) {
+                            const float cv = w1v * r2[c];
+                            coef[c] = pack2(cv, cv);
+                        }
+                        const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(w0s + q * R1);
 #pragma unroll
-                        for (int ja2 = 0; ja2 < TAPS / 2; ++ja2) {
-                            const ulonglong2 wv = r0[ja2];
+                        for (int p2 = 0; p2 < RP / 2; ++p2) {
+                            const ulonglong2 wv = r0[p2];        // (w0[4 p2], w0[4 p2 + 1]), (w0[4 p2 + 2], w0[4 p2 + 3])
 #pragma unroll
-                            for (int c = 0; c < CP; ++c) {
-                                acc[2 * ja2][c] = ffma2(coef[c], wv.x, acc[2 * ja2][c]);
-                                acc[2 * ja2 + 1][c] = ffma2(coef[c], wv.y, acc[2 * ja2 + 1][c]);
+                            for (int c = 0; c < CPL; ++c) {
+                                acc[2 * p2][c] = ffma2(coef[c], wv.x, acc[2 * p2][c]);
+                                acc[2 * p2 + 1][c] = ffma2(coef[c], wv.y, acc[2 * p2 + 1][c]);
                             }
+                        }
+                        if (RP % 2) {
+                            const unsigned long long wv = reinterpret_cast<const unsigned long long *>(w0s + q * R1)[RP - 1];
+#pragma unroll
+                            for (int c = 0; c < CPL; ++c) acc[RP - 1][c] = ffma2(coef[c], wv, acc[RP - 1][c]);
                         }
                     }
                 }

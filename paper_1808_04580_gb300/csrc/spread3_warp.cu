@@ -4,9 +4,10 @@
 //
 // The plan sorts the nodes of every tile by cell, so the nodes of one cell
 // are contiguous; they share the whole (2M)^3 support.  A CTA of NG warps
-// takes one chunk of one tile (TE^3 cells); warp g takes the chunk's slices
-// of 32 nodes g, g + NG, ...  and owns a copy of the tile plus halo
-// (PA = TE + 2M - 1 per axis) in shared memory.
+// takes one chunk of one tile (TE^3 cells); every warp owns a copy of the
+// tile plus halo (PA = TE + 2M - 1 per axis) in shared memory.  Warp g takes
+// the g-th quarter of the chunk's nodes, in slices of 32, so the warps of a
+// CTA finish a chunk together.
 //
 // Per slice, lane i stages node i: its tile-local cell, the 3 x 2M window
 // taps (the plan's per-tap polynomials, Horner in t = 2f - 1 with two taps
@@ -123,16 +124,18 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
         int cur = -1;
-        // this lane's node of the warp's next slice, loaded one slice ahead
-        int base = w.start + g * S;
+        // this warp's share of the chunk; this lane's node of the next slice, loaded one slice ahead
+        const int share = (w.count + NG - 1) / NG;
+        int base = w.start + g * share;
+        const int gend = min(wend, base + share);
         PointF pn = {{0.f, 0.f, 0.f}, 0};
         float xn = 0.f;
-        if (base + lane < wend) {
+        if (base + lane < gend) {
             pn = a.pts[base + lane];
             xn = a.xs[base + lane];
         }
-        for (; base < wend; base += NG * S) {
-            const int cnt = min(S, wend - base);
+        for (; base < gend; base += S) {
+            const int cnt = min(S, gend - base);
             const bool valid = lane < cnt;
             int o = 0;
             {
@@ -144,8 +147,8 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     f[ax] = valid ? pn.f[ax] : 0.f;
                 }
                 const float xv = xn;
-                const int kn = base + NG * S + lane;
-                if (kn < wend) {
+                const int kn = base + S + lane;
+                if (kn < gend) {
                     pn = a.pts[kn];
                     xn = a.xs[kn];
                 }

@@ -13,7 +13,7 @@
 // taps (the plan's per-tap polynomials, Horner in t = 2f - 1 with two taps
 // per fma.rn.f32x2; x~ folded into the axis-1 taps), written once per node.
 // A warp ballot marks the cell runs.  For the accumulation, LPB lanes share
-// a support row jb of axis 1 and each owns CPL support columns jc of axis 2;
+// a support row jb of axis 1 and each owns CPL interleaved columns jc of axis 2;
 // a lane keeps 2M x CPL accumulators as pairs of adjacent rows ja and adds,
 // per node, (c, c) * (w0[ja], w0[ja + 1]) with c = w1[jb] w2[jc], one
 // fma.rn.f32x2 per pair and column.  Every multiply-add lands in the
@@ -65,7 +65,7 @@ struct WarpGeom {
     static constexpr int W_BYTES = S * R1 * 4;
     static constexpr int WARP_BYTES = TILE * 4 + 3 * W_BYTES;
     static constexpr int SMEM = NG * WARP_BYTES;
-    static_assert(TAPS * LPB == LANES && LANES <= 32, "lane layout");
+    static_assert(TAPS * LPB == LANES && LANES <= 32 && CPL % 2 == 0, "lane layout");
     static_assert(WARP_BYTES % 16 == 0, "16-byte aligned per-warp areas");
 };
 
@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
 
     const bool acc_lane = lane < G::LANES;
     const int jb = acc_lane ? lane / G::LPB : 0;
-    const int hseg = acc_lane ? lane - jb * G::LPB : 0;          // which CPL columns: jc = hseg * CPL + c
+    // columns jc = c * LPB + hseg, c < CPL: interleaved, so that in a flush the
+    // 24 lanes (m = 6) address 24 different shared-memory banks
+    const int hseg = acc_lane ? lane - jb * G::LPB : 0;
     for (int e = threadIdx.x; e < M * kPolyCoef; e += NG * 32) {
         const int q = e / kPolyCoef, k = e - q * kPolyCoef;
         polys[q][k] = make_float2(a.poly[2 * q][k], a.poly[2 * q + 1][k]);
@@ -106,13 +108,13 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         __syncwarp();
         if (acc_lane) {
             const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
-            float *col = tile + (s0 * PA + s1 + jb) * PA + s2 + hseg * CPL;
+            float *col = tile + (s0 * PA + s1 + jb) * PA + s2 + hseg;
 #pragma unroll
             for (int p = 0; p < RP; ++p)
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
-                    col[(2 * p) * PA * PA + c] += lane_of(acc[p][c], 0);
-                    col[(2 * p + 1) * PA * PA + c] += lane_of(acc[p][c], 1);
+                    col[(2 * p) * PA * PA + c * G::LPB] += lane_of(acc[p][c], 0);
+                    col[(2 * p + 1) * PA * PA + c * G::LPB] += lane_of(acc[p][c], 1);
                     acc[p][c] = 0ull;
                 }
         }
@@ -186,7 +188,9 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                         const bool in = 4 * j + u < TAPS;
                         v0[u] = in ? t0[(4 * j + u) % TAPS] : 0.f;
                         v1[u] = in ? t1[(4 * j + u) % TAPS] : 0.f;
-                        v2[u] = in ? t2[(4 * j + u) % TAPS] : 0.f;
+                        // axis 2 de-interleaved: position h CPL + c holds tap c LPB + h
+                        const int r = (4 * j + u) % TAPS;
+                        v2[u] = in ? t2[(r % CPL) * G::LPB + r / CPL] : 0.f;
                     }
                     r0[j] = make_float4(v0[0], v0[1], v0[2], v0[3]);
                     r1[j] = make_float4(v1[0], v1[1], v1[2], v1[3]);
@@ -209,12 +213,14 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
 #pragma unroll 2
                     for (int q = i; q < j; ++q) {
                         const float w1v = w1s[q * R1 + jb];
-                        const float *r2 = w2s + q * R1 + hseg * CPL;
+                        const float2 *r2 = reinterpret_cast<const float2 *>(w2s + q * R1 + hseg * CPL);
                         unsigned long long coef[CPL];
 #pragma unroll
-                        for (int c = 0; c < CPL; ++c) {
-                            const float cv = w1v * r2[c];
-                            coef[c] = pack2(cv, cv);
+                        for (int c2 = 0; c2 < CPL / 2; ++c2) {
+                            const float2 v = r2[c2];
+                            const float c0 = w1v * v.x, c1 = w1v * v.y;
+                            coef[2 * c2] = pack2(c0, c0);
+                            coef[2 * c2 + 1] = pack2(c1, c1);
                         }
                         const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(w0s + q * R1);
 #pragma unroll

@@ -49,6 +49,7 @@ struct GatherTCArgs {
     const float *g;   // layout [x2][x1][x0]
     int op;
     int *error_flag;
+    unsigned *counter;    // next work item, shared by all CTAs
     float poly[2 * kMaxM][kPolyCoef];   // window by taps, as in the plan
 };
 
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(16) float2 polys[M][kPolyCoef];   // (tap 2q, tap 2q+1) coefficients
+    __shared__ unsigned next_item;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     for (int e = tid; e < M * kPolyCoef; e += 128) {
@@ -118,7 +120,12 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     // instruction descriptor: D f32, A/B tf32, both K-major, N, M = 128
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
 
-    for (int64_t it = blockIdx.x; it < a.nitems && !failed; it += gridDim.x) {
+    while (!failed) {
+        // the CTA's next work item (largest first: the plan sorts them by size)
+        if (tid == 0) next_item = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int64_t it = next_item;
+        if (it >= a.nitems) break;
         const WorkItem w = a.items[it];
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
@@ -383,6 +390,7 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
     a.g = reinterpret_cast<const float *>(P.g);
     a.op = op;
     a.error_flag = P.error_flag;
+    a.counter = P.work_counter + 1;
     for (int j = 0; j < 2 * kMaxM; ++j)
         for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
     switch (P.m) {

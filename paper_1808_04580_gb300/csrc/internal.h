@@ -85,6 +85,7 @@ struct Plan {
     void *twiddle = nullptr;    // e^{-2 pi i q / ngrid}, q < ngrid/2 (complex, FFT type)
     double *scratch = nullptr;  // small device scalars (reductions, fixed-point scale)
     int *error_flag = nullptr;  // set by a kernel whose bounded wait ran out
+    unsigned *work_counter = nullptr;   // [0] spread, [1] gather: next work item (reset per column)
     int num_sms = 0;
 
     // stage timing: 5 events per timed column (before prep, spread, fft, gather, after)

@@ -465,6 +465,7 @@ static void free_plan(Plan *P) {
     cudaFree(P->twiddle);
     cudaFree(P->scratch);
     cudaFree(P->error_flag);
+    cudaFree(P->work_counter);
     delete P;
 }
 
@@ -527,6 +528,7 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
     NFL_STATUS_TRY(cudaMalloc(&P->scratch, 64 * sizeof(double)));
     NFL_STATUS_TRY(cudaMalloc(&P->error_flag, sizeof(int)));
+    NFL_STATUS_TRY(cudaMalloc(&P->work_counter, 2 * sizeof(unsigned)));
     NFL_STATUS_TRY(cudaMemsetAsync(P->error_flag, 0, sizeof(int), stream));
 
     const int rblocks = 1024;
@@ -646,6 +648,18 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
     cleanup();
     if (ce != cudaSuccess) return NFL_ERR_CUDA;
+    {
+        // largest chunks first: the kernels that take items from a shared counter
+        // then end with small ones (longest-processing-time order)
+        std::vector<WorkItem> h(P->nitems);
+        if (P->nitems > 0) {
+            ce = cudaMemcpy(h.data(), P->items, P->nitems * sizeof(WorkItem), cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) return NFL_ERR_CUDA;
+            std::stable_sort(h.begin(), h.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
+            ce = cudaMemcpy(P->items, h.data(), P->nitems * sizeof(WorkItem), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) return NFL_ERR_CUDA;
+        }
+    }
 
     // FFT buffers, twiddles, multiplier
     const bool fd = fft_is_double(prec);

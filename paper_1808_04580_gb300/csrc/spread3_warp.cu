@@ -44,6 +44,7 @@ struct SpreadWarpArgs {
     int ngrid;
     void *grid;
     const double *abs_sum;
+    unsigned *counter;              // next work item, shared by all CTAs
     float poly[2 * kMaxM][kPolyCoef];
 };
 
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
     float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W_BYTES);       // [S][R1]
     float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + 2 * G::W_BYTES);   // [S][R1]
     __shared__ __align__(16) float2 polys[M][kPolyCoef];
+    __shared__ unsigned next_item;
 
     const bool acc_lane = lane < G::LANES;
     const int jb = acc_lane ? lane / G::LPB : 0;
@@ -120,7 +122,12 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         }
     };
 
-    for (int64_t it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    for (;;) {
+        // the CTA's next work item (largest first: the plan sorts them by size)
+        if (threadIdx.x == 0) next_item = atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int64_t it = next_item;
+        if (it >= a.nitems) break;
         const WorkItem w = a.items[it];
         const int wend = w.start + w.count;
         int tc[3];
@@ -310,6 +317,7 @@ cudaError_t launch_spread3_warp(Plan &P) {
     a.ngrid = P.ngrid;
     a.grid = P.grid;
     a.abs_sum = P.scratch;
+    a.counter = P.work_counter;
     for (int j = 0; j < 2 * kMaxM; ++j)
         for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
     const bool fixed = P.prec == NFL_PREC_FP32C;

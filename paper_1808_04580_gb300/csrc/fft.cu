@@ -62,34 +62,62 @@ __device__ __forceinline__ double fixed_point_unscale(double abs_sum) {
     return ldexp(1.0, -k);
 }
 
-// Radix-2 Stockham autosort FFT on nl lines of length n held in x (scratch y).
-// Stage with half-length l and stride s (l s = n/2):  for j < l, k < s
-//   Y[k + 2 j s]     = X[k + j s] + X[k + j s + n/2]
-//   Y[k + 2 j s + s] = (X[k + j s] - X[k + j s + n/2]) w^{j s},  w = e^{-+2 pi i / n}.
+// Stockham autosort FFT on nl lines of length n (a power of two) held in x
+// (scratch y): radix-4 stages while they fit, then one radix-2 stage if log2 n
+// is odd.  Stage with stride s (the product of the earlier radices), radix R,
+// for j < n / (R s), k < s, q < R:
+//   Y[k + R j s + q s] = w^{q j s} sum_{r < R} X[k + j s + r n / R] e^{-+2 pi i r q / R},
+// w = e^{-+2 pi i / n}; the table holds w^m for m < n/2 and w^{m + n/2} = -w^m.
+template <typename C>
+__device__ __forceinline__ C twiddle(const C *tw, int m, int half, bool inverse) {
+    C w = m < half ? tw[m] : C{-tw[m - half].x, -tw[m - half].y};
+    if (inverse) w.y = -w.y;
+    return w;
+}
+
 template <typename C>
 __device__ C *stockham(C *x, C *y, int nl, int n, int logn, const C *tw, bool inverse) {
-    const int half = n >> 1;                 // n is a power of two: index math by shifts and masks
-    int s = 1;
-    for (int stage = 0; stage < logn; ++stage) {
-        for (int e = threadIdx.x; e < nl * half; e += blockDim.x) {
-            const int line = e >> (logn - 1);
-            const int bidx = e & (half - 1);
-            const int j = bidx >> stage;
-            const int k = bidx & (s - 1);
-            const C *X = x + line * n;
-            C *Y = y + line * n;
-            const C c0 = X[k + j * s];
-            const C c1 = X[k + j * s + half];
-            C w = tw[j * s];
-            if (inverse) w.y = -w.y;
-            Y[k + 2 * j * s] = cadd(c0, c1);
-            Y[k + 2 * j * s + s] = cmul(csub(c0, c1), w);
+    const int half = n >> 1, quarter = n >> 2;
+    int s = 1, logs = 0;
+    for (; logs + 2 <= logn; logs += 2, s <<= 2) {
+        for (int e = threadIdx.x; e < nl * quarter; e += blockDim.x) {
+            const int line = e >> (logn - 2);
+            const int b = e & (quarter - 1);
+            const int j = b >> logs;
+            const int k = b & (s - 1);
+            const C *X = x + line * n + k + j * s;
+            C *Y = y + line * n + k + 4 * j * s;
+            const C a0 = X[0], a1 = X[quarter], a2 = X[half], a3 = X[half + quarter];
+            const C b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), d = csub(a1, a3);
+            // (a1 - a3) e^{-+i pi / 2}: -i d forward, +i d inverse
+            const C b3 = inverse ? C{-d.y, d.x} : C{d.y, -d.x};
+            const int t = j * s;
+            Y[0] = cadd(b0, b2);
+            Y[s] = cmul(cadd(b1, b3), twiddle(tw, t, half, inverse));
+            Y[2 * s] = cmul(csub(b0, b2), twiddle(tw, 2 * t, half, inverse));
+            Y[3 * s] = cmul(csub(b1, b3), twiddle(tw, 3 * t, half, inverse));
         }
         __syncthreads();
-        C *t = x;
+        C *tmp = x;
         x = y;
-        y = t;
-        s <<= 1;
+        y = tmp;
+    }
+    if (logs < logn) {
+        for (int e = threadIdx.x; e < nl * half; e += blockDim.x) {
+            const int line = e >> (logn - 1);
+            const int b = e & (half - 1);
+            const int j = b >> logs;
+            const int k = b & (s - 1);
+            const C *X = x + line * n + k + j * s;
+            C *Y = y + line * n + k + 2 * j * s;
+            const C c0 = X[0], c1 = X[half];
+            Y[0] = cadd(c0, c1);
+            Y[s] = cmul(csub(c0, c1), twiddle(tw, j * s, half, inverse));
+        }
+        __syncthreads();
+        C *tmp = x;
+        x = y;
+        y = tmp;
     }
     return x;
 }

@@ -28,6 +28,8 @@
 // 64-bit fixed point (scale 2^k from sum |x~|, so nothing can overflow) and
 // adds it with an integer atomic.  So FP32C sums at most 2048 / NG nodes of a
 // tile position in FP32 (512 for NG = 4) before the exact integer part.
+#include <type_traits>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -100,10 +102,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
     __syncthreads();
 
     unsigned long long acc[RP][CPL];              // (ja, ja + 1) pairs for each column jc
-#pragma unroll
-    for (int p = 0; p < RP; ++p)
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) acc[p][c] = 0ull;
+    bool fresh = true;                            // the next node starts the accumulators
 
     // add the accumulators of cell o to this warp's tile copy
     auto flush = [&](int o) {
@@ -117,8 +116,44 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                 for (int c = 0; c < CPL; ++c) {
                     col[(2 * p) * PA * PA + c * G::LPB] += lane_of(acc[p][c], 0);
                     col[(2 * p + 1) * PA * PA + c * G::LPB] += lane_of(acc[p][c], 1);
-                    acc[p][c] = 0ull;
                 }
+        }
+        fresh = true;
+    };
+
+    // one node's taps into the accumulators: (c, c) * (w0[ja], w0[ja + 1]), c = w1[jb] w2[jc];
+    // INIT sets them (first node after a flush), otherwise adds
+    auto node = [&](int q, auto init) {
+        constexpr bool INIT = decltype(init)::value;
+        const float w1v = w1s[q * R1 + jb];
+        const float2 *r2 = reinterpret_cast<const float2 *>(w2s + q * R1 + hseg * CPL);
+        unsigned long long coef[CPL];
+#pragma unroll
+        for (int c2 = 0; c2 < CPL / 2; ++c2) {
+            const float2 v = r2[c2];
+            const float c0 = w1v * v.x, c1 = w1v * v.y;
+            coef[2 * c2] = pack2(c0, c0);
+            coef[2 * c2 + 1] = pack2(c1, c1);
+        }
+        const unsigned long long *r0 = reinterpret_cast<const unsigned long long *>(w0s + q * R1);
+#pragma unroll
+        for (int p2 = 0; p2 < (RP + 1) / 2; ++p2) {
+            unsigned long long wv[2];
+            if (2 * p2 + 1 < RP) {
+                const ulonglong2 w2v = reinterpret_cast<const ulonglong2 *>(r0)[p2];
+                wv[0] = w2v.x;
+                wv[1] = w2v.y;
+            } else {
+                wv[0] = r0[2 * p2];
+                wv[1] = 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (2 * p2 + u >= RP) continue;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+                    acc[2 * p2 + u][c] = INIT ? fmul2(coef[c], wv[u]) : ffma2(coef[c], wv[u], acc[2 * p2 + u][c]);
+            }
         }
     };
 
@@ -217,35 +252,12 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     cur = oi;
                 }
                 if (acc_lane) {
+                    int q = i;
+                    if (fresh) node(q++, std::true_type{});
 #pragma unroll 2
-                    for (int q = i; q < j; ++q) {
-                        const float w1v = w1s[q * R1 + jb];
-                        const float2 *r2 = reinterpret_cast<const float2 *>(w2s + q * R1 + hseg * CPL);
-                        unsigned long long coef[CPL];
-#pragma unroll
-                        for (int c2 = 0; c2 < CPL / 2; ++c2) {
-                            const float2 v = r2[c2];
-                            const float c0 = w1v * v.x, c1 = w1v * v.y;
-                            coef[2 * c2] = pack2(c0, c0);
-                            coef[2 * c2 + 1] = pack2(c1, c1);
-                        }
-                        const ulonglong2 *r0 = reinterpret_cast<const ulonglong2 *>(w0s + q * R1);
-#pragma unroll
-                        for (int p2 = 0; p2 < RP / 2; ++p2) {
-                            const ulonglong2 wv = r0[p2];        // (w0[4 p2], w0[4 p2 + 1]), (w0[4 p2 + 2], w0[4 p2 + 3])
-#pragma unroll
-                            for (int c = 0; c < CPL; ++c) {
-                                acc[2 * p2][c] = ffma2(coef[c], wv.x, acc[2 * p2][c]);
-                                acc[2 * p2 + 1][c] = ffma2(coef[c], wv.y, acc[2 * p2 + 1][c]);
-                            }
-                        }
-                        if (RP % 2) {
-                            const unsigned long long wv = reinterpret_cast<const unsigned long long *>(w0s + q * R1)[RP - 1];
-#pragma unroll
-                            for (int c = 0; c < CPL; ++c) acc[RP - 1][c] = ffma2(coef[c], wv, acc[RP - 1][c]);
-                        }
-                    }
+                    for (; q < j; ++q) node(q, std::false_type{});
                 }
+                fresh = false;
                 i = j;
             }
             __syncwarp();                         // the next slice overwrites the staged taps
@@ -253,30 +265,40 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         if (cur >= 0) flush(cur);
         __syncthreads();
 
-        // sum the tile copies -> global grid (c fastest, matching the grid's x2 axis), clear them
-        for (int e = threadIdx.x; e < PA3; e += NG * 32) {
-            float v = 0.f;
+        // sum the tile copies -> global grid (c fastest, matching the grid's x2 axis), clear
+        // them; four consecutive positions per thread and 16-byte shared accesses
+        for (int e4 = threadIdx.x; e4 < G::TILE / 4; e4 += NG * 32) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int gg = 0; gg < NG; ++gg) {
-                float *t = reinterpret_cast<float *>(smem_raw + gg * G::WARP_BYTES);
-                v += t[e];
-                t[e] = 0.f;
+                float4 *t = reinterpret_cast<float4 *>(smem_raw + gg * G::WARP_BYTES) + e4;
+                const float4 tv = *t;
+                v.x += tv.x;
+                v.y += tv.y;
+                v.z += tv.z;
+                v.w += tv.w;
+                *t = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            if (v == 0.f) continue;
-            const int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
-            int p0 = tc[0] * TE - (M - 1) + q0;
-            int p1 = tc[1] * TE - (M - 1) + q1;
-            int p2 = tc[2] * TE - (M - 1) + q2;
-            if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-            if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-            if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-            if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
-            const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
-            if (FIXED)
-                atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
-                          (unsigned long long)to_fixed(v * fscale));
-            else
-                atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * e4 + u;
+                if (vv[u] == 0.f || e >= PA3) continue;
+                const int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
+                int p0 = tc[0] * TE - (M - 1) + q0;
+                int p1 = tc[1] * TE - (M - 1) + q1;
+                int p2 = tc[2] * TE - (M - 1) + q2;
+                if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+                if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+                if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
+                const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+                if (FIXED)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
+                              (unsigned long long)to_fixed(vv[u] * fscale));
+                else
+                    atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, vv[u]);
+            }
         }
         __syncthreads();
     }

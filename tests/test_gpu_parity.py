@@ -103,17 +103,43 @@ def test_mixed_precision_forms(prec, tol):
     assert plan.info()["device_error"] == 0
 
 
-# every 3-D tile shape of the column spread and the tensor-core interpolation
+# every 3-D tile shape of the spread kernels (warp-slice: m = 2, 3, 4, 6; cell-run:
+# m = 7, 8; shared-tile: m = 5) and of the tensor-core interpolation, both mixed forms
+@pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
 @pytest.mark.parametrize("m,N", [(2, 16), (3, 16), (4, 32), (6, 32), (7, 32), (5, 32), (8, 32)])
-def test_fp32c_each_window_size(m, N):
+def test_mixed_forms_each_window_size(m, N, prec, tol):
     n = 2600
     v = _cloud("clusters", n, 3, seed=30 + m)
     x = workloads.rhs(n, seed=31 + m)
     ref = fastsum.NormalizedFastsum(v, 0.4, N, m, m)
-    plan = Plan(gpu(v), 0.4, N, m, m, -1.0, "fp32c")
+    plan = Plan(gpu(v), 0.4, N, m, m, -1.0, prec)
     y = plan.apply_W(gpu(x)).cpu().numpy()
-    assert rel(y, ref.apply_W(x)) < 2e-6
-    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=2e-6)
+    assert rel(y, ref.apply_W(x)) < tol
+    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)
+    yl = plan.apply_Ls(gpu(x)).cpu().numpy()
+    assert rel(x - yl, x - ref.apply_Ls(x)) < tol
+    assert plan.info()["device_error"] == 0
+
+
+# supports that wrap around the periodic grid (span > 2N), and d = 1, 2, in the mixed forms
+MIXED_EDGE_CASES = [
+    ("normal", 200, 3, 1.0, 8, 4, 4, 0.125),
+    ("normal", 300, 3, 1.0, 8, 2, 2, 0.125),
+    ("normal", 300, 2, 1.0, 8, 6, 2, 0.125),
+    ("normal", 700, 2, 0.5, 32, 3, 3, -1.0),
+    ("normal", 500, 1, 0.3, 64, 5, 5, -1.0),
+]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
+@pytest.mark.parametrize("case", MIXED_EDGE_CASES, ids=lambda c: "n%d-d%d-N%d-m%d" % (c[1], c[2], c[4], c[5]))
+def test_mixed_forms_wrap_and_low_dimensions(case, prec, tol):
+    kind, n, d, sigma, N, m, p, eps_B = case
+    v = _cloud(kind, n, d, seed=40 + n)
+    x = workloads.rhs(n, seed=41 + n)
+    ref = fastsum.NormalizedFastsum(v, sigma, N, m, p, None if eps_B < 0 else eps_B)
+    plan = Plan(gpu(v), sigma, N, m, p, eps_B, prec)
+    assert rel(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x)) < tol
     assert plan.info()["device_error"] == 0
 
 

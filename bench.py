@@ -349,6 +349,7 @@ def main():
                            n * nrhs * 8 // 2**20, n * 16 // 2**20),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "box": info["box"], "work_items": info["work_items"]},
+            "point_rhs_per_s": value * n,
             "stage_ms_per_column": {"prep": stages["prep"] / max(1, stages["columns"]), "spread": spread_ms,
                                     "fft": fft_ms, "gather": gather_ms},
             "fp64_plain": fp64,

@@ -51,7 +51,22 @@ typedef enum {
     NFL_ERR_OUT_OF_MEMORY = 8       /* a device allocation failed                           */
 } nfl_status;
 
-enum { NFL_KERNEL_GAUSSIAN = 0 };
+/* Kernels of Sec. 2 (after eq. (W_gaussian)); r = ||v_j - v_i||, shape parameter s:
+ *   GAUSSIAN             exp(-r^2 / s^2)        K(0) = 1
+ *   LAPLACIAN_RBF        exp(-r / s)            K(0) = 1  (cusp at r = 0: the fast sum
+ *                                                          converges slowly in N)
+ *   MULTIQUADRIC         (r^2 + s^2)^{1/2}      K(0) = s
+ *   INV_MULTIQUADRIC     (r^2 + s^2)^{-1/2}     K(0) = 1/s
+ * Alg. 2 step 2 scales s with the nodes (s~ = rho s); for the multiquadrics
+ * the fast sum's output is then scaled by 1/rho (multiquadric) or rho (inverse
+ * multiquadric), which makes the scaled kernel equal the caller's (reading of
+ * Alg. 2 steps 2, 4, 5, whose printed rule c := c/rho does not). */
+enum {
+    NFL_KERNEL_GAUSSIAN = 0,
+    NFL_KERNEL_LAPLACIAN_RBF = 1,
+    NFL_KERNEL_MULTIQUADRIC = 2,
+    NFL_KERNEL_INV_MULTIQUADRIC = 3
+};
 
 /* Arithmetic of the spread / FFT / gather steps.  Epilogues (-K(0) x,
  * D^{-1/2} scaling, x - A x) and all solver scalars are FP64 in every mode.
@@ -70,7 +85,7 @@ typedef struct {
     int d;                /* dimension 1..3                                    */
     int N, m, p;          /* bandwidth, window cut-off, regularization order   */
     int precision;        /* NFL_PREC_*                                        */
-    double sigma;         /* kernel width in the caller's coordinates          */
+    double sigma;         /* kernel shape parameter in the caller's coordinates */
     double eps_B;         /* regularization width                              */
     double rho;           /* node scale factor (Alg. 2 step 1)                 */
     double sigma_tilde;   /* rho * sigma (Alg. 2 step 2)                       */
@@ -83,20 +98,24 @@ typedef struct {
     int degree_ok;        /* 1 if min_degree > 0 (A, L_s and solvers usable)  */
     int device_error;     /* 1 if a kernel's bounded wait ran out (results of
                              the products since then are unreliable)          */
+    int kernel;           /* NFL_KERNEL_*                                      */
+    double k0;            /* K(0) in the caller's coordinates                  */
+    double out_scale;     /* factor from the scaled fast sum to the caller's   */
 } nfl_info;
 
 /*
  * Alg. 2 steps 1-4 (Sec. 3.1): shift the nodes by their bounding-box
  * midpoint and scale them by rho = (1/4 - eps_B/2) / max_j ||v_j - c||
- * (rho = 1 when all nodes coincide), set sigma~ = rho sigma, compute the
+ * (rho = 1 when all nodes coincide), set sigma~ = rho sigma (the kernel's
+ * shape parameter; see the kernel list above), compute the
  * coefficients b_l of the regularized kernel by the trapezoidal rule
  * (Sec. 3, eq. (b_l::K_RF)) and the degrees d_E = W~_E 1 - K(0) 1.
  *
  *   v         device, n x d row-major FP64 node coordinates (read only; may
  *             be freed after the call returns).
  *   n         >= 1.   d in {1, 2, 3}.
- *   kernel    NFL_KERNEL_GAUSSIAN.
- *   sigma     > 0.
+ *   kernel    NFL_KERNEL_* (above).
+ *   sigma     > 0: the kernel's shape parameter (sigma, or c for the multiquadrics).
  *   N         bandwidth: a power of two in [4, 512] (Fig. tab:fastsum_param).
  *   m         window cut-off, 1 <= m <= 12.
  *   p         regularization smoothness; p <= 0 selects the default p = m.

@@ -1,6 +1,9 @@
 /*
- * O1 row sums in plain C: (W x)_j = sum_{i != j} exp(-||v_j - v_i||^2 / sigma^2) x_i
- * for selected rows j, each over all n sources (Sec. 2, eq. (W_gaussian)).
+ * O1 row sums in plain C: (W x)_j = sum_{i != j} K(v_j - v_i) x_i for selected
+ * rows j, each over all n sources, with the kernels of Sec. 2: kind 0 the
+ * Gaussian exp(-r^2/sigma^2) (eq. (W_gaussian)), 1 the Laplacian RBF
+ * exp(-r/sigma), 2 the multiquadric (r^2 + c^2)^{1/2}, 3 the inverse
+ * multiquadric (r^2 + c^2)^{-1/2}; r = ||v_j - v_i||, c passed as sigma.
  *
  * Test infrastructure (the oracle): only tests/, the smoke check and the
  * CPU-baseline leg of bench.py may load this library.  Plain loops in FP64,
@@ -22,14 +25,22 @@ int oracle_max_threads(void) {
 
 /* v: n x d row-major; x: n x nrhs column-major with leading dimension ldx;
  * rows: nrows indices; out: nrows x nrhs column-major (leading dim nrows). */
-int oracle_gauss_rows(const double *v, int64_t n, int d, double sigma,
-                      const double *x, int64_t nrhs, int64_t ldx,
-                      const int64_t *rows, int64_t nrows, double *out,
-                      int nthreads) {
-    if (n < 0 || d < 1 || sigma <= 0.0 || nrhs < 1 || ldx < n) return 1;
+static double kernel_of(int kind, double dist2, double sigma) {
+    switch (kind) {
+        case 0: return exp(-dist2 / (sigma * sigma));
+        case 1: return exp(-sqrt(dist2) / sigma);
+        case 2: return sqrt(dist2 + sigma * sigma);
+        default: return 1.0 / sqrt(dist2 + sigma * sigma);
+    }
+}
+
+int oracle_kernel_rows(const double *v, int64_t n, int d, int kind, double sigma,
+                       const double *x, int64_t nrhs, int64_t ldx,
+                       const int64_t *rows, int64_t nrows, double *out,
+                       int nthreads) {
+    if (n < 0 || d < 1 || kind < 0 || kind > 3 || sigma <= 0.0 || nrhs < 1 || ldx < n) return 1;
     for (int64_t k = 0; k < nrows; ++k)
         if (rows[k] < 0 || rows[k] >= n) return 1;
-    const double inv_s2 = 1.0 / (sigma * sigma);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -44,7 +55,7 @@ int oracle_gauss_rows(const double *v, int64_t n, int d, double sigma,
                 const double diff = v[j * d + a] - v[i * d + a];
                 dist2 += diff * diff;
             }
-            const double w = exp(-dist2 * inv_s2);
+            const double w = kernel_of(kind, dist2, sigma);
             for (int64_t r = 0; r < nrhs; ++r) out[k + r * nrows] += w * x[i + r * ldx];
         }
     }

@@ -1,9 +1,11 @@
-"""O1, the ground truth: direct FP64 sums with the Gaussian weight matrix.
+"""O1, the ground truth: direct FP64 sums with the kernel weight matrix.
 
 Test infrastructure (the oracle); see the package docstring for who may use it.
 
 Sec. 2, eq. (W_gaussian): W_ji = exp(-||v_j - v_i||^2 / sigma^2) for j != i,
-W_jj = 0.  Degree d_j = sum_i W_ji; D = diag(d); L = D - W;
+W_jj = 0; the other kernels of Sec. 2 (Laplacian RBF exp(-r/sigma), the
+multiquadric (r^2 + c^2)^{1/2} and its inverse, r = ||v_j - v_i||, shape
+parameter in ``sigma``) by name.  Degree d_j = sum_i W_ji; D = diag(d); L = D - W;
 A = D^{-1/2} W D^{-1/2}; L_s = I - A (Sec. 2, eq. (nomlap)).
 Everything is in the original coordinates (no scaling, no shift).
 
@@ -22,42 +24,55 @@ import os
 import numpy as np
 
 
-def weight_matrix(v, sigma):
+def _radial(r2, sigma, kernel):
+    """K from the squared distance, written out for each kernel of Sec. 2."""
+    if kernel == "gaussian":
+        return np.exp(-r2 / sigma ** 2)
+    if kernel == "laplacian_rbf":
+        return np.exp(-np.sqrt(r2) / sigma)
+    if kernel == "multiquadric":
+        return np.sqrt(r2 + sigma ** 2)
+    if kernel == "inverse_multiquadric":
+        return 1.0 / np.sqrt(r2 + sigma ** 2)
+    raise ValueError("unknown kernel %r" % (kernel,))
+
+
+def weight_matrix(v, sigma, kernel="gaussian"):
     """Dense W (n x n), zero diagonal."""
     v = np.atleast_2d(np.asarray(v, dtype=np.float64))
     diff = v[:, None, :] - v[None, :, :]
-    W = np.exp(-(diff ** 2).sum(axis=2) / sigma ** 2)
+    W = _radial((diff ** 2).sum(axis=2), sigma, kernel)
     np.fill_diagonal(W, 0.0)
     return W
 
 
-def degree(v, sigma):
-    return weight_matrix(v, sigma).sum(axis=1)
+def degree(v, sigma, kernel="gaussian"):
+    return weight_matrix(v, sigma, kernel).sum(axis=1)
 
 
-def apply_W(v, sigma, x):
-    return weight_matrix(v, sigma) @ np.asarray(x, dtype=np.float64)
+def apply_W(v, sigma, x, kernel="gaussian"):
+    return weight_matrix(v, sigma, kernel) @ np.asarray(x, dtype=np.float64)
 
 
-def normalized_adjacency(v, sigma):
+def normalized_adjacency(v, sigma, kernel="gaussian"):
     """A = D^{-1/2} W D^{-1/2}."""
-    W = weight_matrix(v, sigma)
+    W = weight_matrix(v, sigma, kernel)
     dinv = 1.0 / np.sqrt(W.sum(axis=1))
     return dinv[:, None] * W * dinv[None, :]
 
 
-def apply_A(v, sigma, x):
-    return normalized_adjacency(v, sigma) @ np.asarray(x, dtype=np.float64)
+def apply_A(v, sigma, x, kernel="gaussian"):
+    return normalized_adjacency(v, sigma, kernel) @ np.asarray(x, dtype=np.float64)
 
 
-def apply_Ls(v, sigma, x):
+def apply_Ls(v, sigma, x, kernel="gaussian"):
     x = np.asarray(x, dtype=np.float64)
-    return x - apply_A(v, sigma, x)
+    return x - apply_A(v, sigma, x, kernel)
 
 
-def laplacian(v, sigma):
+def laplacian(v, sigma, kernel="gaussian"):
     """L = D - W."""
-    W = weight_matrix(v, sigma)
+    W = weight_matrix(v, sigma, kernel)
     return np.diag(W.sum(axis=1)) - W
 
 
@@ -75,9 +90,9 @@ def _lib():
             from . import build as _build
             _build.build()
         lib = ctypes.CDLL(path)
-        lib.oracle_gauss_rows.restype = ctypes.c_int
-        lib.oracle_gauss_rows.argtypes = [
-            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+        lib.oracle_kernel_rows.restype = ctypes.c_int
+        lib.oracle_kernel_rows.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
         lib.oracle_max_threads.restype = ctypes.c_int
@@ -90,7 +105,10 @@ def max_threads():
     return int(_lib().oracle_max_threads())
 
 
-def rows_W(v, sigma, x, rows, nthreads=0):
+_KIND = {"gaussian": 0, "laplacian_rbf": 1, "multiquadric": 2, "inverse_multiquadric": 3}
+
+
+def rows_W(v, sigma, x, rows, nthreads=0, kernel="gaussian"):
     """(W x)_j for j in rows, each summed over all n sources, x (n,) or (n, r)."""
     v = np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
     n, d = v.shape
@@ -99,9 +117,9 @@ def rows_W(v, sigma, x, rows, nthreads=0):
     X = np.asfortranarray(x.reshape(n, -1))
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     out = np.zeros((rows.size, X.shape[1]), dtype=np.float64, order="F")
-    rc = _lib().oracle_gauss_rows(
-        v.ctypes.data, n, d, float(sigma), X.ctypes.data, X.shape[1], n,
+    rc = _lib().oracle_kernel_rows(
+        v.ctypes.data, n, d, _KIND[kernel], float(sigma), X.ctypes.data, X.shape[1], n,
         rows.ctypes.data, rows.size, out.ctypes.data, int(nthreads))
     if rc != 0:
-        raise ValueError("oracle_gauss_rows: bad arguments")
+        raise ValueError("oracle_kernel_rows: bad arguments")
     return out[:, 0] if squeeze else out

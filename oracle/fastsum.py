@@ -11,7 +11,8 @@ and f_RF(v_j) ~ (W~ x)_j with W~ = W + K(0) I (Sec. 3, eq. (nfftWtilde_x)).
 
 Alg. 2 (Sec. 3.1), steps 1-4 once per setup:
   step 1  rho with ||rho v_j|| <= 1/4 - eps_B/2, v_j := rho v_j
-  step 2  sigma := rho sigma (Gaussian)
+  step 2  sigma := rho sigma (Gaussian, Laplacian RBF); for the multiquadrics
+          see the reading below
   step 3  control parameters (N, m, p, eps_B; defaults p = m, eps_B = p/N,
           Fig. tab:fastsum_param) and b_l by eq. (b_l::K_RF)
   step 4  D_E = diag(W~_E 1 - K(0) 1)
@@ -28,6 +29,13 @@ Readings:
     product for real x is its real part.  The real part of a Hermitian form
     is symmetric, so the resulting operator is exactly symmetric.
   * L_s x = x - A x (Sec. 2, eq. (nomlap)).
+  * Multiquadric kernels (Alg. 2 steps 2, 4, 5): the printed rule "c := c/rho,
+    scale the output by rho (multiquadric) or 1/rho (inverse multiquadric)"
+    does not reproduce the kernel in the scaled coordinates.  With
+    v~ = rho v, (||v~_j - v~_i||^2 + (rho c)^2)^(+-1/2) = rho^(+-1) K(v_j - v_i),
+    so this oracle uses c~ = rho c and scales Alg. 1's output by 1/rho
+    (multiquadric) or rho (inverse multiquadric); the test against the
+    direct sum pins this reading, and shows that the printed rule misses it.
 
 Pins: O3 against O2 at m = 8 (~1e-13 relative), O2 against the direct sum
 O1 for parameters where the kernel error is tiny, the a-priori bound of
@@ -64,30 +72,35 @@ def trig_polynomial_sum(vt, x, bhat, N):
 
 
 class NormalizedFastsum:
-    """Alg. 2 for the Gaussian kernel: setup (steps 1-4) and products (step 5)."""
+    """Alg. 2: setup (steps 1-4) and products (step 5) for the kernels of Sec. 2."""
 
-    K0 = 1.0  # K(0) for the Gaussian
-
-    def __init__(self, v, sigma, N, m, p=None, eps_B=None, alpha=2):
+    def __init__(self, v, sigma, N, m, p=None, eps_B=None, alpha=2, kernel="gaussian"):
         if N % 2:
             raise ValueError("N must be even")
+        if kernel not in _kernel.KERNELS:
+            raise ValueError("unknown kernel %r" % (kernel,))
+        self.kernel = kernel
         self.N, self.m, self.alpha = int(N), int(m), int(alpha)
         self.p = int(m if p is None else p)
         self.eps_B = float(self.p / self.N if eps_B is None else eps_B)
         self.vt, self.rho, self.center = scale_nodes(v, self.eps_B)       # step 1
         self.sigma = float(sigma)
         self.sigma_t = self.rho * self.sigma                               # step 2
+        # output scale of Alg. 1 back to the original coordinates, and K(0) there
+        self.out_scale = {"multiquadric": 1.0 / self.rho,
+                          "inverse_multiquadric": self.rho}.get(kernel, 1.0)
+        self.K0 = float(_kernel.radial(0.0, self.sigma, kernel))
         self.d = self.vt.shape[1]
         self.bhat = _kernel.fourier_coefficients(                          # step 3
-            self.N, self.d, self.sigma_t, self.eps_B, self.p)
+            self.N, self.d, self.sigma_t, self.eps_B, self.p, kernel)
         ones = np.ones(self.vt.shape[0])
         self.degree = self.apply_Wtilde(ones) - self.K0 * ones             # step 4
         with np.errstate(divide="ignore", invalid="ignore"):
             self.dinv = 1.0 / np.sqrt(self.degree)
 
     def apply_Wtilde(self, x):
-        """W~_E x, the real part of Alg. 1's output."""
-        return fastsum(self.vt, x, self.bhat, self.N, self.m, self.alpha).real
+        """W~_E x, the real part of Alg. 1's output in the original coordinates."""
+        return self.out_scale * fastsum(self.vt, x, self.bhat, self.N, self.m, self.alpha).real
 
     def apply_W(self, x):
         """W_E x = W~_E x - K(0) x (Sec. 3, the diagonal identity)."""
@@ -107,4 +120,4 @@ class NormalizedFastsum:
     def apply_W_exact_trig(self, x):
         """O2: W with K replaced by Re K_RF exactly (no window error)."""
         x = np.asarray(x, dtype=np.float64)
-        return trig_polynomial_sum(self.vt, x, self.bhat, self.N).real - self.K0 * x
+        return self.out_scale * trig_polynomial_sum(self.vt, x, self.bhat, self.N).real - self.K0 * x

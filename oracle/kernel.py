@@ -28,6 +28,12 @@ and even; sum_l b_l = K_R(0); K_RF interpolates K_R at the grid nodes j/N;
 b_l against the closed-form Fourier transform of the Gaussian for small sigma.
 The exact choice of T_B is a reading: "parity unpinned" for T_B's values in
 the shell beyond its defining end conditions.
+
+Other kernels (Sec. 2, after eq. (W_gaussian); used by Alg. 2 steps 2, 4, 5):
+the Laplacian RBF exp(-||y||/sigma), the multiquadric (||y||^2 + c^2)^{1/2}
+and the inverse multiquadric (||y||^2 + c^2)^{-1/2}.  Every function below
+takes the kernel by name (default "gaussian") and its shape parameter
+(sigma, or c for the two multiquadrics) in the ``sigma`` argument.
 """
 import math
 
@@ -58,7 +64,57 @@ def gaussian_derivative(r, sigma, k):
     return (-1.0 / sigma) ** k * hk * np.exp(-x * x)
 
 
-def boundary_polynomial(sigma, eps_B, p):
+KERNELS = ("gaussian", "laplacian_rbf", "multiquadric", "inverse_multiquadric")
+
+
+def radial(r, sigma, kind="gaussian"):
+    """K as a function of r = ||y|| for the kernels of Sec. 2."""
+    r = np.asarray(r, dtype=np.float64)
+    if kind == "gaussian":
+        return gaussian(r, sigma)
+    if kind == "laplacian_rbf":
+        return np.exp(-r / sigma)
+    if kind == "multiquadric":
+        return np.sqrt(r * r + sigma * sigma)
+    if kind == "inverse_multiquadric":
+        return 1.0 / np.sqrt(r * r + sigma * sigma)
+    raise ValueError("unknown kernel %r" % (kind,))
+
+
+def _falling(alpha, j):
+    """alpha (alpha - 1) ... (alpha - j + 1)."""
+    out = 1.0
+    for t in range(j):
+        out *= alpha - t
+    return out
+
+
+def radial_derivative(r, sigma, k, kind="gaussian"):
+    """k-th derivative in r of the radial kernel.
+
+    Laplacian RBF: (-1/sigma)^k exp(-r/sigma).  Multiquadrics: with
+    r^2 + c^2 = (r - ic)(r + ic) and alpha = +-1/2, the product rule gives
+    sum_j binom(k, j) (alpha)_j (r - ic)^(alpha - j) (alpha)_(k-j) (r + ic)^(alpha - k + j)
+    with falling factorials (alpha)_j; the sum is real.
+    """
+    if kind == "gaussian":
+        return gaussian_derivative(r, sigma, k)
+    r = np.asarray(r, dtype=np.float64)
+    if kind == "laplacian_rbf":
+        return (-1.0 / sigma) ** k * np.exp(-r / sigma)
+    if kind in ("multiquadric", "inverse_multiquadric"):
+        alpha = 0.5 if kind == "multiquadric" else -0.5
+        zm = r - 1j * sigma
+        zp = r + 1j * sigma
+        out = np.zeros_like(zm)
+        for j in range(k + 1):
+            out = out + (math.comb(k, j) * _falling(alpha, j) * _falling(alpha, k - j)
+                         * zm ** (alpha - j) * zp ** (alpha - k + j))
+        return out.real
+    raise ValueError("unknown kernel %r" % (kind,))
+
+
+def boundary_polynomial(sigma, eps_B, p, kind="gaussian"):
     """Coefficients c_0..c_{2p-1} of T_B(r) = sum_k c_k s^k, s = (r - a)/eps_B.
 
     a = 1/2 - eps_B.  Left end: T_B^(k)(a) = K^(k)(a), k < p, which fixes
@@ -70,14 +126,14 @@ def boundary_polynomial(sigma, eps_B, p):
     a = 0.5 - eps_B
     c = np.zeros(2 * p)
     for k in range(p):
-        c[k] = gaussian_derivative(a, sigma, k) * eps_B ** k / math.factorial(k)
+        c[k] = radial_derivative(a, sigma, k, kind) * eps_B ** k / math.factorial(k)
     # j-th derivative of s^k at s = 1 is k!/(k-j)! for k >= j, else 0.
     def dpow(k, j):
         return math.factorial(k) / math.factorial(k - j) if k >= j else 0.0
     M = np.zeros((p, p))
     rhs = np.zeros(p)
     for j in range(p):
-        rhs[j] = (float(gaussian(0.5, sigma)) if j == 0 else 0.0) - sum(
+        rhs[j] = (float(radial(0.5, sigma, kind)) if j == 0 else 0.0) - sum(
             c[k] * dpow(k, j) for k in range(p))
         for col, k in enumerate(range(p, 2 * p)):
             M[j, col] = dpow(k, j)
@@ -85,10 +141,10 @@ def boundary_polynomial(sigma, eps_B, p):
     return c
 
 
-def boundary_polynomial_eval(r, sigma, eps_B, p, coeffs=None):
+def boundary_polynomial_eval(r, sigma, eps_B, p, coeffs=None, kind="gaussian"):
     """T_B(r) from the coefficients above (Horner in s = (r - a)/eps_B)."""
     if coeffs is None:
-        coeffs = boundary_polynomial(sigma, eps_B, p)
+        coeffs = boundary_polynomial(sigma, eps_B, p, kind)
     s = (np.asarray(r, dtype=np.float64) - (0.5 - eps_B)) / eps_B
     out = np.zeros_like(s)
     for ck in coeffs[::-1]:
@@ -96,15 +152,15 @@ def boundary_polynomial_eval(r, sigma, eps_B, p, coeffs=None):
     return out
 
 
-def regularized_kernel(r, sigma, eps_B, p):
+def regularized_kernel(r, sigma, eps_B, p, kind="gaussian"):
     """K_R as a function of r = ||y|| (Sec. 3, the K_R ansatz)."""
     r = np.asarray(r, dtype=np.float64)
     if eps_B <= 0.0:
-        return gaussian(np.minimum(r, 0.5), sigma)
+        return radial(np.minimum(r, 0.5), sigma, kind)
     a = 0.5 - eps_B
-    coeffs = boundary_polynomial(sigma, eps_B, p)
-    inner = gaussian(r, sigma)
-    shell = boundary_polynomial_eval(np.minimum(r, 0.5), sigma, eps_B, p, coeffs)
+    coeffs = boundary_polynomial(sigma, eps_B, p, kind)
+    inner = radial(r, sigma, kind)
+    shell = boundary_polynomial_eval(np.minimum(r, 0.5), sigma, eps_B, p, coeffs, kind)
     return np.where(r <= a, inner, shell)
 
 
@@ -113,7 +169,7 @@ def frequency_set(N):
     return np.arange(-N // 2, N // 2)
 
 
-def fourier_coefficients(N, d, sigma, eps_B, p):
+def fourier_coefficients(N, d, sigma, eps_B, p, kind="gaussian"):
     """b_l for l in I_N (Sec. 3, eq. (b_l::K_RF)), returned as a complex array.
 
     Array axis a holds l_a + N/2, i.e. index 0 is l_a = -N/2.  The sum over
@@ -123,7 +179,7 @@ def fourier_coefficients(N, d, sigma, eps_B, p):
     j = frequency_set(N)
     grids = np.meshgrid(*([j / N] * d), indexing="ij")
     r = np.sqrt(sum(g * g for g in grids))
-    samples = regularized_kernel(r, sigma, eps_B, p)       # index j + N/2
+    samples = regularized_kernel(r, sigma, eps_B, p, kind)  # index j + N/2
     samples_mod = np.fft.ifftshift(samples)                # index j mod N
     dft = np.fft.fftn(samples_mod)                         # index l mod N
     return np.fft.fftshift(dft) / float(N) ** d            # index l + N/2

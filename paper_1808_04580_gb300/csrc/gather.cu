@@ -31,6 +31,7 @@ struct GatherArgs {
     int ngrid;
     const void *g;        // reversed-axis layout: index (..(x_{d-1} L_{d-2} + ..) L_0 + x_0)
     int op;
+    double out_scale, k0;   // W x = out_scale f - K(0) x (caller's coordinates)
     double b, inv_sinh_bm;
 };
 
@@ -116,15 +117,15 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a) {
             const int i = a.perm[k];
             const double fd = double(f);
             if (a.op == OP_DEGREE) {
-                const double dd = fd - 1.0;
+                const double dd = a.out_scale * fd - a.k0;
                 a.degree_out[i] = dd;
                 a.dinv_out[k] = dd > 0.0 ? 1.0 / sqrt(dd) : 0.0;
             } else if (a.op == OP_W) {
-                a.y[i] = fd - a.x[i];
+                a.y[i] = a.out_scale * fd - a.k0 * a.x[i];
             } else {
                 const double di = a.dinv[k];
                 const double xi = a.x[i];
-                const double ax = di * (fd - di * xi);
+                const double ax = di * (a.out_scale * fd - a.k0 * di * xi);
                 a.y[i] = a.op == OP_A ? ax : xi - ax;
             }
         }
@@ -188,6 +189,8 @@ cudaError_t launch_gather(Plan &P, int op, const double *x, double *y) {
     a.ngrid = P.ngrid;
     a.g = P.g;
     a.op = op;
+    a.out_scale = P.out_scale;
+    a.k0 = P.k0;
     a.b = P.kb_b;
     a.inv_sinh_bm = P.kb_inv_sinh_bm;
     switch (P.prec * 4 + P.d) {

@@ -48,6 +48,7 @@ struct GatherTCArgs {
     int ngrid;
     const float *g;   // layout [x2][x1][x0]
     int op;
+    double out_scale, k0;   // W x = out_scale f - K(0) x (caller's coordinates)
     int *error_flag;
     unsigned *counter;    // next work item, shared by all CTAs
     float poly[2 * kMaxM][kPolyCoef];   // window by taps, as in the plan
@@ -318,13 +319,13 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 if (live) {
                     const double fd = double(f);
                     if (a.op == OP_DEGREE) {
-                        const double dd = fd - 1.0;
+                        const double dd = a.out_scale * fd - a.k0;
                         a.degree_out[iq] = dd;
                         a.dinv_out[kq] = dd > 0.0 ? 1.0 / sqrt(dd) : 0.0;
                     } else if (a.op == OP_W) {
-                        a.y[iq] = fd - xq;
+                        a.y[iq] = a.out_scale * fd - a.k0 * xq;
                     } else {
-                        const double ax = dq * (fd - dq * xq);
+                        const double ax = dq * (a.out_scale * fd - a.k0 * dq * xq);
                         a.y[iq] = a.op == OP_A ? ax : xq - ax;
                     }
                 }
@@ -389,6 +390,8 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
     a.ngrid = P.ngrid;
     a.g = reinterpret_cast<const float *>(P.g);
     a.op = op;
+    a.out_scale = P.out_scale;
+    a.k0 = P.k0;
     a.error_flag = P.error_flag;
     a.counter = P.work_counter + 1;
     for (int j = 0; j < 2 * kMaxM; ++j)

@@ -39,6 +39,9 @@ struct Plan {
     // problem
     int64_t n = 0;
     int d = 0, N = 0, m = 0, p = 0, prec = 0;
+    int kernel = NFL_KERNEL_GAUSSIAN;
+    double out_scale = 1.0;     // scaled fast sum -> caller's coordinates (multiquadrics: 1/rho, rho)
+    double k0 = 1.0;            // K(0) in the caller's coordinates
     double sigma = 0, sigma_t = 0, rho = 1, eps_B = 0;
     double center[3] = {0, 0, 0};
     cudaStream_t stream = 0;

@@ -213,7 +213,7 @@ __global__ void fill_items(const int32_t *count, const int64_t *start, const int
 
 // ----------------------------------------------------------- coefficients
 struct KRParams {
-    int N, d;
+    int N, d, kind;
     double sigma_t, eps_B;
     int ncoef;
     double coef[32];
@@ -236,8 +236,13 @@ __global__ void kr_samples(double *S, KRParams p) {
         double val;
         const double a0 = 0.5 - p.eps_B;
         if (p.eps_B <= 0.0 || rr <= a0) {
-            const double q = fmin(rr, 0.5) / p.sigma_t;
-            val = exp(-q * q);
+            const double r = fmin(rr, 0.5), st = p.sigma_t;
+            switch (p.kind) {
+                case NFL_KERNEL_LAPLACIAN_RBF: val = exp(-r / st); break;
+                case NFL_KERNEL_MULTIQUADRIC: val = sqrt(r * r + st * st); break;
+                case NFL_KERNEL_INV_MULTIQUADRIC: val = 1.0 / sqrt(r * r + st * st); break;
+                default: val = exp(-(r / st) * (r / st)); break;
+            }
         } else {
             const double s = (fmin(rr, 0.5) - a0) / p.eps_B;
             val = 0.0;
@@ -323,15 +328,47 @@ static double gauss_deriv(double r, double sigma, int k) {
     return std::pow(-1.0 / sigma, k) * hermite_phys(k, x) * std::exp(-x * x);
 }
 
-// Two-point Taylor polynomial T_B(r) = sum_k c_k s^k, s = (r - a)/eps_B, a = 1/2 - eps_B:
-// T_B^(k)(a) = K^(k)(a) for k < p;  T_B(1/2) = K(1/2), T_B^(k)(1/2) = 0 for 1 <= k < p.
-static bool boundary_coefficients(double sigma, double eps_B, int p, double *c) {
-    const double a = 0.5 - eps_B;
+// The radial kernel K(r) of each NFL_KERNEL_* with shape parameter s.
+static double kernel_value(int kind, double r, double s) {
+    switch (kind) {
+        case NFL_KERNEL_LAPLACIAN_RBF: return std::exp(-r / s);
+        case NFL_KERNEL_MULTIQUADRIC: return std::sqrt(r * r + s * s);
+        case NFL_KERNEL_INV_MULTIQUADRIC: return 1.0 / std::sqrt(r * r + s * s);
+        default: return std::exp(-(r / s) * (r / s));
+    }
+}
+
+// Taylor coefficients t_k = K^(k)(a) / k!, k < p, of the radial kernel at r = a.
+// Multiquadrics: K(a + h) = P(h)^alpha with P(h) = a^2 + s^2 + 2 a h + h^2 and
+// alpha = +-1/2; the coefficients of a power of a power series follow from
+// P u' = alpha P' u:  k P_0 u_k = sum_{j=1,2} ((alpha + 1) j - k) P_j u_{k-j}.
+static void kernel_taylor(int kind, double a, double s, int p, double *t) {
+    if (kind == NFL_KERNEL_MULTIQUADRIC || kind == NFL_KERNEL_INV_MULTIQUADRIC) {
+        const double alpha = kind == NFL_KERNEL_MULTIQUADRIC ? 0.5 : -0.5;
+        const double P0 = a * a + s * s, P[3] = {P0, 2.0 * a, 1.0};
+        t[0] = std::pow(P0, alpha);
+        for (int k = 1; k < p; ++k) {
+            double acc = 0.0;
+            for (int j = 1; j <= 2 && j <= k; ++j) acc += ((alpha + 1.0) * j - k) * P[j] * t[k - j];
+            t[k] = acc / (k * P0);
+        }
+        return;
+    }
     double fact = 1.0;
     for (int k = 0; k < p; ++k) {
         if (k > 0) fact *= k;
-        c[k] = gauss_deriv(a, sigma, k) * std::pow(eps_B, k) / fact;
+        const double dk = kind == NFL_KERNEL_LAPLACIAN_RBF ? std::pow(-1.0 / s, k) * std::exp(-a / s)
+                                                           : gauss_deriv(a, s, k);
+        t[k] = dk / fact;
     }
+}
+
+// Two-point Taylor polynomial T_B(r) = sum_k c_k s^k, s = (r - a)/eps_B, a = 1/2 - eps_B:
+// T_B^(k)(a) = K^(k)(a) for k < p;  T_B(1/2) = K(1/2), T_B^(k)(1/2) = 0 for 1 <= k < p.
+static bool boundary_coefficients(int kind, double sigma, double eps_B, int p, double *c) {
+    const double a = 0.5 - eps_B;
+    kernel_taylor(kind, a, sigma, p, c);
+    for (int k = 0; k < p; ++k) c[k] *= std::pow(eps_B, k);
     auto dpow = [](int k, int j) {
         if (k < j) return 0.0;
         double r = 1.0;
@@ -340,7 +377,7 @@ static bool boundary_coefficients(double sigma, double eps_B, int p, double *c) 
     };
     std::vector<double> A(p * p), rhs(p);
     for (int j = 0; j < p; ++j) {
-        double s = (j == 0) ? std::exp(-0.25 / (sigma * sigma)) : 0.0;
+        double s = (j == 0) ? kernel_value(kind, 0.5, sigma) : 0.0;
         for (int k = 0; k < p; ++k) s -= c[k] * dpow(k, j);
         rhs[j] = s;
         for (int col = 0; col < p; ++col) A[j * p + col] = dpow(p + col, j);
@@ -385,12 +422,13 @@ nfl_status compute_coefficients(Plan &P) {
     KRParams kp{};
     kp.N = N;
     kp.d = d;
+    kp.kind = P.kernel;
     kp.sigma_t = P.sigma_t;
     kp.eps_B = P.eps_B;
     kp.ncoef = 0;
     if (P.eps_B > 0.0) {
         if (2 * P.p > 32) return NFL_ERR_INVALID_ARG;
-        if (!boundary_coefficients(P.sigma_t, P.eps_B, P.p, kp.coef)) return NFL_ERR_INVALID_ARG;
+        if (!boundary_coefficients(P.kernel, P.sigma_t, P.eps_B, P.p, kp.coef)) return NFL_ERR_INVALID_ARG;
         kp.ncoef = 2 * P.p;
     }
     int64_t full = 1;
@@ -515,7 +553,7 @@ static void window_poly(Plan &P) {
     }
 }
 
-static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sigma, int N, int m, int p,
+static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel, double sigma, int N, int m, int p,
                                    double eps_B, int prec, cudaStream_t stream, Plan *P) {
     P->n = n; P->d = d; P->N = N; P->m = m; P->p = p; P->prec = prec;
     P->sigma = sigma; P->eps_B = eps_B; P->stream = stream;
@@ -562,6 +600,11 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, double sig
     const double radius = std::sqrt(r2);
     P->rho = radius > 0.0 ? (0.25 - 0.5 * eps_B) / radius : 1.0;   // all nodes coincide: any rho fits
     P->sigma_t = P->rho * sigma;                                    // step 2
+    // the scaled kernel is rho^(+-1) times the caller's for the multiquadrics
+    P->kernel = kernel;
+    P->out_scale = kernel == NFL_KERNEL_MULTIQUADRIC ? 1.0 / P->rho
+                   : (kernel == NFL_KERNEL_INV_MULTIQUADRIC ? P->rho : 1.0);
+    P->k0 = kernel_value(kernel, 0.0, sigma);
 
     // active box: cells floor(n v~) - t0 with t0 leaving m taps (and one cell) of room
     Geometry G{};
@@ -741,7 +784,8 @@ nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double
                            double eps_B, int precision, void *stream, nfl_plan **out) {
     if (!out) return NFL_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!v || n < 1 || n > 0x7fffffff || d < 1 || d > 3 || kernel != NFL_KERNEL_GAUSSIAN) return NFL_ERR_INVALID_ARG;
+    if (!v || n < 1 || n > 0x7fffffff || d < 1 || d > 3 || kernel < NFL_KERNEL_GAUSSIAN ||
+        kernel > NFL_KERNEL_INV_MULTIQUADRIC) return NFL_ERR_INVALID_ARG;
     if (!(sigma > 0.0) || !std::isfinite(sigma)) return NFL_ERR_INVALID_ARG;
     if (N < 4 || N > 512 || (N & (N - 1)) != 0) return NFL_ERR_INVALID_ARG;
     if (m < 1 || m > nfl::kMaxM) return NFL_ERR_INVALID_ARG;
@@ -753,7 +797,7 @@ nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double
         return NFL_ERR_INVALID_ARG;
     Plan *P = new (std::nothrow) Plan();
     if (!P) return NFL_ERR_OUT_OF_MEMORY;
-    nfl_status st = nfl::plan_create_impl(v, n, d, sigma, N, m, p, eps_B, precision, (cudaStream_t)stream, P);
+    nfl_status st = nfl::plan_create_impl(v, n, d, kernel, sigma, N, m, p, eps_B, precision, (cudaStream_t)stream, P);
     if (st != NFL_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
         nfl::free_plan(P);
@@ -784,6 +828,9 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->eps_B = P->eps_B;
     info->rho = P->rho;
     info->sigma_tilde = P->sigma_t;
+    info->kernel = P->kernel;
+    info->k0 = P->k0;
+    info->out_scale = P->out_scale;
     for (int a = 0; a < 3; ++a) {
         info->center[a] = P->center[a];
         info->box[a] = a < P->d ? P->L[a] : 1;

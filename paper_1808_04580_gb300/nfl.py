@@ -41,7 +41,8 @@ class Info(ctypes.Structure):
         ("eps_B", ctypes.c_double), ("rho", ctypes.c_double), ("sigma_tilde", ctypes.c_double),
         ("center", ctypes.c_double * 3), ("box", ctypes.c_int * 3), ("tiles", ctypes.c_int64),
         ("work_items", ctypes.c_int64), ("min_degree", ctypes.c_double), ("max_degree", ctypes.c_double),
-        ("degree_ok", ctypes.c_int), ("device_error", ctypes.c_int),
+        ("degree_ok", ctypes.c_int), ("device_error", ctypes.c_int), ("kernel", ctypes.c_int),
+        ("k0", ctypes.c_double), ("out_scale", ctypes.c_double),
     ]
 
 
@@ -120,10 +121,17 @@ def _as_columns(x, n):
     return x.t().contiguous(), x.shape[1], False
 
 
-class Plan:
-    """Alg. 2 setup for one point cloud; products with W, A and L_s."""
+KERNELS = {"gaussian": 0, "laplacian_rbf": 1, "multiquadric": 2, "inverse_multiquadric": 3}
 
-    def __init__(self, v, sigma, N, m, p=0, eps_B=-1.0, precision="fp64"):
+
+class Plan:
+    """Alg. 2 setup for one point cloud; products with W, A and L_s.
+
+    ``kernel`` names one of the kernels of Sec. 2 (``KERNELS``); ``sigma`` is its
+    shape parameter (sigma, or c for the multiquadrics).
+    """
+
+    def __init__(self, v, sigma, N, m, p=0, eps_B=-1.0, precision="fp64", kernel="gaussian"):
         _cuda_f64(v, "v")
         if v.dim() != 2:
             raise ValueError("v must be (n, d)")
@@ -133,7 +141,7 @@ class Plan:
         self._h = None
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            st = _lib().nfl_plan_create(v.data_ptr(), self.n, self.d, 0, float(sigma), int(N), int(m), int(p),
+            st = _lib().nfl_plan_create(v.data_ptr(), self.n, self.d, KERNELS[kernel], float(sigma), int(N), int(m), int(p),
                                         float(eps_B), PRECISIONS[precision], _stream(), ctypes.byref(h))
         _check(st, "nfl_plan_create")
         self._h = h

@@ -13,7 +13,7 @@ import pytest
 import torch
 
 from oracle import direct, fastsum, spectral
-from paper_1808_04580_gb300 import NflError, Plan, workloads
+from paper_1808_04580_gb300 import KERNELS, NflError, Plan, workloads
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -141,6 +141,27 @@ def test_mixed_forms_wrap_and_low_dimensions(case, prec, tol):
     plan = Plan(gpu(v), sigma, N, m, p, eps_B, prec)
     assert rel(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x)) < tol
     assert plan.info()["device_error"] == 0
+
+
+# the other kernels of Sec. 2 through Alg. 2 (scaling rule, K(0), output scale)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 2e-6)])
+@pytest.mark.parametrize("kind,d", [("laplacian_rbf", 3), ("multiquadric", 3), ("inverse_multiquadric", 3),
+                                    ("multiquadric", 2), ("inverse_multiquadric", 1)])
+def test_kernel_variants_match_alg2_oracle(kind, d, prec, tol):
+    n = 1500
+    v = _cloud("clusters", n, d, seed=50 + d)
+    x = workloads.rhs(n, seed=51)
+    ref = fastsum.NormalizedFastsum(v, 0.5, 32, 4, 4, kernel=kind)
+    plan = Plan(gpu(v), 0.5, 32, 4, 4, -1.0, prec, kernel=kind)
+    info = plan.info()
+    assert info["kernel"] == KERNELS[kind]
+    assert info["k0"] == pytest.approx(ref.K0, rel=1e-15)
+    assert info["out_scale"] == pytest.approx(ref.out_scale, rel=1e-12)
+    xt = gpu(x)
+    assert rel(plan.apply_W(xt).cpu().numpy(), ref.apply_W(x)) < tol
+    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)
+    assert rel(plan.apply_A(xt).cpu().numpy(), ref.apply_A(x)) < tol
+    assert info["device_error"] == 0
 
 
 def test_block_of_right_hand_sides_equals_columns():

@@ -57,15 +57,19 @@ typedef enum {
  *                                                          converges slowly in N)
  *   MULTIQUADRIC         (r^2 + s^2)^{1/2}      K(0) = s
  *   INV_MULTIQUADRIC     (r^2 + s^2)^{-1/2}     K(0) = 1/s
+ *   GAUSSIAN_DSIGMA      (2 r^2 / s^3) exp(-r^2 / s^2), the s-derivative of the
+ *                        Gaussian (for gradients in sigma)  K(0) = 0
  * Alg. 2 step 2 scales s with the nodes (s~ = rho s); for the multiquadrics
  * the fast sum's output is then scaled by 1/rho (multiquadric) or rho (inverse
  * multiquadric), which makes the scaled kernel equal the caller's (reading of
- * Alg. 2 steps 2, 4, 5, whose printed rule c := c/rho does not). */
+ * Alg. 2 steps 2, 4, 5, whose printed rule c := c/rho does not); likewise by
+ * rho for GAUSSIAN_DSIGMA. */
 enum {
     NFL_KERNEL_GAUSSIAN = 0,
     NFL_KERNEL_LAPLACIAN_RBF = 1,
     NFL_KERNEL_MULTIQUADRIC = 2,
-    NFL_KERNEL_INV_MULTIQUADRIC = 3
+    NFL_KERNEL_INV_MULTIQUADRIC = 3,
+    NFL_KERNEL_GAUSSIAN_DSIGMA = 4
 };
 
 /* Arithmetic of the spread / FFT / gather steps.  Epilogues (-K(0) x,
@@ -206,6 +210,37 @@ nfl_status nfl_lanczos_k_smallest(nfl_plan *plan, int k, double tol, int maxit,
 nfl_status nfl_cg_solve(nfl_plan *plan, double beta, const double *shift,
                         const double *f, double *u, double tol, int maxit,
                         int *iters, double *relres);
+
+/*
+ * Gradients of a loss l(u) through the solve of nfl_cg_solve, given the
+ * forward solution u and g = dl/du (the differentiable form of the system of
+ * Sec. 6.2.2).  The operator beta L_s + diag(s) is symmetric, so one more
+ * solve gives lambda = (beta L_s + diag(s))^{-1} g, and
+ *   dl/df = lambda,  dl/ds_i = -lambda_i u_i,  dl/dbeta = -lambda^T L_s u,
+ *   dl/dsigma = -beta lambda^T (dL_s/dsigma) u,
+ * where, with d the degrees, delta = W_sigma 1, W_sigma = dW/dsigma (the
+ * plan dplan of kernel NFL_KERNEL_GAUSSIAN_DSIGMA), a~ = D^{-1/2} a and
+ * b~ = D^{-1/2} b (differentiating L_s = I - D^{-1/2} W D^{-1/2}, Sec. 2):
+ *   a^T (dL_s/dsigma) b = -a~^T W_sigma b~ + 1/2 sum_i (delta_i / d_i) (a~_i (W b~)_i + (W a~)_i b~_i).
+ * All products are the plans' fast sums.
+ *
+ *   plan        the NFL_KERNEL_GAUSSIAN plan of the forward solve.
+ *   dplan       NFL_KERNEL_GAUSSIAN_DSIGMA plan with the same nodes, sigma, N,
+ *               m, p and eps_B; may be NULL when grad_sigma is NULL.
+ *   beta, shift, tol, maxit   as in nfl_cg_solve (same values as the forward solve).
+ *   u           device n FP64: the forward solution.
+ *   g           device n FP64: dl/du.
+ *   grad_f      device n FP64: initial guess of the adjoint solve on entry,
+ *               lambda = dl/df on exit.
+ *   grad_shift  device n FP64 (out), may be NULL.
+ *   grad_beta, grad_sigma   host FP64 (out), may be NULL.
+ *   iters, relres           host (may be NULL): of the adjoint solve.
+ * Errors as nfl_cg_solve; NFL_ERR_INVALID_ARG when dplan does not match plan.
+ */
+nfl_status nfl_cg_solve_backward(nfl_plan *plan, nfl_plan *dplan, double beta, const double *shift,
+                                 const double *u, const double *g, double tol, int maxit, double *grad_f,
+                                 double *grad_shift, double *grad_beta, double *grad_sigma, int *iters,
+                                 double *relres);
 
 /*
  * nfl_cg_solve without device allocation.  The paper has no counterpart:

@@ -3,7 +3,8 @@
  * rows j, each over all n sources, with the kernels of Sec. 2: kind 0 the
  * Gaussian exp(-r^2/sigma^2) (eq. (W_gaussian)), 1 the Laplacian RBF
  * exp(-r/sigma), 2 the multiquadric (r^2 + c^2)^{1/2}, 3 the inverse
- * multiquadric (r^2 + c^2)^{-1/2}; r = ||v_j - v_i||, c passed as sigma.
+ * multiquadric (r^2 + c^2)^{-1/2}, 4 the sigma-derivative of the Gaussian
+ * (2 r^2 / sigma^3) exp(-r^2/sigma^2); r = ||v_j - v_i||, c passed as sigma.
  *
  * Test infrastructure (the oracle): only tests/, the smoke check and the
  * CPU-baseline leg of bench.py may load this library.  Plain loops in FP64,
@@ -30,7 +31,8 @@ static double kernel_of(int kind, double dist2, double sigma) {
         case 0: return exp(-dist2 / (sigma * sigma));
         case 1: return exp(-sqrt(dist2) / sigma);
         case 2: return sqrt(dist2 + sigma * sigma);
-        default: return 1.0 / sqrt(dist2 + sigma * sigma);
+        case 3: return 1.0 / sqrt(dist2 + sigma * sigma);
+        default: return 2.0 * dist2 / (sigma * sigma * sigma) * exp(-dist2 / (sigma * sigma));
     }
 }
 
@@ -38,7 +40,7 @@ int oracle_kernel_rows(const double *v, int64_t n, int d, int kind, double sigma
                        const double *x, int64_t nrhs, int64_t ldx,
                        const int64_t *rows, int64_t nrows, double *out,
                        int nthreads) {
-    if (n < 0 || d < 1 || kind < 0 || kind > 3 || sigma <= 0.0 || nrhs < 1 || ldx < n) return 1;
+    if (n < 0 || d < 1 || kind < 0 || kind > 4 || sigma <= 0.0 || nrhs < 1 || ldx < n) return 1;
     for (int64_t k = 0; k < nrows; ++k)
         if (rows[k] < 0 || rows[k] >= n) return 1;
 #ifdef _OPENMP

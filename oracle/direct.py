@@ -5,7 +5,7 @@ Test infrastructure (the oracle); see the package docstring for who may use it.
 Sec. 2, eq. (W_gaussian): W_ji = exp(-||v_j - v_i||^2 / sigma^2) for j != i,
 W_jj = 0; the other kernels of Sec. 2 (Laplacian RBF exp(-r/sigma), the
 multiquadric (r^2 + c^2)^{1/2} and its inverse, r = ||v_j - v_i||, shape
-parameter in ``sigma``) by name.  Degree d_j = sum_i W_ji; D = diag(d); L = D - W;
+parameter in ``sigma``) and the sigma-derivative of the Gaussian by name.  Degree d_j = sum_i W_ji; D = diag(d); L = D - W;
 A = D^{-1/2} W D^{-1/2}; L_s = I - A (Sec. 2, eq. (nomlap)).
 Everything is in the original coordinates (no scaling, no shift).
 
@@ -34,6 +34,8 @@ def _radial(r2, sigma, kernel):
         return np.sqrt(r2 + sigma ** 2)
     if kernel == "inverse_multiquadric":
         return 1.0 / np.sqrt(r2 + sigma ** 2)
+    if kernel == "gaussian_dsigma":
+        return 2.0 * r2 / sigma ** 3 * np.exp(-r2 / sigma ** 2)
     raise ValueError("unknown kernel %r" % (kernel,))
 
 
@@ -105,7 +107,7 @@ def max_threads():
     return int(_lib().oracle_max_threads())
 
 
-_KIND = {"gaussian": 0, "laplacian_rbf": 1, "multiquadric": 2, "inverse_multiquadric": 3}
+_KIND = {"gaussian": 0, "laplacian_rbf": 1, "multiquadric": 2, "inverse_multiquadric": 3, "gaussian_dsigma": 4}
 
 
 def rows_W(v, sigma, x, rows, nthreads=0, kernel="gaussian"):

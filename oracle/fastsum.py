@@ -36,6 +36,8 @@ Readings:
     so this oracle uses c~ = rho c and scales Alg. 1's output by 1/rho
     (multiquadric) or rho (inverse multiquadric); the test against the
     direct sum pins this reading, and shows that the printed rule misses it.
+    The sigma-derivative of the Gaussian scales as rho^-1 in the same way
+    (output times rho).
 
 Pins: O3 against O2 at m = 8 (~1e-13 relative), O2 against the direct sum
 O1 for parameters where the kernel error is tiny, the a-priori bound of
@@ -87,8 +89,8 @@ class NormalizedFastsum:
         self.sigma = float(sigma)
         self.sigma_t = self.rho * self.sigma                               # step 2
         # output scale of Alg. 1 back to the original coordinates, and K(0) there
-        self.out_scale = {"multiquadric": 1.0 / self.rho,
-                          "inverse_multiquadric": self.rho}.get(kernel, 1.0)
+        self.out_scale = {"multiquadric": 1.0 / self.rho, "inverse_multiquadric": self.rho,
+                          "gaussian_dsigma": self.rho}.get(kernel, 1.0)
         self.K0 = float(_kernel.radial(0.0, self.sigma, kernel))
         self.d = self.vt.shape[1]
         self.bhat = _kernel.fourier_coefficients(                          # step 3

@@ -31,7 +31,9 @@ the shell beyond its defining end conditions.
 
 Other kernels (Sec. 2, after eq. (W_gaussian); used by Alg. 2 steps 2, 4, 5):
 the Laplacian RBF exp(-||y||/sigma), the multiquadric (||y||^2 + c^2)^{1/2}
-and the inverse multiquadric (||y||^2 + c^2)^{-1/2}.  Every function below
+and the inverse multiquadric (||y||^2 + c^2)^{-1/2}; and, for gradients with
+respect to sigma, the sigma-derivative of the Gaussian,
+d/dsigma exp(-||y||^2/sigma^2) = (2 ||y||^2 / sigma^3) exp(-||y||^2/sigma^2).  Every function below
 takes the kernel by name (default "gaussian") and its shape parameter
 (sigma, or c for the two multiquadrics) in the ``sigma`` argument.
 """
@@ -64,7 +66,7 @@ def gaussian_derivative(r, sigma, k):
     return (-1.0 / sigma) ** k * hk * np.exp(-x * x)
 
 
-KERNELS = ("gaussian", "laplacian_rbf", "multiquadric", "inverse_multiquadric")
+KERNELS = ("gaussian", "laplacian_rbf", "multiquadric", "inverse_multiquadric", "gaussian_dsigma")
 
 
 def radial(r, sigma, kind="gaussian"):
@@ -78,6 +80,8 @@ def radial(r, sigma, kind="gaussian"):
         return np.sqrt(r * r + sigma * sigma)
     if kind == "inverse_multiquadric":
         return 1.0 / np.sqrt(r * r + sigma * sigma)
+    if kind == "gaussian_dsigma":
+        return 2.0 * r * r / sigma ** 3 * gaussian(r, sigma)
     raise ValueError("unknown kernel %r" % (kind,))
 
 
@@ -111,6 +115,10 @@ def radial_derivative(r, sigma, k, kind="gaussian"):
             out = out + (math.comb(k, j) * _falling(alpha, j) * _falling(alpha, k - j)
                          * zm ** (alpha - j) * zp ** (alpha - k + j))
         return out.real
+    if kind == "gaussian_dsigma":
+        # Leibniz on r^2 g(r): r^2 g^(k) + 2 k r g^(k-1) + k (k - 1) g^(k-2)
+        g = lambda j: gaussian_derivative(r, sigma, j) if j >= 0 else 0.0
+        return 2.0 / sigma ** 3 * (r * r * g(k) + 2.0 * k * r * g(k - 1) + k * (k - 1) * g(k - 2))
     raise ValueError("unknown kernel %r" % (kind,))
 
 

@@ -241,6 +241,7 @@ __global__ void kr_samples(double *S, KRParams p) {
                 case NFL_KERNEL_LAPLACIAN_RBF: val = exp(-r / st); break;
                 case NFL_KERNEL_MULTIQUADRIC: val = sqrt(r * r + st * st); break;
                 case NFL_KERNEL_INV_MULTIQUADRIC: val = 1.0 / sqrt(r * r + st * st); break;
+                case NFL_KERNEL_GAUSSIAN_DSIGMA: val = 2.0 * r * r / (st * st * st) * exp(-(r / st) * (r / st)); break;
                 default: val = exp(-(r / st) * (r / st)); break;
             }
         } else {
@@ -334,6 +335,7 @@ static double kernel_value(int kind, double r, double s) {
         case NFL_KERNEL_LAPLACIAN_RBF: return std::exp(-r / s);
         case NFL_KERNEL_MULTIQUADRIC: return std::sqrt(r * r + s * s);
         case NFL_KERNEL_INV_MULTIQUADRIC: return 1.0 / std::sqrt(r * r + s * s);
+        case NFL_KERNEL_GAUSSIAN_DSIGMA: return 2.0 * r * r / (s * s * s) * std::exp(-(r / s) * (r / s));
         default: return std::exp(-(r / s) * (r / s));
     }
 }
@@ -357,8 +359,18 @@ static void kernel_taylor(int kind, double a, double s, int p, double *t) {
     double fact = 1.0;
     for (int k = 0; k < p; ++k) {
         if (k > 0) fact *= k;
-        const double dk = kind == NFL_KERNEL_LAPLACIAN_RBF ? std::pow(-1.0 / s, k) * std::exp(-a / s)
-                                                           : gauss_deriv(a, s, k);
+        double dk;
+        if (kind == NFL_KERNEL_LAPLACIAN_RBF) {
+            dk = std::pow(-1.0 / s, k) * std::exp(-a / s);
+        } else if (kind == NFL_KERNEL_GAUSSIAN_DSIGMA) {
+            // (2/s^3) d^k [r^2 g(r)] = (2/s^3) (r^2 g^(k) + 2 k r g^(k-1) + k (k-1) g^(k-2))
+            dk = a * a * gauss_deriv(a, s, k);
+            if (k >= 1) dk += 2.0 * k * a * gauss_deriv(a, s, k - 1);
+            if (k >= 2) dk += k * (k - 1.0) * gauss_deriv(a, s, k - 2);
+            dk *= 2.0 / (s * s * s);
+        } else {
+            dk = gauss_deriv(a, s, k);
+        }
         t[k] = dk / fact;
     }
 }
@@ -603,7 +615,7 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
     // the scaled kernel is rho^(+-1) times the caller's for the multiquadrics
     P->kernel = kernel;
     P->out_scale = kernel == NFL_KERNEL_MULTIQUADRIC ? 1.0 / P->rho
-                   : (kernel == NFL_KERNEL_INV_MULTIQUADRIC ? P->rho : 1.0);
+                   : ((kernel == NFL_KERNEL_INV_MULTIQUADRIC || kernel == NFL_KERNEL_GAUSSIAN_DSIGMA) ? P->rho : 1.0);
     P->k0 = kernel_value(kernel, 0.0, sigma);
 
     // active box: cells floor(n v~) - t0 with t0 leaving m taps (and one cell) of room
@@ -785,7 +797,7 @@ nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double
     if (!out) return NFL_ERR_INVALID_ARG;
     *out = nullptr;
     if (!v || n < 1 || n > 0x7fffffff || d < 1 || d > 3 || kernel < NFL_KERNEL_GAUSSIAN ||
-        kernel > NFL_KERNEL_INV_MULTIQUADRIC) return NFL_ERR_INVALID_ARG;
+        kernel > NFL_KERNEL_GAUSSIAN_DSIGMA) return NFL_ERR_INVALID_ARG;
     if (!(sigma > 0.0) || !std::isfinite(sigma)) return NFL_ERR_INVALID_ARG;
     if (N < 4 || N > 512 || (N & (N - 1)) != 0) return NFL_ERR_INVALID_ARG;
     if (m < 1 || m > nfl::kMaxM) return NFL_ERR_INVALID_ARG;

@@ -435,3 +435,107 @@ nfl_status nfl_cg_solve(nfl_plan *plan, double beta, const double *shift, const 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------- gradients through CG
+namespace nfl {
+
+// out_i = -lambda_i u_i
+__global__ void neg_product(const double *lam, const double *u, int64_t n, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = -lam[i] * u[i];
+}
+
+// a~ = a / sqrt(d), b~ = b / sqrt(d)
+__global__ void scale_by_degree(const double *a, const double *b, const double *d, int64_t n, double *at,
+                                double *bt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = 1.0 / sqrt(d[i]);
+        at[i] = a[i] * s;
+        bt[i] = b[i] * s;
+    }
+}
+
+// per-block partial sums of -a~_i (W_s b~)_i + (delta_i / d_i) (a~_i (W b~)_i + (W a~)_i b~_i) / 2
+__global__ void dsigma_form_partials(const double *at, const double *bt, const double *Wsb, const double *Wb,
+                                     const double *Wa, const double *delta, const double *d, int64_t n,
+                                     double *part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += -at[i] * Wsb[i] + 0.5 * delta[i] / d[i] * (at[i] * Wb[i] + Wa[i] * bt[i]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+}  // namespace nfl
+
+extern "C" {
+
+nfl_status nfl_cg_solve_backward(nfl_plan *plan, nfl_plan *dplan, double beta, const double *shift,
+                                 const double *u, const double *g, double tol, int maxit, double *grad_f,
+                                 double *grad_shift, double *grad_beta, double *grad_sigma, int *iters,
+                                 double *relres) {
+    using namespace nfl;
+    if (!plan || !u || !g || !grad_f) return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (grad_sigma && !dplan) return NFL_ERR_INVALID_ARG;
+    if (dplan) {
+        const Plan &D = *reinterpret_cast<const Plan *>(dplan);
+        if (D.n != P.n || D.d != P.d || D.kernel != NFL_KERNEL_GAUSSIAN_DSIGMA || P.kernel != NFL_KERNEL_GAUSSIAN ||
+            D.sigma != P.sigma || D.N != P.N || D.m != P.m || D.p != P.p || D.eps_B != P.eps_B)
+            return NFL_ERR_INVALID_ARG;
+    }
+    // lambda = (beta L_s + diag(s))^{-1} g: the operator is symmetric
+    nfl_status st = nfl_cg_solve(plan, beta, shift, g, grad_f, tol, maxit, iters, relres);
+    if (st != NFL_OK) return st;
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    const int vb = vec_blocks(P);
+    const double *lam = grad_f;
+    if (grad_shift) neg_product<<<vb, 256, 0, s>>>(lam, u, n, grad_shift);
+    if (!grad_beta && !grad_sigma) return cudaStreamSynchronize(s) == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+    Dev part, sc, T0, T1, T2, T3, T4;
+    if (cudaMalloc(&part.buf, kRedBlocks * 8) != cudaSuccess || cudaMalloc(&sc.buf, 8 * 8) != cudaSuccess ||
+        cudaMalloc(&T0.buf, n * 8) != cudaSuccess)
+        return NFL_ERR_OUT_OF_MEMORY;
+    if (grad_beta) {
+        // dl/dbeta = -lambda^T L_s u
+        st = run_column(P, OP_LS, u, T0.buf);
+        if (st != NFL_OK) return st;
+        double v = 0.0;
+        if (dot(P, lam, T0.buf, part.buf, sc.buf, &v) != cudaSuccess) return NFL_ERR_CUDA;
+        *grad_beta = -v;
+    }
+    if (grad_sigma) {
+        Plan &D = *reinterpret_cast<Plan *>(dplan);
+        if (cudaMalloc(&T1.buf, n * 8) != cudaSuccess || cudaMalloc(&T2.buf, n * 8) != cudaSuccess ||
+            cudaMalloc(&T3.buf, n * 8) != cudaSuccess || cudaMalloc(&T4.buf, n * 8) != cudaSuccess)
+            return NFL_ERR_OUT_OF_MEMORY;
+        double *at = T0.buf, *bt = T1.buf, *Wb = T2.buf, *Wa = T3.buf, *Wsb = T4.buf;
+        scale_by_degree<<<vb, 256, 0, s>>>(lam, u, P.degree, n, at, bt);
+        st = run_column(P, OP_W, bt, Wb);
+        if (st == NFL_OK) st = run_column(P, OP_W, at, Wa);
+        if (st != NFL_OK) return st;
+        // the derivative plan runs on this plan's stream for the call
+        const cudaStream_t ds = D.stream;
+        D.stream = s;
+        st = run_column(D, OP_W, bt, Wsb);
+        D.stream = ds;
+        if (st != NFL_OK) return st;
+        dsigma_form_partials<<<kRedBlocks, 256, 0, s>>>(at, bt, Wsb, Wb, Wa, D.degree, P.degree, n, part.buf);
+        sum_partials<<<1, 256, 0, s>>>(part.buf, kRedBlocks, 1, sc.buf);
+        double form = 0.0;
+        if (cudaMemcpyAsync(&form, sc.buf, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return NFL_ERR_CUDA;
+        *grad_sigma = -beta * form;                       // form = lambda^T (dL_s/dsigma) u
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -66,6 +66,8 @@ SIGNATURES = {
     "nfl_apply_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                ctypes.POINTER(_L), _I]),
     "nfl_cg_solve_noalloc": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nfl_cg_solve_backward": (_I, [_P, _P, _D, _P, _P, _P, _D, _I, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                   ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_plan_set_profiling": (_I, [_P, _I]),
     "nfl_plan_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
     "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
@@ -121,7 +123,7 @@ def _as_columns(x, n):
     return x.t().contiguous(), x.shape[1], False
 
 
-KERNELS = {"gaussian": 0, "laplacian_rbf": 1, "multiquadric": 2, "inverse_multiquadric": 3}
+KERNELS = {"gaussian": 0, "laplacian_rbf": 1, "multiquadric": 2, "inverse_multiquadric": 3, "gaussian_dsigma": 4}
 
 
 class Plan:
@@ -245,6 +247,28 @@ class Plan:
         if check:
             _check(st, "nfl_cg_solve_noalloc" if noalloc else "nfl_cg_solve")
         return u, it.value, rel.value, st
+
+    def cg_solve_backward(self, u, g, beta=1.0, shift=None, dplan=None, tol=1e-10, maxit=1000, want_shift=True):
+        """nfl_cg_solve_backward: (grad_f, grad_shift or None, grad_beta, grad_sigma or None, iters, relres)."""
+        self._sync_stream()
+        u = _cuda_f64(u, "u").contiguous()
+        g = _cuda_f64(g, "g").contiguous()
+        sp = None
+        if shift is not None:
+            shift = _cuda_f64(shift, "shift").contiguous()
+            sp = shift.data_ptr()
+        grad_f = torch.zeros_like(g)
+        grad_shift = torch.empty_like(g) if want_shift else None
+        gb = ctypes.c_double(0.0)
+        gs = ctypes.c_double(0.0)
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = _lib().nfl_cg_solve_backward(
+            self._h, dplan._h if dplan is not None else None, float(beta), sp, u.data_ptr(), g.data_ptr(),
+            float(tol), int(maxit), grad_f.data_ptr(), grad_shift.data_ptr() if want_shift else None,
+            ctypes.byref(gb), ctypes.byref(gs) if dplan is not None else None, ctypes.byref(it), ctypes.byref(rel))
+        _check(st, "nfl_cg_solve_backward")
+        return grad_f, grad_shift, gb.value, (gs.value if dplan is not None else None), it.value, rel.value
 
 
 _OPS = {"W": 0, "A": 1, "Ls": 2}

@@ -56,7 +56,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     bad = [
         (fake, 0, 3, 0, 1.0, 32, 4, 4, -1.0, 0),     # n = 0
         (fake, 10, 4, 0, 1.0, 32, 4, 4, -1.0, 0),    # d = 4
-        (fake, 10, 3, 4, 1.0, 32, 4, 4, -1.0, 0),    # unknown kernel
+        (fake, 10, 3, 5, 1.0, 32, 4, 4, -1.0, 0),    # unknown kernel
         (fake, 10, 3, -1, 1.0, 32, 4, 4, -1.0, 0),   # unknown kernel
         (fake, 10, 3, 0, -1.0, 32, 4, 4, -1.0, 0),   # sigma <= 0
         (fake, 10, 3, 0, 1.0, 30, 4, 4, -1.0, 0),    # N not a power of two

@@ -11,7 +11,7 @@ import sympy
 
 from oracle import direct, fastsum, kernel
 
-KINDS = ["gaussian", "laplacian_rbf", "multiquadric", "inverse_multiquadric"]
+KINDS = ["gaussian", "laplacian_rbf", "multiquadric", "inverse_multiquadric", "gaussian_dsigma"]
 
 
 def _expr(kind, r, s):
@@ -21,20 +21,23 @@ def _expr(kind, r, s):
         return sympy.exp(-r / s)
     if kind == "multiquadric":
         return sympy.sqrt(r ** 2 + s ** 2)
+    if kind == "gaussian_dsigma":
+        return sympy.diff(sympy.exp(-(r / s) ** 2), s)
     return 1 / sympy.sqrt(r ** 2 + s ** 2)
 
 
 def _sym_derivative(kind, s, k, r0):
-    r = sympy.symbols("r", positive=True)
-    e = _expr(kind, r, sympy.Float(s, 30))
+    r, sg = sympy.symbols("r sg", positive=True)
+    e = _expr(kind, r, sg).subs(sg, sympy.Float(s, 30))
     return float(sympy.diff(e, r, k).subs(r, sympy.Float(r0, 30)).evalf(30))
 
 
 @pytest.mark.parametrize("kind", KINDS)
 def test_values_and_k0(kind):
     c = 0.3
-    k0 = {"gaussian": 1.0, "laplacian_rbf": 1.0, "multiquadric": c, "inverse_multiquadric": 1.0 / c}[kind]
-    assert float(kernel.radial(0.0, c, kind)) == pytest.approx(k0, rel=1e-15)
+    k0 = {"gaussian": 1.0, "laplacian_rbf": 1.0, "multiquadric": c, "inverse_multiquadric": 1.0 / c,
+          "gaussian_dsigma": 0.0}[kind]
+    assert float(kernel.radial(0.0, c, kind)) == pytest.approx(k0, rel=1e-15, abs=0.0)
     for r0 in (0.05, 0.4, 1.7):
         assert float(kernel.radial(r0, c, kind)) == pytest.approx(_sym_derivative(kind, c, 0, r0), rel=1e-14)
 
@@ -69,7 +72,8 @@ def test_coefficients_sum_to_regularized_kernel_at_zero(kind):
     # sum_l b_l = K_RF(0) = K_R(0) (the trapezoidal rule interpolates at the nodes)
     b = kernel.fourier_coefficients(16, 3, 0.3, 0.125, 4, kind)
     assert abs(b.imag).max() < 1e-12 * abs(b.real).max()
-    assert b.real.sum() == pytest.approx(float(kernel.radial(0.0, 0.3, kind)), rel=1e-12)
+    assert b.real.sum() == pytest.approx(float(kernel.radial(0.0, 0.3, kind)), rel=1e-12,
+                                         abs=1e-12 * abs(b.real).max())
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -77,7 +81,8 @@ def test_direct_two_nodes_closed_form(kind):
     v = np.array([[0.0, 0.0, 0.0], [0.3, 0.4, 0.0]])   # distance 0.5
     c = 0.8
     w = {"gaussian": math.exp(-0.25 / 0.64), "laplacian_rbf": math.exp(-0.5 / 0.8),
-         "multiquadric": math.sqrt(0.25 + 0.64), "inverse_multiquadric": 1.0 / math.sqrt(0.25 + 0.64)}[kind]
+         "multiquadric": math.sqrt(0.25 + 0.64), "inverse_multiquadric": 1.0 / math.sqrt(0.25 + 0.64),
+         "gaussian_dsigma": 2.0 * 0.25 / 0.8 ** 3 * math.exp(-0.25 / 0.64)}[kind]
     x = np.array([2.0, -3.0])
     np.testing.assert_allclose(direct.apply_W(v, c, x, kind), [-3.0 * w, 2.0 * w], rtol=1e-15)
     np.testing.assert_allclose(direct.apply_A(v, c, x, kind), [-3.0, 2.0], rtol=1e-14)
@@ -100,7 +105,7 @@ def cloud():
 
 
 @pytest.mark.parametrize("kind,tol", [("gaussian", 1e-12), ("multiquadric", 1e-5),
-                                      ("inverse_multiquadric", 1e-6)])
+                                      ("inverse_multiquadric", 1e-6), ("gaussian_dsigma", 1e-12)])
 def test_alg2_matches_direct_sum(cloud, kind, tol):
     v, x = cloud
     ref = direct.apply_W(v, 0.7, x, kind)
@@ -133,3 +138,12 @@ def test_printed_multiquadric_rule_misses_the_kernel(cloud):
     printed = ours.rho * fastsum.fastsum(ours.vt, x, b_printed, 64, 8).real - c * x
     assert np.linalg.norm(ours.apply_W(x) - ref) / np.linalg.norm(ref) < 1e-4
     assert np.linalg.norm(printed - ref) / np.linalg.norm(ref) > 0.1
+
+
+def test_gaussian_dsigma_is_the_sigma_derivative(cloud):
+    """W_sigma x equals the central difference in sigma of the Gaussian W x."""
+    v, x = cloud
+    h = 1e-5
+    fd = (direct.apply_W(v, 0.7 + h, x) - direct.apply_W(v, 0.7 - h, x)) / (2 * h)
+    ex = direct.apply_W(v, 0.7, x, "gaussian_dsigma")
+    assert np.abs(fd - ex).max() < 1e-8 * np.abs(ex).max()

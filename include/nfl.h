@@ -197,6 +197,25 @@ nfl_status nfl_lanczos_k_smallest(nfl_plan *plan, int k, double tol, int maxit,
                                   uint64_t seed, double *evals, double *evecs, int *iters);
 
 /*
+ * Nystrom-Gaussian-NFFT (Alg. 3, Sec. 5.2): the k largest eigenpairs of
+ * A = D^{-1/2} W D^{-1/2}, approximately, from a rank-M approximation
+ * (A Q)(Q^T A Q)^+_M (A Q)^T with Q = orth(A G) for a Gaussian n x L block G:
+ * 2L products with A (the plan's fast sums), Gram-Schmidt QR with
+ * reorthogonalization on the device, and two small symmetric
+ * eigen-decompositions (L x L and M x M, cyclic Jacobi on the host).
+ *
+ *   k, L, M   1 <= k <= M <= L <= min(n, 512).
+ *   G         device n x L FP64 column-major random block (read only), or NULL
+ *             to draw it on the device from seed.
+ *   evals     host, k FP64: the approximate eigenvalues of A, descending.
+ *   evecs     device, n x k FP64 column-major orthonormal vectors (may be NULL).
+ * Returns NFL_ERR_BREAKDOWN when Q^T A Q has fewer than M positive
+ * eigenvalues, NFL_ERR_NONPOSITIVE_DEGREE as the products do.
+ */
+nfl_status nfl_nystrom_k_largest(nfl_plan *plan, int k, int L, int M, const double *G, uint64_t seed,
+                                 double *evals, double *evecs);
+
+/*
  * Conjugate gradients for (beta L_s + diag(s)) u = f, the system of Sec. 6.2.2
  * (eq. (ssl::system) is beta L_s + I).  Stops when ||r||_2 <= tol ||f||_2.
  *

@@ -43,3 +43,31 @@ def residual_norms(Aop, lam, V):
     for j in range(V.shape[1]):
         res.append(np.linalg.norm(Aop(V[:, j]) - lam[j] * V[:, j]))
     return np.array(res)
+
+
+def nystrom_gaussian(apply_A, G, k, M):
+    """Alg. 3 (Sec. 5.2, "Nystrom-Gaussian-NFFT"), step by step in numpy.
+
+    apply_A  callable: n x c block -> A times the block (column by column).
+    G        n x L random Gaussian block (passed in, so both sides use the same).
+    Returns the k largest approximate eigenvalues of A (descending) and the
+    matching orthonormal vectors (n x k).  numpy.linalg.qr / eigh are the
+    library primitives of the QR and eigen-decomposition steps.
+    """
+    G = np.asarray(G, dtype=np.float64)
+    Y = apply_A(G)                                   # step 3: Y = A G
+    Q, _ = np.linalg.qr(Y)                           #         Q = orth(Y)
+    B1 = apply_A(Q)                                  # step 4: B1 = A Q
+    B2 = Q.T @ B1                                    #         B2 = Q^T B1
+    B2 = 0.5 * (B2 + B2.T)
+    sig, U = np.linalg.eigh(B2)                      # step 5: M largest positive
+    order = np.argsort(sig)[::-1][:M]
+    sig, U = sig[order], U[:, order]
+    if not np.all(sig > 0.0):
+        raise ValueError("B2 has fewer than M positive eigenvalues")
+    Qh, Rh = np.linalg.qr(B1 @ U)                    # step 6: Qh Rh = B1 U_M
+    T = Rh @ np.diag(1.0 / sig) @ Rh.T               # step 7: eig of Rh Sigma^-1 Rh^T
+    lam, Uh = np.linalg.eigh(0.5 * (T + T.T))
+    V = Qh @ Uh
+    order = np.argsort(lam)[::-1][:k]                # step 8: k largest
+    return lam[order], V[:, order]

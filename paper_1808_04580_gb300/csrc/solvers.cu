@@ -539,3 +539,202 @@ nfl_status nfl_cg_solve_backward(nfl_plan *plan, nfl_plan *dplan, double beta, c
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ Alg. 3: Nystrom-Gaussian-NFFT
+namespace nfl {
+
+// Cyclic Jacobi iteration for a symmetric c x c matrix (host, FP64, row-major):
+// A = V diag(lam) V^T, V column j the eigenvector of lam[j].  Plane rotations
+// zero one off-diagonal pair at a time (the classical method; a few sweeps
+// converge quadratically for these small matrices).
+static bool jacobi_eig(std::vector<double> A, int c, std::vector<double> &lam, std::vector<double> &V) {
+    V.assign((size_t)c * c, 0.0);
+    for (int i = 0; i < c; ++i) V[(size_t)i * c + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < c; ++i)
+            for (int j = 0; j < c; ++j) {
+                const double a2 = A[(size_t)i * c + j] * A[(size_t)i * c + j];
+                tot += a2;
+                if (i != j) off += a2;
+            }
+        if (off <= 1e-30 * tot || off == 0.0) {
+            lam.resize(c);
+            for (int i = 0; i < c; ++i) lam[i] = A[(size_t)i * c + i];
+            return true;
+        }
+        for (int p = 0; p < c; ++p)
+            for (int q = p + 1; q < c; ++q) {
+                const double apq = A[(size_t)p * c + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[(size_t)q * c + q] - A[(size_t)p * c + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < c; ++k) {        // columns p, q
+                    const double akp = A[(size_t)k * c + p], akq = A[(size_t)k * c + q];
+                    A[(size_t)k * c + p] = cs * akp - sn * akq;
+                    A[(size_t)k * c + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < c; ++k) {        // rows p, q
+                    const double apk = A[(size_t)p * c + k], aqk = A[(size_t)q * c + k];
+                    A[(size_t)p * c + k] = cs * apk - sn * aqk;
+                    A[(size_t)q * c + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < c; ++k) {
+                    const double vkp = V[(size_t)k * c + p], vkq = V[(size_t)k * c + q];
+                    V[(size_t)k * c + p] = cs * vkp - sn * vkq;
+                    V[(size_t)k * c + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    return false;
+}
+
+// Orthonormalize the c columns of X (n x c, column-major, in place) by
+// Gram-Schmidt with one reorthogonalization (DGKS).  R (host, c x c, row-major,
+// upper triangular) receives X_in = X_out R; a column that falls below 1e-13
+// of its norm is dependent and becomes zero (R_jj = 0).
+static nfl_status gs_qr(Plan &P, double *X, int c, double *part, double *sc, std::vector<double> &R) {
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    const int vb = vec_blocks(P);
+    R.assign((size_t)c * c, 0.0);
+    std::vector<double> coef(c);
+    for (int j = 0; j < c; ++j) {
+        double *xj = X + (int64_t)j * n;
+        double n0 = 0.0;
+        if (dot(P, xj, xj, part, sc, &n0) != cudaSuccess) return NFL_ERR_CUDA;
+        if (!std::isfinite(n0)) return NFL_ERR_NAN;
+        for (int pass = 0; pass < 2 && j > 0; ++pass) {
+            dim3 g(kRedBlocks, j);
+            multidot_partials<<<g, 256, 0, s>>>(X, n, xj, part);
+            sum_partials<<<std::min(j, 1024), 256, 0, s>>>(part, kRedBlocks, j, sc);
+            sub_Qc<<<vb, 256, j * sizeof(double), s>>>(X, n, j, sc, xj);
+            if (cudaMemcpyAsync(coef.data(), sc, j * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return NFL_ERR_CUDA;
+            for (int i = 0; i < j; ++i) R[(size_t)i * c + j] += coef[i];
+        }
+        double nn = 0.0;
+        if (dot(P, xj, xj, part, sc, &nn) != cudaSuccess) return NFL_ERR_CUDA;
+        const double nrm = std::sqrt(nn);
+        const bool dependent = !(nrm > 1e-13 * std::sqrt(n0));
+        R[(size_t)j * c + j] = dependent ? 0.0 : nrm;
+        scale_copy<<<vb, 256, 0, s>>>(xj, xj, n, dependent ? 0.0 : 1.0 / nrm);
+    }
+    return NFL_OK;
+}
+
+// Y[:, j] = X R[:, j] for j < ncol_out, X n x c on the device, R host c x ncol_out row-major.
+static nfl_status times_small(Plan &P, const double *X, int c, const std::vector<double> &R, int ncol_out,
+                              double *Y, double *sc) {
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    std::vector<double> col(c);
+    for (int j = 0; j < ncol_out; ++j) {
+        for (int i = 0; i < c; ++i) col[i] = R[(size_t)i * ncol_out + j];
+        if (cudaMemcpyAsync(sc, col.data(), c * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return NFL_ERR_CUDA;
+        gemv_Qs<<<vec_blocks(P), 256, c * sizeof(double), s>>>(X, n, c, sc, Y + (int64_t)j * n);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return NFL_ERR_CUDA;
+    }
+    return NFL_OK;
+}
+
+}  // namespace nfl
+
+extern "C" {
+
+nfl_status nfl_nystrom_k_largest(nfl_plan *plan, int k, int L, int M, const double *G, uint64_t seed,
+                                 double *evals, double *evecs) {
+    using namespace nfl;
+    if (!plan || !evals || k < 1 || M < k || L < M) return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (L > P.n || L > 512) return NFL_ERR_INVALID_ARG;
+    if (!P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;               // step 2 (degrees of the plan)
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    Dev Yb, Bb, Cb, part, sc;
+    if (cudaMalloc(&Yb.buf, (size_t)n * L * 8) != cudaSuccess || cudaMalloc(&Bb.buf, (size_t)n * L * 8) != cudaSuccess ||
+        cudaMalloc(&Cb.buf, (size_t)n * M * 8) != cudaSuccess ||
+        cudaMalloc(&part.buf, (size_t)kRedBlocks * L * 8) != cudaSuccess || cudaMalloc(&sc.buf, (size_t)(L + 8) * 8) != cudaSuccess)
+        return NFL_ERR_OUT_OF_MEMORY;
+    double *Y = Yb.buf, *B1 = Bb.buf, *C = Cb.buf;
+    // step 3: Y = A G column by column, Q = orth(Y) (in place)
+    if (G) {
+        if (cudaMemcpyAsync(B1, G, (size_t)n * L * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return NFL_ERR_CUDA;
+    } else {
+        random_normal<<<vec_blocks(P), 256, 0, s>>>(B1, n * L, seed);
+    }
+    for (int j = 0; j < L; ++j) {
+        nfl_status st = run_column(P, OP_A, B1 + (int64_t)j * n, Y + (int64_t)j * n);
+        if (st != NFL_OK) return st;
+    }
+    std::vector<double> R;
+    nfl_status st = gs_qr(P, Y, L, part.buf, sc.buf, R);
+    if (st != NFL_OK) return st;
+    // step 4: B1 = A Q, B2 = Q^T B1 (symmetrized)
+    for (int j = 0; j < L; ++j) {
+        st = run_column(P, OP_A, Y + (int64_t)j * n, B1 + (int64_t)j * n);
+        if (st != NFL_OK) return st;
+    }
+    std::vector<double> B2((size_t)L * L);
+    for (int j = 0; j < L; ++j) {
+        dim3 g(kRedBlocks, L);
+        multidot_partials<<<g, 256, 0, s>>>(Y, n, B1 + (int64_t)j * n, part.buf);
+        sum_partials<<<std::min(L, 1024), 256, 0, s>>>(part.buf, kRedBlocks, L, sc.buf);
+        std::vector<double> col(L);
+        if (cudaMemcpyAsync(col.data(), sc.buf, L * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return NFL_ERR_CUDA;
+        for (int i = 0; i < L; ++i) B2[(size_t)i * L + j] = col[i];
+    }
+    for (int i = 0; i < L; ++i)
+        for (int j = i + 1; j < L; ++j) {
+            const double a = 0.5 * (B2[(size_t)i * L + j] + B2[(size_t)j * L + i]);
+            B2[(size_t)i * L + j] = B2[(size_t)j * L + i] = a;
+        }
+    // step 5: the M largest positive eigenvalues of B2 and their eigenvectors U_M (L x M)
+    std::vector<double> sig, U;
+    if (!jacobi_eig(B2, L, sig, U)) return NFL_ERR_NOT_CONVERGED;
+    std::vector<int> order(L);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return sig[a] > sig[b]; });
+    std::vector<double> UM((size_t)L * M), sigM(M);
+    for (int t = 0; t < M; ++t) {
+        sigM[t] = sig[order[t]];
+        if (!(sigM[t] > 0.0)) return NFL_ERR_BREAKDOWN;
+        for (int i = 0; i < L; ++i) UM[(size_t)i * M + t] = U[(size_t)i * L + order[t]];
+    }
+    // step 6: Qh Rh = B1 U_M
+    st = times_small(P, B1, L, UM, M, C, sc.buf);
+    if (st != NFL_OK) return st;
+    std::vector<double> Rh;
+    st = gs_qr(P, C, M, part.buf, sc.buf, Rh);
+    if (st != NFL_OK) return st;
+    // step 7: eig of T = Rh Sigma_M^{-1} Rh^T; V_M = Qh Uh
+    std::vector<double> T((size_t)M * M, 0.0);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double acc = 0.0;
+            for (int t = 0; t < M; ++t) acc += Rh[(size_t)i * M + t] * Rh[(size_t)j * M + t] / sigM[t];
+            T[(size_t)i * M + j] = acc;
+        }
+    std::vector<double> lam, Uh;
+    if (!jacobi_eig(T, M, lam, Uh)) return NFL_ERR_NOT_CONVERGED;
+    std::vector<int> ord(M);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+    // step 8: the k largest
+    for (int t = 0; t < k; ++t) evals[t] = lam[ord[t]];
+    if (evecs) {
+        std::vector<double> Uk((size_t)M * k);
+        for (int i = 0; i < M; ++i)
+            for (int t = 0; t < k; ++t) Uk[(size_t)i * k + t] = Uh[(size_t)i * M + ord[t]];
+        st = times_small(P, C, M, Uk, k, evecs, sc.buf);
+        if (st != NFL_OK) return st;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -66,6 +66,7 @@ SIGNATURES = {
     "nfl_apply_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                ctypes.POINTER(_L), _I]),
     "nfl_cg_solve_noalloc": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nfl_nystrom_k_largest": (_I, [_P, _I, _I, _I, _P, ctypes.c_uint64, _P, _P]),
     "nfl_cg_solve_backward": (_I, [_P, _P, _D, _P, _P, _P, _D, _I, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D),
                                    ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_plan_set_profiling": (_I, [_P, _I]),
@@ -224,6 +225,23 @@ class Plan:
         if check:
             _check(st, "nfl_lanczos_k_smallest")
         return evals, (evecs.t() if vectors else None), iters.value, st
+
+    def nystrom_k_largest(self, k, L, M, G=None, seed=0, vectors=True):
+        """Alg. 3: (eigenvalues of A descending (numpy), n x k vectors or None)."""
+        self._sync_stream()
+        gp = None
+        if G is not None:
+            G = _cuda_f64(G, "G")
+            if G.shape != (self.n, L):
+                raise ValueError("G must be (n, L)")
+            G = G.t().contiguous()                   # column-major n x L
+            gp = G.data_ptr()
+        evals = np.zeros(k, dtype=np.float64)
+        evecs = torch.empty((k, self.n), dtype=torch.float64, device=self.device) if vectors else None
+        st = _lib().nfl_nystrom_k_largest(self._h, int(k), int(L), int(M), gp, int(seed), evals.ctypes.data,
+                                          evecs.data_ptr() if vectors else None)
+        _check(st, "nfl_nystrom_k_largest")
+        return evals, (evecs.t() if vectors else None)
 
     def cg_solve(self, f, beta=1.0, shift=None, u0=None, tol=1e-10, maxit=1000, check=True, noalloc=False):
         """Solve (beta L_s + diag(shift)) u = f: (u, iters, relres, status).

@@ -42,6 +42,7 @@ struct PassArgs {
     int nA, nB;
     int64_t sA, sB;
     int Lin;
+    unsigned lin_magic;   // ceil(2^32 / Lin): e / Lin = umulhi(e, lin_magic) for e < 2^22
     int64_t oC, oA;
     int Lout;
     int n, logn, N;
@@ -51,6 +52,19 @@ struct PassArgs {
     int real_in, real_out;
     const double *abs_sum;  // int64 fixed-point input: sum |x~| of the spread call
 };
+
+// Grid value as a real of the FFT type.  int64 fixed point to FP32 through its
+// 32-bit halves (hi 2^32 + lo, both converted exactly or to nearest), which
+// stays on the FP32 pipe; the result is within one FP32 rounding of the value.
+template <typename T> __device__ __forceinline__ T to_real(float v) { return T(v); }
+template <typename T> __device__ __forceinline__ T to_real(double v) { return T(v); }
+template <typename T> __device__ __forceinline__ T to_real(long long v);
+template <> __device__ __forceinline__ float to_real<float>(long long v) {
+    const float hi = __int2float_rn((int)(v >> 32));
+    const float lo = __uint2float_rn((unsigned)(v & 0xFFFFFFFFll));
+    return fmaf(hi, 4294967296.0f, lo);
+}
+template <> __device__ __forceinline__ double to_real<double>(long long v) { return double(v); }
 
 // 2^-k for the fixed-point scale 2^k used by the spread kernel.
 __device__ __forceinline__ double fixed_point_unscale(double abs_sum) {
@@ -137,24 +151,24 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     for (int e = threadIdx.x; e < a.BB * n; e += blockDim.x) bx[e] = C{T(0), T(0)};
     __syncthreads();
 
-    double in_scale = 1.0;
-    if (std::is_same<TIN, long long>::value) in_scale = fixed_point_unscale(*a.abs_sum);
+    T in_scale = T(1);
+    if (std::is_same<TIN, long long>::value) in_scale = T(fixed_point_unscale(*a.abs_sum));
 
     // load
     for (int e = threadIdx.x; e < nb * a.Lin; e += blockDim.x) {
-        const int bb = e / a.Lin;
+        const int bb = (int)__umulhi((unsigned)e, a.lin_magic);
         const int c = e - bb * a.Lin;
         const int64_t src = ai * a.sA + (int64_t)(b0 + bb) * a.sB + c;
         C v;
         if (MODE == P_FWD_R2C || (MODE == P_FUSED && a.real_in)) {
             const TIN *in = reinterpret_cast<const TIN *>(a.in);
-            v = C{T(double(in[src]) * in_scale), T(0)};
+            v = C{to_real<T>(in[src]) * in_scale, T(0)};
         } else {
             v = reinterpret_cast<const C *>(a.in)[src];
         }
         if (MODE == P_INV_C2C) {
             const int k = c - N / 2;
-            bx[bb * n + ((k + n) % n)] = v;
+            bx[bb * n + ((k + n) & (n - 1))] = v;
         } else if (MODE == P_INV_C2R) {
             bx[bb * n + c] = v;
             if (c >= 1) bx[bb * n + (n - c)] = C{v.x, -v.y};
@@ -170,8 +184,8 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     if (MODE == P_FUSED) {
         const T *M = reinterpret_cast<const T *>(a.M);
         for (int e = threadIdx.x; e < a.BB * n; e += blockDim.x) {
-            const int bb = e / n;
-            const int q = e - bb * n;
+            const int bb = e >> a.logn;
+            const int q = e & (n - 1);
             const int k = q < n / 2 ? q : q - n;
             C v = res[e];
             if (bb < nb && k >= -N / 2 && k <= N / 2) {
@@ -188,12 +202,13 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     }
 
     // store, b fastest
+    const unsigned nb_magic = 0xFFFFFFFFu / (unsigned)nb + 1u;   // e / nb = umulhi(e, nb_magic), nb <= 16
     for (int e = threadIdx.x; e < nb * a.Lout; e += blockDim.x) {
-        const int cc = e / nb;
+        const int cc = nb == 1 ? e : (int)__umulhi((unsigned)e, nb_magic);
         const int bb = e - cc * nb;
         int idx;
         if (MODE == P_FWD_R2C) idx = cc;
-        else if (MODE == P_FWD_C2C) idx = (cc - N / 2 + n) % n;
+        else if (MODE == P_FWD_C2C) idx = (cc - N / 2 + n) & (n - 1);
         else idx = cc;
         const C v = res[bb * n + idx];
         const int64_t dst = cc * a.oC + (int64_t)ai * a.oA + b0 + bb;
@@ -210,6 +225,7 @@ static cudaError_t run_pass(Plan &P, PassArgs a) {
     BB = BB > 16 ? 16 : (BB < 1 ? 1 : BB);
     if (!std::is_same<T, float>::value && BB > 8) BB = 8;
     a.BB = BB;
+    a.lin_magic = (unsigned)((0x100000000ull + (unsigned)a.Lin - 1) / (unsigned)a.Lin);
     const int smem = 2 * BB * a.n * (int)sizeof(C);
     NFL_CUDA_TRY(cudaFuncSetAttribute(fft_pass<T, TIN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid((a.nB + BB - 1) / BB, a.nA);

@@ -294,6 +294,17 @@ nfl_status nfl_cg_solve_noalloc(nfl_plan *plan, double beta, const double *shift
 nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable);
 nfl_status nfl_plan_stage_times(nfl_plan *plan, double *ms, int64_t *columns);
 
+/*
+ * Failure-detection test hook; the paper has no counterpart.  kind 1 makes
+ * the tensor-core interpolation skip its MMAs, so its bounded waits (limited
+ * to 10 ms of device time in this mode, 2 s otherwise) run out: the kernel
+ * sets the plan's device_error (nfl_plan_info), skips its remaining work,
+ * frees its tensor memory and returns; nothing traps or hangs.  kind 0
+ * switches it off (device_error stays set for the plan).  Products made in
+ * this mode are meaningless.  NFL_ERR_INVALID_ARG for other kinds.
+ */
+nfl_status nfl_plan_inject_fault(nfl_plan *plan, int kind);
+
 /* Number of kernel launches one product column makes (for launch accounting). */
 nfl_status nfl_plan_kernels_per_column(const nfl_plan *plan, int *kernels);
 

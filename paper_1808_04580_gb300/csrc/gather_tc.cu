@@ -51,6 +51,8 @@ struct GatherTCArgs {
     double out_scale, k0;   // W x = out_scale f - K(0) x (caller's coordinates)
     int *error_flag;
     unsigned *counter;    // next work item, shared by all CTAs
+    int skip_mma;                 // fault test: the MMAs are never issued, so every wait runs out
+    unsigned long long wait_ns;   // limit of each bounded wait
     float poly[2 * kMaxM][kPolyCoef];   // window by taps, as in the plan
 };
 
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
                 if (failed) break;   // uniform: decided by __syncthreads_or below
-                if (tid == 0) {
+                if (tid == 0 && !a.skip_mma) {
                     const uint32_t aH = smem_u32(sA_hi), aL = smem_u32(sA_lo);
                     const uint32_t bH = smem_u32(sB_hi) + h * (N * 64), bL = smem_u32(sB_lo) + h * (N * 64);
                     int issued = 0;
@@ -269,14 +271,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 }
                 // bounded wait for the MMAs
                 {
-                    uint32_t done = 0, spins = 0;
-                    while (!done) {
-                        asm volatile(
-                            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                            : "=r"(done)
-                            : "r"(smem_u32(&mbar)), "r"(phase));
-                        if (!done && ++spins > kSpinLimit) break;
-                    }
+                    const bool done = mbar_wait_bounded(smem_u32(&mbar), phase, kSpinLimit, a.wait_ns);
                     // every thread takes the same decision (barriers below stay matched)
                     if (__syncthreads_or(!done)) {
                         failed = true;
@@ -338,12 +333,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     }
     if (failed) {
         // give MMAs still in flight a second bounded chance to finish before freeing TMEM
-        uint32_t done = 0, spins = 0;
-        while (!done && spins++ < kSpinLimit)
-            asm volatile(
-                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(smem_u32(&mbar)), "r"(phase ^ 1u));
+        mbar_wait_bounded(smem_u32(&mbar), phase ^ 1u, kSpinLimit, a.wait_ns);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -394,6 +384,8 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
     a.k0 = P.k0;
     a.error_flag = P.error_flag;
     a.counter = P.work_counter + 1;
+    a.skip_mma = P.fault_kind == 1 ? 1 : 0;
+    a.wait_ns = P.fault_kind == 1 ? 10000000ull : 2000000000ull;
     for (int j = 0; j < 2 * kMaxM; ++j)
         for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
     switch (P.m) {

@@ -89,6 +89,7 @@ struct Plan {
     double *scratch = nullptr;  // small device scalars (reductions, fixed-point scale)
     int *error_flag = nullptr;  // set by a kernel whose bounded wait ran out
     unsigned *work_counter = nullptr;   // [0] spread, [1] gather: next work item (reset per column)
+    int fault_kind = 0;         // fault test (nfl_plan_inject_fault): 1 = interpolation MMAs never issued
     int num_sms = 0;
 
     // stage timing: 5 events per timed column (before prep, spread, fft, gather, after)

@@ -826,6 +826,12 @@ void nfl_plan_destroy(nfl_plan *plan) {
     nfl::free_plan(P);
 }
 
+nfl_status nfl_plan_inject_fault(nfl_plan *plan, int kind) {
+    if (!plan || kind < 0 || kind > 1) return NFL_ERR_INVALID_ARG;
+    reinterpret_cast<nfl::Plan *>(plan)->fault_kind = kind;
+    return NFL_OK;
+}
+
 nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     if (!plan || !info) return NFL_ERR_INVALID_ARG;
     const Plan *P = reinterpret_cast<const Plan *>(plan);

@@ -42,21 +42,34 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
-// Wait for phase `parity` of an mbarrier, at most `limit` polls; true if it completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t parity, uint32_t limit) {
+// Device clock in nanoseconds.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier, at most `limit` polls and `limit_ns`
+// nanoseconds; true if it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t parity, uint32_t limit,
+                                                  uint64_t limit_ns = 2000000000ull) {
+    const uint64_t t0 = global_ns();
     uint32_t done = 0, spins = 0;
     while (!done) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(mbar_addr), "r"(parity));
-        if (!done && ++spins > limit) break;
+        if (done) break;
+        if (++spins > limit) break;
+        if ((spins & 31u) == 0u && global_ns() - t0 > limit_ns) break;
     }
     return done != 0;
 }
 
-// Spin limit of the bounded waits on an MMA-completion mbarrier: a wait that
-// runs out sets the plan's error flag and the kernel skips its remaining work.
+// Limits of the bounded waits on an MMA-completion mbarrier (polls, and 2 s of
+// device time unless a fault test shortens it): a wait that runs out sets the
+// plan's error flag and the kernel skips its remaining work.
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 }  // namespace nfl

@@ -72,6 +72,7 @@ SIGNATURES = {
     "nfl_plan_set_profiling": (_I, [_P, _I]),
     "nfl_plan_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
     "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
+    "nfl_plan_inject_fault": (_I, [_P, _I]),
     "nfl_status_string": (ctypes.c_char_p, [_I]),
 }
 
@@ -177,6 +178,10 @@ class Plan:
         cols = ctypes.c_int64(0)
         _check(_lib().nfl_plan_stage_times(self._h, ms, ctypes.byref(cols)), "nfl_plan_stage_times")
         return dict(prep=ms[0], spread=ms[1], fft=ms[2], gather=ms[3], columns=cols.value)
+
+    def inject_fault(self, kind):
+        """Failure-detection test hook (nfl_plan_inject_fault)."""
+        _check(_lib().nfl_plan_inject_fault(self._h, int(kind)), "nfl_plan_inject_fault")
 
     def kernels_per_column(self):
         k = ctypes.c_int(0)

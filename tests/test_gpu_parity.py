@@ -270,3 +270,15 @@ def test_cg_solve_matches_dense_solve():
     u, iters, relres, st = plan.cg_solve(gpu(f), beta=beta, shift=gpu(shift), tol=1e-12, maxit=2000)
     assert relres <= 1e-12
     assert rel(u.cpu().numpy(), u_ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("fp32c", 1e-6), ("fp32", 1e-6)])
+def test_repeat_products_agree(prec, tol):
+    """Run-to-run spread of the same product (atomic order varies, nothing else)."""
+    v = _cloud("clusters", 20000, 3, seed=60)
+    x = workloads.rhs(20000, seed=61)
+    plan = Plan(gpu(v), 0.3, 32, 6, 6, -1.0, prec)
+    xt = gpu(x)
+    ys = [plan.apply_W(xt) for _ in range(3)]
+    for y in ys[1:]:
+        assert float(torch.linalg.norm(y - ys[0]) / torch.linalg.norm(ys[0])) < tol

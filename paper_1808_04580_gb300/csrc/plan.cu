@@ -128,9 +128,17 @@ __global__ void count_keys(const double *v, int64_t n, Geometry G, int cells_per
         int cell[3];
         double frac[3];
         node_cell(v, i, G, cell, frac);
+        // cell inside the tile; in 3-D ordered (axis 0, axis 2, axis 1) so that the
+        // cells of one (axis 0, axis 2) column of the tile are contiguous
         int local = 0;
-        if (cells_per_tile > 1)
-            for (int a = 0; a < G.d; ++a) local = local * G.tile_edge + cell[a] % G.tile_edge;
+        if (cells_per_tile > 1) {
+            if (G.d == 3) {
+                const int te = G.tile_edge;
+                local = ((cell[0] % te) * te + cell[2] % te) * te + cell[1] % te;
+            } else {
+                for (int a = 0; a < G.d; ++a) local = local * G.tile_edge + cell[a] % G.tile_edge;
+            }
+        }
         const int key = tile_of(cell, G) * cells_per_tile + local;
         key_of[i] = key;
         rank[i] = atomicAdd(&count[key], 1);

@@ -58,17 +58,25 @@ struct WarpGeom {
     static constexpr int LPB = M == 6 ? 2 : (M == 4 ? 4 : (M == 3 ? 3 : 2));   // lanes per support row jb
     static constexpr int CPL = TAPS / LPB;        // support columns per lane
     static constexpr int RP = TAPS / 2;           // row pairs (ja, ja + 1)
-    static constexpr int LANES = TAPS * LPB;      // lanes that accumulate
+    // FULLB: the lanes cover all PA rows of axis 1 of the tile (when they fit in a
+    // warp), so a cell run is a whole (axis 0, axis 2) column of the tile and the
+    // flushes are TE times rarer; otherwise the 2M support rows of one cell
+    static constexpr bool FULLB = PA * LPB <= 32;
+    static constexpr int JB = FULLB ? PA : TAPS;  // axis-1 rows covered by the lanes
+    static constexpr int LANES = JB * LPB;        // lanes that accumulate
     static constexpr int NG = 4;                  // warps (tile copies) per CTA
     static constexpr int S = 32;                  // nodes per slice
     static constexpr int TILE = (PA3 + 3) / 4 * 4;
     // per node, rows of staged taps (axes 0, 1, 2) whose strides are odd multiples
     // of 16 bytes, so the 16-byte stores of the 32 lanes fall in distinct bank groups
     static constexpr int R1 = ((TAPS + 3) / 4) % 2 ? (TAPS + 3) / 4 * 4 : (TAPS + 3) / 4 * 4 + 4;   // floats per row
+    // axis-1 rows: the taps placed over all JB rows for FULLB
+    static constexpr int RB = FULLB ? (JB + 3) / 4 * 4 : R1;
     static constexpr int W_BYTES = S * R1 * 4;
-    static constexpr int WARP_BYTES = TILE * 4 + 3 * W_BYTES;
+    static constexpr int WB_BYTES = S * RB * 4;
+    static constexpr int WARP_BYTES = TILE * 4 + 2 * W_BYTES + WB_BYTES;
     static constexpr int SMEM = NG * WARP_BYTES;
-    static_assert(TAPS * LPB == LANES && LANES <= 32 && CPL % 2 == 0, "lane layout");
+    static_assert(LANES <= 32 && CPL % 2 == 0, "lane layout");
     static_assert(WARP_BYTES % 16 == 0, "16-byte aligned per-warp areas");
 };
 
@@ -76,21 +84,21 @@ template <int M, int TE, bool FIXED>
 __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(SpreadWarpArgs a) {
     using G = WarpGeom<M, TE>;
     constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, RP = G::RP, CPL = G::CPL, S = G::S, NG = G::NG,
-                  R1 = G::R1;
+                  R1 = G::R1, RB = G::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     unsigned char *mine = smem_raw + g * G::WARP_BYTES;
     float *tile = reinterpret_cast<float *>(mine);
     float *w0s = reinterpret_cast<float *>(mine + G::TILE * 4);                     // [S][R1]
-    float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W_BYTES);       // [S][R1]
-    float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + 2 * G::W_BYTES);   // [S][R1]
+    float *w2s = reinterpret_cast<float *>(mine + G::TILE * 4 + G::W_BYTES);       // [S][R1]
+    float *w1s = reinterpret_cast<float *>(mine + G::TILE * 4 + 2 * G::W_BYTES);   // [S][RB]
     __shared__ __align__(16) float2 polys[M][kPolyCoef];
     __shared__ unsigned next_item;
 
     const bool acc_lane = lane < G::LANES;
-    const int jb = acc_lane ? lane / G::LPB : 0;
+    const int jb = acc_lane ? lane / G::LPB : 0;   // support row of the cell, or tile row for FULLB
     // columns jc = c * LPB + hseg, c < CPL: interleaved, so that in a flush the
-    // 24 lanes (m = 6) address 24 different shared-memory banks
+    // lanes (30 for m = 6) address different shared-memory banks
     const int hseg = acc_lane ? lane - jb * G::LPB : 0;
     for (int e = threadIdx.x; e < M * kPolyCoef; e += NG * 32) {
         const int q = e / kPolyCoef, k = e - q * kPolyCoef;
@@ -108,7 +116,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
     auto flush = [&](int o) {
         __syncwarp();
         if (acc_lane) {
-            const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
+            const int s0 = o & 255, s1 = G::FULLB ? 0 : (o >> 8) & 255, s2 = o >> 16;
             float *col = tile + (s0 * PA + s1 + jb) * PA + s2 + hseg;
 #pragma unroll
             for (int p = 0; p < RP; ++p)
@@ -125,7 +133,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
     // INIT sets them (first node after a flush), otherwise adds
     auto node = [&](int q, auto init) {
         constexpr bool INIT = decltype(init)::value;
-        const float w1v = w1s[q * R1 + jb];
+        const float w1v = w1s[q * RB + jb];
         const float2 *r2 = reinterpret_cast<const float2 *>(w2s + q * R1 + hseg * CPL);
         unsigned long long coef[CPL];
 #pragma unroll
@@ -185,9 +193,12 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
             {
                 // stage node `lane` of the slice
                 float f[3];
+                int s1 = 0;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
-                    o |= (valid ? cell_axis(pn.cell, ax) - tc[ax] * TE : 0) << (8 * ax);
+                    const int sa = valid ? cell_axis(pn.cell, ax) - tc[ax] * TE : 0;
+                    if (ax == 1) s1 = sa;
+                    if (ax != 1 || !G::FULLB) o |= sa << (8 * ax);     // FULLB runs ignore axis 1
                     f[ax] = valid ? pn.f[ax] : 0.f;
                 }
                 const float xv = xn;
@@ -220,23 +231,40 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                 }
                 // 16-byte stores of this lane's rows
                 float4 *r0 = reinterpret_cast<float4 *>(w0s + lane * R1);
-                float4 *r1 = reinterpret_cast<float4 *>(w1s + lane * R1);
+                float4 *r1 = reinterpret_cast<float4 *>(w1s + lane * RB);
                 float4 *r2 = reinterpret_cast<float4 *>(w2s + lane * R1);
 #pragma unroll
                 for (int j = 0; j < (TAPS + 3) / 4; ++j) {
-                    float v0[4], v1[4], v2[4];
+                    float v0[4], v2[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const bool in = 4 * j + u < TAPS;
                         v0[u] = in ? t0[(4 * j + u) % TAPS] : 0.f;
-                        v1[u] = in ? t1[(4 * j + u) % TAPS] : 0.f;
                         // axis 2 de-interleaved: position h CPL + c holds tap c LPB + h
                         const int r = (4 * j + u) % TAPS;
                         v2[u] = in ? t2[(r % CPL) * G::LPB + r / CPL] : 0.f;
                     }
                     r0[j] = make_float4(v0[0], v0[1], v0[2], v0[3]);
-                    r1[j] = make_float4(v1[0], v1[1], v1[2], v1[3]);
                     r2[j] = make_float4(v2[0], v2[1], v2[2], v2[3]);
+                }
+                // axis 1: FULLB places the taps at the node's tile row s1 (selects, no indexing)
+#pragma unroll
+                for (int j = 0; j < RB / 4; ++j) {
+                    float v1[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int row = 4 * j + u;
+                        float val = 0.f;
+                        if (G::FULLB) {
+#pragma unroll
+                            for (int d = 0; d < TE; ++d)
+                                if (row - d >= 0 && row - d < TAPS) val = (s1 == d) ? t1[row - d] : val;
+                        } else if (row < TAPS) {
+                            val = t1[row];
+                        }
+                        v1[u] = val;
+                    }
+                    r1[j] = make_float4(v1[0], v1[1], v1[2], v1[3]);
                 }
             }
             const int prev = __shfl_up_sync(0xffffffffu, o, 1);

@@ -56,19 +56,19 @@ struct GatherTCArgs {
     float poly[2 * kMaxM][kPolyCoef];   // window by taps, as in the plan
 };
 
-// out[q] = tap[q - s] for 0 <= q - s < TAPS, else 0, with s in [0, TE): the
-// node's taps placed at its tile-local cell offset (selects, no indexing).
+// out[q] = tap[q - s] for 0 <= q - s < TAPS, else 0, with s in [0, TE) and TE a
+// power of two: the node's taps placed at its tile-local cell offset by a
+// logarithmic shifter (one select per entry and bit of s, no indexing).
 template <int TAPS, int PAD, int TE>
 __device__ __forceinline__ void place_taps(const float (&tap)[TAPS], int s, float (&out)[PAD]) {
+    static_assert((TE & (TE - 1)) == 0 && TAPS + TE - 1 <= PAD, "shifter layout");
 #pragma unroll
-    for (int q = 0; q < PAD; ++q) {
-        float v = 0.f;
+    for (int q = 0; q < PAD; ++q) out[q] = q < TAPS ? tap[q] : 0.f;
 #pragma unroll
-        for (int d = 0; d < TE; ++d) {
-            const int j = q - d;
-            if (j >= 0 && j < TAPS) v = (s == d) ? tap[j] : v;
-        }
-        out[q] = v;
+    for (int bit = 1; bit < TE; bit <<= 1) {
+        const bool on = (s & bit) != 0;
+#pragma unroll
+        for (int q = PAD - 1; q >= 0; --q) out[q] = on ? (q >= bit ? out[q - bit] : 0.f) : out[q];
     }
 }
 
@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     using G = TCGeom<M, TE>;
     constexpr int PA = G::PA, N = G::N, NH = G::NH, NCOL = G::NCOL, TAPS = 2 * M;
     static_assert(PA <= 16, "K is padded to 16");
+    static_assert(kPolyCoef % 2 == 0, "coefficients loaded in pairs");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sA_hi = smem_raw;
     unsigned char *sA_lo = sA_hi + G::A_BYTES;
@@ -193,12 +194,19 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                     const unsigned long long T2 = pack2(fmaf(2.f, f2, -1.f), fmaf(2.f, f2, -1.f));
 #pragma unroll
                     for (int q = 0; q < M; ++q) {
-                        unsigned long long h1 = pc[q * kPolyCoef + kPolyCoef - 1], h2 = h1;
+                        // coefficient pairs (k, k + 1) with 16-byte loads; Horner from k = 9 down
+                        const ulonglong2 *pq = reinterpret_cast<const ulonglong2 *>(pc + q * kPolyCoef);
+                        ulonglong2 cc = pq[kPolyCoef / 2 - 1];
+                        unsigned long long h1 = cc.y, h2 = cc.y;
+                        h1 = ffma2(h1, T1, cc.x);
+                        h2 = ffma2(h2, T2, cc.x);
 #pragma unroll
-                        for (int k = kPolyCoef - 2; k >= 0; --k) {
-                            const unsigned long long c = pc[q * kPolyCoef + k];
-                            h1 = ffma2(h1, T1, c);
-                            h2 = ffma2(h2, T2, c);
+                        for (int i = kPolyCoef / 2 - 2; i >= 0; --i) {
+                            cc = pq[i];
+                            h1 = ffma2(h1, T1, cc.y);
+                            h2 = ffma2(h2, T2, cc.y);
+                            h1 = ffma2(h1, T1, cc.x);
+                            h2 = ffma2(h2, T2, cc.x);
                         }
                         tap1[2 * q] = lane_of(h1, 0);
                         tap1[2 * q + 1] = lane_of(h1, 1);
@@ -214,9 +222,15 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                     const unsigned long long T0 = pack2(fmaf(2.f, f0, -1.f), fmaf(2.f, f0, -1.f));
 #pragma unroll
                     for (int q = 0; q < M; ++q) {
-                        unsigned long long h0 = pc[q * kPolyCoef + kPolyCoef - 1];
+                        const ulonglong2 *pq = reinterpret_cast<const ulonglong2 *>(pc + q * kPolyCoef);
+                        ulonglong2 cc = pq[kPolyCoef / 2 - 1];
+                        unsigned long long h0 = ffma2(cc.y, T0, cc.x);
 #pragma unroll
-                        for (int k = kPolyCoef - 2; k >= 0; --k) h0 = ffma2(h0, T0, pc[q * kPolyCoef + k]);
+                        for (int i = kPolyCoef / 2 - 2; i >= 0; --i) {
+                            cc = pq[i];
+                            h0 = ffma2(h0, T0, cc.y);
+                            h0 = ffma2(h0, T0, cc.x);
+                        }
                         tap0[2 * q] = live ? lane_of(h0, 0) : 0.f;
                         tap0[2 * q + 1] = live ? lane_of(h0, 1) : 0.f;
                     }

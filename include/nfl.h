@@ -165,6 +165,26 @@ nfl_status nfl_apply_Ls(nfl_plan *plan, const double *x, int64_t ldx,
                         double *y, int64_t ldy, int nrhs);
 
 /*
+ * y = op(x) for blocks in HOST memory, op 0 = W, 1 = A, 2 = L_s (the products
+ * of nfl_apply_W, nfl_apply_A and nfl_apply_Ls: Alg. 1, Alg. 2 step 5).
+ * Column c is copied to a device slot of the plan, multiplied on the plan's
+ * stream and copied back; the copies run on two streams the plan creates on
+ * first use, so column c + 1 travels in and column c - 1 travels out while
+ * column c is multiplied.  The copies overlap the products only when the
+ * host memory is page-locked (cudaHostAlloc, cudaHostRegister); pageable
+ * memory gives the same result without the overlap.  Any memory the CUDA
+ * runtime can copy from (cudaMemcpyDefault) is accepted.
+ *   x, y     FP64 blocks of nrhs >= 1 columns, leading dimensions ldx, ldy >= n;
+ *            they must not overlap.  The library reads x and writes y only
+ *            during the call.
+ * The plan allocates 6 n FP64 of device staging on first use and keeps it
+ * until nfl_plan_destroy.  Synchronizes the host: y is complete when the call
+ * returns, and after an error no copy is still running.
+ */
+nfl_status nfl_apply_host(nfl_plan *plan, int op, const double *x, int64_t ldx,
+                          double *y, int64_t ldy, int nrhs);
+
+/*
  * Products for many independent graphs in one call (a batch of plans):
  * y_g = op(x_g) for g < G with op 0 = W, 1 = A, 2 = L_s, each x_g / y_g a
  * device block of nrhs columns with leading dimension ld[g] >= n_g.  All

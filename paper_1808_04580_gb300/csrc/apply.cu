@@ -50,9 +50,75 @@ static nfl_status apply(nfl_plan *plan, int op, const double *x, int64_t ldx, do
     return NFL_OK;
 }
 
+// Products with host-resident blocks.  Column c goes through device slot
+// c mod kHostSlots: copied in on the h2d stream, multiplied on the plan's
+// stream, copied out on the d2h stream.  Events order the three streams, so
+// column c + 1 travels in and column c - 1 travels out while column c is
+// multiplied, and a slot is refilled only after its previous column is done
+// with it.
+static cudaError_t host_pipeline_init(Plan &P) {
+    if (!P.host_stage) NFL_CUDA_TRY(cudaMalloc(&P.host_stage, sizeof(double) * 2 * kHostSlots * (size_t)P.n));
+    if (!P.h2d) NFL_CUDA_TRY(cudaStreamCreateWithFlags(&P.h2d, cudaStreamNonBlocking));
+    if (!P.d2h) NFL_CUDA_TRY(cudaStreamCreateWithFlags(&P.d2h, cudaStreamNonBlocking));
+    if (!P.ev_start) NFL_CUDA_TRY(cudaEventCreateWithFlags(&P.ev_start, cudaEventDisableTiming));
+    for (int s = 0; s < kHostSlots; ++s) {
+        if (!P.ev_in[s]) NFL_CUDA_TRY(cudaEventCreateWithFlags(&P.ev_in[s], cudaEventDisableTiming));
+        if (!P.ev_done[s]) NFL_CUDA_TRY(cudaEventCreateWithFlags(&P.ev_done[s], cudaEventDisableTiming));
+        if (!P.ev_out[s]) NFL_CUDA_TRY(cudaEventCreateWithFlags(&P.ev_out[s], cudaEventDisableTiming));
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t issue_host_column(Plan &P, int op, const double *x, double *y, int c, nfl_status &st) {
+    const int s = c % kHostSlots;
+    const size_t bytes = sizeof(double) * (size_t)P.n;
+    double *xs = P.host_stage + (size_t)s * P.n;
+    double *ys = P.host_stage + (size_t)(kHostSlots + s) * P.n;
+    if (c >= kHostSlots) NFL_CUDA_TRY(cudaStreamWaitEvent(P.h2d, P.ev_done[s], 0));   // slot's x read
+    NFL_CUDA_TRY(cudaMemcpyAsync(xs, x, bytes, cudaMemcpyDefault, P.h2d));
+    NFL_CUDA_TRY(cudaEventRecord(P.ev_in[s], P.h2d));
+    NFL_CUDA_TRY(cudaStreamWaitEvent(P.stream, P.ev_in[s], 0));
+    if (c >= kHostSlots) NFL_CUDA_TRY(cudaStreamWaitEvent(P.stream, P.ev_out[s], 0));  // slot's y sent
+    st = run_column(P, op, xs, ys);
+    if (st != NFL_OK) return cudaSuccess;
+    NFL_CUDA_TRY(cudaEventRecord(P.ev_done[s], P.stream));
+    NFL_CUDA_TRY(cudaStreamWaitEvent(P.d2h, P.ev_done[s], 0));
+    NFL_CUDA_TRY(cudaMemcpyAsync(y, ys, bytes, cudaMemcpyDefault, P.d2h));
+    return cudaEventRecord(P.ev_out[s], P.d2h);
+}
+
+static nfl_status apply_host(nfl_plan *plan, int op, const double *x, int64_t ldx, double *y, int64_t ldy,
+                             int nrhs) {
+    if (!plan || !x || !y || nrhs < 1 || op < 0 || op > 2) return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (ldx < P.n || ldy < P.n) return NFL_ERR_INVALID_ARG;
+    const int ops[3] = {OP_W, OP_A, OP_LS};
+    if (ops[op] != OP_W && !P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
+    NFL_STATUS_TRY(host_pipeline_init(P));
+    nfl_status st = NFL_OK;
+    cudaError_t e = cudaEventRecord(P.ev_start, P.stream);   // copies follow the work queued before
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.h2d, P.ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.d2h, P.ev_start, 0);
+    for (int c = 0; c < nrhs && e == cudaSuccess && st == NFL_OK; ++c)
+        e = issue_host_column(P, ops[op], x + c * ldx, y + c * ldy, c, st);
+    // wait for everything issued, also after an error: y is final and x free on return
+    const cudaError_t e1 = cudaStreamSynchronize(P.h2d);
+    const cudaError_t e2 = cudaStreamSynchronize(P.stream);
+    const cudaError_t e3 = cudaStreamSynchronize(P.d2h);
+    if (st != NFL_OK) return st;
+    for (cudaError_t ei : {e, e1, e2, e3})
+        if (ei != cudaSuccess) return ei == cudaErrorMemoryAllocation ? NFL_ERR_OUT_OF_MEMORY : NFL_ERR_CUDA;
+    return NFL_OK;
+}
+
 }  // namespace nfl
 
 extern "C" {
+
+nfl_status nfl_apply_host(nfl_plan *plan, int op, const double *x, int64_t ldx, double *y, int64_t ldy,
+                          int nrhs) {
+    return nfl::apply_host(plan, op, x, ldx, y, ldy, nrhs);
+}
 
 nfl_status nfl_apply_W(nfl_plan *plan, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
     return nfl::apply(plan, nfl::OP_W, x, ldx, y, ldy, nrhs);

@@ -33,6 +33,7 @@ struct WorkItem {
 };
 
 constexpr int kMaxM = 12;
+constexpr int kHostSlots = 3;   // device staging slots per direction for host-buffer products
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 
 struct Plan {
@@ -91,6 +92,13 @@ struct Plan {
     unsigned *work_counter = nullptr;   // [0] spread, [1] gather: next work item (reset per column)
     int fault_kind = 0;         // fault test (nfl_plan_inject_fault): 1 = interpolation MMAs never issued
     int num_sms = 0;
+
+    // host-buffer products (nfl_apply_host), made on first use: kHostSlots device
+    // slots for x columns followed by kHostSlots for y columns, and two copy streams
+    double *host_stage = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_start = nullptr;
+    cudaEvent_t ev_in[kHostSlots] = {}, ev_done[kHostSlots] = {}, ev_out[kHostSlots] = {};
 
     // stage timing: 5 events per timed column (before prep, spread, fft, gather, after)
     bool profile = false;

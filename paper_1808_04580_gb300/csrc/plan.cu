@@ -508,6 +508,17 @@ nfl_status compute_coefficients(Plan &P) {
 static void free_plan(Plan *P) {
     if (!P) return;
     for (cudaEvent_t e : P->events) cudaEventDestroy(e);
+    if (P->h2d) cudaStreamSynchronize(P->h2d);
+    if (P->d2h) cudaStreamSynchronize(P->d2h);
+    for (int s = 0; s < kHostSlots; ++s) {
+        if (P->ev_in[s]) cudaEventDestroy(P->ev_in[s]);
+        if (P->ev_done[s]) cudaEventDestroy(P->ev_done[s]);
+        if (P->ev_out[s]) cudaEventDestroy(P->ev_out[s]);
+    }
+    if (P->ev_start) cudaEventDestroy(P->ev_start);
+    if (P->h2d) cudaStreamDestroy(P->h2d);
+    if (P->d2h) cudaStreamDestroy(P->d2h);
+    cudaFree(P->host_stage);
     cudaFree(P->items);
     cudaFree(P->pts);
     cudaFree(P->perm);

@@ -61,6 +61,7 @@ SIGNATURES = {
     "nfl_apply_W": (_I, [_P, _P, _L, _P, _L, _I]),
     "nfl_apply_A": (_I, [_P, _P, _L, _P, _L, _I]),
     "nfl_apply_Ls": (_I, [_P, _P, _L, _P, _L, _I]),
+    "nfl_apply_host": (_I, [_P, _I, _P, _L, _P, _L, _I]),
     "nfl_lanczos_k_smallest": (_I, [_P, _I, _D, _I, ctypes.c_uint64, _P, _P, ctypes.POINTER(_I)]),
     "nfl_cg_solve": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_apply_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -215,6 +216,36 @@ class Plan:
     def apply_Ls(self, x, out=None):
         """L_s x = x - A_E x."""
         return self._apply(_lib().nfl_apply_Ls, "nfl_apply_Ls", x, out)
+
+    def apply_host(self, x, op="Ls", out=None):
+        """op(x) for a HOST float64 block, op in "W", "A", "Ls" (nfl_apply_host).
+
+        x: CPU tensor (n,) or (n, r); the columns travel to the device and back
+        in a pipeline that overlaps the copies with the products when x and out
+        are in page-locked memory (``pin_memory()``).  Column-major storage, as
+        ``X.t()`` of a contiguous (r, n) tensor, is used in place.  Returns a CPU
+        tensor shaped like x (``out``: a contiguous (r, n) or (n,) CPU tensor).
+        """
+        if not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype != torch.float64:
+            raise TypeError("x must be a CPU float64 tensor")
+        if x.dim() == 1:
+            if x.shape[0] != self.n:
+                raise ValueError("x has %d rows, plan has %d" % (x.shape[0], self.n))
+            xc, r, vec = x.contiguous(), 1, True
+        elif x.dim() == 2 and x.shape[0] == self.n:
+            xc, r, vec = x.t().contiguous(), x.shape[1], False
+        else:
+            raise ValueError("x must be (n,) or (n, r)")
+        if out is None:
+            y = torch.empty_like(xc, pin_memory=xc.is_pinned())
+        else:
+            if out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != xc.numel():
+                raise ValueError("out must be a contiguous CPU float64 tensor of r x n elements")
+            y = out
+        self._sync_stream()
+        _check(_lib().nfl_apply_host(self._h, _OPS[op], xc.data_ptr(), self.n, y.data_ptr(), self.n, r),
+               "nfl_apply_host")
+        return y if vec else y.view(r, self.n).t()
 
     def lanczos_k_smallest(self, k, tol=1e-10, maxit=None, seed=0, vectors=True, check=True):
         """k smallest eigenpairs of L_s: (evals ndarray ascending, evecs (n, k) tensor or None, iters, status)."""

@@ -68,3 +68,16 @@ def test_invalid_arguments_rejected_on_host(lib):
     for args in bad:
         assert f(*args, None, ctypes.byref(out)) == 1, args
         assert out.value is None
+
+
+def test_host_products_reject_bad_arguments_without_gpu(lib):
+    f = lib.nfl_apply_host
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_int64, ctypes.c_int]
+    buf = (ctypes.c_double * 8)()
+    assert f(None, 2, buf, 4, buf, 4, 1) == 1                      # no plan
+    assert f(ctypes.c_void_p(16), 2, None, 4, buf, 4, 1) == 1      # no x
+    assert f(ctypes.c_void_p(16), 3, buf, 4, buf, 4, 1) == 1       # unknown op
+    assert f(ctypes.c_void_p(16), -1, buf, 4, buf, 4, 1) == 1      # unknown op
+    assert f(ctypes.c_void_p(16), 2, buf, 4, buf, 4, 0) == 1       # no columns

@@ -282,6 +282,31 @@ nfl_status nfl_cg_solve_backward(nfl_plan *plan, nfl_plan *dplan, double beta, c
                                  double *relres);
 
 /*
+ * Gradient of the bilinear form a^T A_E b (A = D^{-1/2} W D^{-1/2}, Sec. 2,
+ * eq. (nomlap)) with respect to the node coordinates, the degrees d = W 1
+ * moving with the nodes.  Differentiating A, with a~ = D^{-1/2} a,
+ * b~ = D^{-1/2} b and c = (a~ (W b~) + b~ (W a~)) / d:
+ *   a^T dA b = sum_ij dW_ij (a~_i b~_j - c_i / 2),
+ * and for the Gaussian (Sec. 2, eq. (W_gaussian)), grad K(y) = -(2 / sigma^2) y K(y):
+ *   g_k = -(2 / sigma^2) (y_k S0_k - S1_k),
+ *   S0 = a~ (W b~) + b~ (W a~) - c d / 2 - (W c) / 2,
+ *   S1 = a~ W(b~ y) + b~ W(a~ y) - c (W y) / 2 - W(c y) / 2,
+ * y = v - center (any shift gives the same g; the plan's centre keeps the
+ * products well scaled).  3 + 4 d fast products with W, all with the
+ * plan's kernel (even, so the plan's coefficients serve).  With
+ * a = lambda, b = u of nfl_cg_solve_backward, beta g is dl/dv of the
+ * differentiable solve of Sec. 6.2.2.
+ *   plan    NFL_KERNEL_GAUSSIAN plan (others: NFL_ERR_INVALID_ARG).
+ *   v       device n x d FP64 row-major: the nodes the plan was created with.
+ *   a, b    device n FP64.
+ *   grad    device n x d FP64 row-major (out).
+ * Synchronizes the plan's stream.  Allocates 15 n FP64 of device scratch.
+ */
+nfl_status nfl_form_grad_nodes(nfl_plan *plan, const double *v, const double *a, const double *b,
+                               double *grad);
+
+
+/*
  * nfl_cg_solve without device allocation.  The paper has no counterpart:
  * this is a deployment variant of nfl_cg_solve for callers that cannot
  * call cudaMalloc / cudaFree while they solve (work captured into a CUDA

@@ -16,7 +16,9 @@ Pins (tests/test_oracle_direct.py): n = 1 and n = 2 closed forms; L 1 = 0;
 L_s D^{1/2} 1 = 0; the quadratic form u^T L u = 1/2 sum W_ji (u_j - u_i)^2
 (Sec. 2) by an explicit pair loop; spectrum of L_s in [0, 2] with a zero
 eigenvalue; c well-separated clusters give c (numerically) zero eigenvalues;
-the C row sums against the dense matrix.
+the C row sums against the dense matrix; the node-coordinate gradient of
+a^T A b against central differences of the dense form, its translation
+invariance (the node gradients sum to zero) and n = 2 (A is constant).
 """
 import ctypes
 import os
@@ -82,6 +84,24 @@ def laplacian(v, sigma, kernel="gaussian"):
 # Plain-C row sums for large n.
 
 _LIB = None
+
+
+def form_grad_nodes(v, sigma, a, b):
+    """Gradient of G(v) = a^T A(v) b in the node coordinates (Gaussian kernel), by
+    the chain rule on the dense matrices: A_ij = W_ij / sqrt(d_i d_j) with
+    d_i = sum_l W_il, so dG/dW_ij = a~_i b~_j + dG/dd_i with a~ = a / sqrt(d),
+    b~ = b / sqrt(d), dG/dd_i = -(a~_i (W b~)_i + b~_i (W a~)_i) / (2 d_i); and
+    dW_ij/dv_k = -(2 / sigma^2) W_ij (v_i - v_j) (delta_ik - delta_jk)
+    (Sec. 2, eqs. (W_gaussian) and (nomlap)).  Returns n x d.
+    """
+    v = np.asarray(v, dtype=np.float64)
+    W = weight_matrix(v, sigma)
+    d = W.sum(axis=1)
+    at, bt = a / np.sqrt(d), b / np.sqrt(d)
+    gd = -0.5 * (at * (W @ bt) + bt * (W @ at)) / d
+    M = np.outer(at, bt) + gd[:, None]                  # dG/dW_ij
+    T = (M * W)[:, :, None] * (v[:, None, :] - v[None, :, :])
+    return -(2.0 / sigma ** 2) * (T.sum(axis=1) - T.sum(axis=0))
 
 
 def _lib():

@@ -540,6 +540,87 @@ nfl_status nfl_cg_solve_backward(nfl_plan *plan, nfl_plan *dplan, double beta, c
 
 }  // extern "C"
 
+// ------------------------------------- gradient of a~^T W b~ in the node coordinates
+namespace nfl {
+
+// c = (a~ (W b~) + b~ (W a~)) / d
+__global__ void form_c(const double *at, const double *bt, const double *Wa, const double *Wb, const double *d,
+                       int64_t n, double *c) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c[i] = (at[i] * Wb[i] + bt[i] * Wa[i]) / d[i];
+}
+
+// S0 = a~ (W b~) + b~ (W a~) - c d / 2 - (W c) / 2
+__global__ void form_s0(const double *at, const double *bt, const double *Wa, const double *Wb, const double *c,
+                        const double *d, const double *Wc, int64_t n, double *S0) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        S0[i] = at[i] * Wb[i] + bt[i] * Wa[i] - 0.5 * c[i] * d[i] - 0.5 * Wc[i];
+}
+
+// columns (b~ y, a~ y, y, c y) of X (n x 4, column-major) for y = v_alpha - center_alpha
+__global__ void form_columns(const double *v, int dim, int alpha, double center, const double *at, const double *bt,
+                             const double *c, int64_t n, double *X) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double y = v[i * dim + alpha] - center;
+        X[i] = bt[i] * y;
+        X[i + n] = at[i] * y;
+        X[i + 2 * n] = y;
+        X[i + 3 * n] = c[i] * y;
+    }
+}
+
+// grad[i, alpha] = scale (y_i S0_i - (a~_i Y0_i + b~_i Y1_i - c_i Y2_i / 2 - Y3_i / 2))
+__global__ void form_grad_axis(const double *v, int dim, int alpha, double center, const double *S0,
+                               const double *at, const double *bt, const double *c, const double *Y, int64_t n,
+                               double scale, double *grad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double y = v[i * dim + alpha] - center;
+        const double s1 = at[i] * Y[i] + bt[i] * Y[i + n] - 0.5 * c[i] * Y[i + 2 * n] - 0.5 * Y[i + 3 * n];
+        grad[i * dim + alpha] = scale * (y * S0[i] - s1);
+    }
+}
+
+}  // namespace nfl
+
+extern "C" {
+
+nfl_status nfl_form_grad_nodes(nfl_plan *plan, const double *v, const double *a, const double *b, double *grad) {
+    using namespace nfl;
+    if (!plan || !v || !a || !b || !grad) return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (P.kernel != NFL_KERNEL_GAUSSIAN) return NFL_ERR_INVALID_ARG;
+    if (!P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    const int vb = vec_blocks(P);
+    Dev at, bt, Wa, Wb, c, Wc, S0, X, Y;
+    for (Dev *t : {&at, &bt, &Wa, &Wb, &c, &Wc, &S0})
+        if (cudaMalloc(&t->buf, n * 8) != cudaSuccess) return NFL_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc(&X.buf, 4 * n * 8) != cudaSuccess || cudaMalloc(&Y.buf, 4 * n * 8) != cudaSuccess)
+        return NFL_ERR_OUT_OF_MEMORY;
+    scale_by_degree<<<vb, 256, 0, s>>>(a, b, P.degree, n, at.buf, bt.buf);
+    nfl_status st = run_column(P, OP_W, at.buf, Wa.buf);
+    if (st == NFL_OK) st = run_column(P, OP_W, bt.buf, Wb.buf);
+    if (st != NFL_OK) return st;
+    form_c<<<vb, 256, 0, s>>>(at.buf, bt.buf, Wa.buf, Wb.buf, P.degree, n, c.buf);
+    st = run_column(P, OP_W, c.buf, Wc.buf);
+    if (st != NFL_OK) return st;
+    form_s0<<<vb, 256, 0, s>>>(at.buf, bt.buf, Wa.buf, Wb.buf, c.buf, P.degree, Wc.buf, n, S0.buf);
+    // grad K(y) = -(2 / sigma^2) y K(y) for the Gaussian
+    const double scale = -2.0 / (P.sigma * P.sigma);
+    for (int alpha = 0; alpha < P.d; ++alpha) {
+        form_columns<<<vb, 256, 0, s>>>(v, P.d, alpha, P.center[alpha], at.buf, bt.buf, c.buf, n, X.buf);
+        for (int col = 0; col < 4 && st == NFL_OK; ++col) st = run_column(P, OP_W, X.buf + col * n, Y.buf + col * n);
+        if (st != NFL_OK) return st;
+        form_grad_axis<<<vb, 256, 0, s>>>(v, P.d, alpha, P.center[alpha], S0.buf, at.buf, bt.buf, c.buf, Y.buf, n,
+                                          scale, grad);
+    }
+    if (cudaGetLastError() != cudaSuccess) return NFL_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+}
+
+}  // extern "C"
+
 // ------------------------------------------------ Alg. 3: Nystrom-Gaussian-NFFT
 namespace nfl {
 

@@ -68,6 +68,7 @@ SIGNATURES = {
                                ctypes.POINTER(_L), _I]),
     "nfl_cg_solve_noalloc": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_nystrom_k_largest": (_I, [_P, _I, _I, _I, _P, ctypes.c_uint64, _P, _P]),
+    "nfl_form_grad_nodes": (_I, [_P, _P, _P, _P, _P]),
     "nfl_cg_solve_backward": (_I, [_P, _P, _D, _P, _P, _P, _D, _I, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D),
                                    ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_plan_set_profiling": (_I, [_P, _I]),
@@ -301,6 +302,19 @@ class Plan:
         if check:
             _check(st, "nfl_cg_solve_noalloc" if noalloc else "nfl_cg_solve")
         return u, it.value, rel.value, st
+
+    def form_grad_nodes(self, v, a, b):
+        """d(a^T A_E b)/dv for the nodes v (n, d) of this Gaussian plan (nfl_form_grad_nodes)."""
+        self._sync_stream()
+        v = _cuda_f64(v, "v").contiguous()
+        a = _cuda_f64(a, "a").contiguous()
+        b = _cuda_f64(b, "b").contiguous()
+        if v.shape != (self.n, self.d) or a.shape != (self.n,) or b.shape != (self.n,):
+            raise ValueError("v must be (n, d), a and b (n,)")
+        g = torch.empty_like(v)
+        _check(_lib().nfl_form_grad_nodes(self._h, v.data_ptr(), a.data_ptr(), b.data_ptr(), g.data_ptr()),
+               "nfl_form_grad_nodes")
+        return g
 
     def cg_solve_backward(self, u, g, beta=1.0, shift=None, dplan=None, tol=1e-10, maxit=1000, want_shift=True):
         """nfl_cg_solve_backward: (grad_f, grad_shift or None, grad_beta, grad_sigma or None, iters, relres)."""

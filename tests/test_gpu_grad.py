@@ -125,3 +125,56 @@ def test_backward_rejects_mismatched_plans(problem):
     from paper_1808_04580_gb300 import NflError
     with pytest.raises(NflError):
         p.cg_solve_backward(u, gpu(w), beta=0.7, shift=gpu(s), dplan=other)
+
+
+# ---------------------------------------------------------------- node coordinates
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("fp32c", 2e-5), ("fp32", 2e-5)])
+@pytest.mark.parametrize("d", [3, 2])
+def test_form_grad_nodes_against_dense_oracle(problem, prec, tol, d):
+    """d(a^T A b)/dv of the library, element by element against the oracle's dense chain rule."""
+    v, _, _, _ = problem
+    v = np.ascontiguousarray(v[:, :d])
+    rng = np.random.default_rng(31)
+    a, b = rng.standard_normal(v.shape[0]), rng.standard_normal(v.shape[0])
+    p = Plan(gpu(v), 0.5, 64, 8, 8, -1.0, prec)
+    g = p.form_grad_nodes(gpu(v), gpu(a), gpu(b)).cpu().numpy()
+    ref = direct.form_grad_nodes(v, 0.5, a, b)
+    assert g.shape == ref.shape
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < tol
+
+
+def test_node_gradient_of_solve_against_dense_oracle(problem):
+    """torch autograd dl/dv through cg_solve: element by element against
+    beta * dense form gradient at the dense lambda, u; and the directional
+    derivative against central differences of the dense loss."""
+    v, f, s, w = problem
+    sigma, beta = 0.5, 0.7
+    n = v.shape[0]
+
+    def dense_solution(vv):
+        Ls = np.eye(n) - direct.normalized_adjacency(vv, sigma)
+        return np.linalg.solve(beta * Ls + np.diag(s), f), beta * Ls + np.diag(s)
+
+    vt = gpu(v).requires_grad_(True)
+    p = Plan(vt.detach(), sigma, ARGS["N"], ARGS["m"], ARGS["p"], -1.0, "fp64")
+    u = cg_solve(p, gpu(f), gpu(s), beta, v=vt, tol=1e-13, maxit=2000)
+    (u * gpu(w)).sum().backward()
+    g = vt.grad.cpu().numpy()
+
+    ud, Md = dense_solution(v)
+    lam = np.linalg.solve(Md, w)
+    ref = beta * direct.form_grad_nodes(v, sigma, lam, ud)
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-8
+
+    dv = np.random.default_rng(5).standard_normal(v.shape)
+    h = 1e-5
+    fd = (w @ dense_solution(v + h * dv)[0] - w @ dense_solution(v - h * dv)[0]) / (2 * h)
+    assert float((g * dv).sum()) == pytest.approx(fd, rel=1e-6)
+
+
+def test_form_grad_nodes_rejects_other_kernels(problem):
+    v, f, _, _ = problem
+    from paper_1808_04580_gb300 import NflError
+    p = Plan(gpu(v), 0.5, 64, 8, 8, -1.0, "fp64", kernel="inverse_multiquadric")
+    with pytest.raises(NflError):
+        p.form_grad_nodes(gpu(v), gpu(f), gpu(f))

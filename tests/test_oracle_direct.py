@@ -90,3 +90,45 @@ def test_c_rows_match_dense():
     ref = direct.weight_matrix(v, 0.8) @ x
     np.testing.assert_allclose(out, ref[rows], rtol=1e-13, atol=1e-13)
     np.testing.assert_allclose(direct.rows_W(v, 0.8, x[:, 1], rows), ref[rows, 1], rtol=1e-13)
+
+
+# ---------------------------------------------------------------- node gradient
+def _form(v, sigma, a, b):
+    return float(a @ direct.normalized_adjacency(v, sigma) @ b)
+
+
+def test_form_grad_nodes_central_differences():
+    rng = np.random.default_rng(21)
+    n, sigma = 25, 0.7
+    v = rng.standard_normal((n, 3))
+    a, b = rng.standard_normal(n), rng.standard_normal(n)
+    g = direct.form_grad_nodes(v, sigma, a, b)
+    h = 1e-6
+    fd = np.zeros_like(v)
+    for k in range(n):
+        for al in range(3):
+            vp, vm = v.copy(), v.copy()
+            vp[k, al] += h
+            vm[k, al] -= h
+            fd[k, al] = (_form(vp, sigma, a, b) - _form(vm, sigma, a, b)) / (2 * h)
+    assert np.abs(g - fd).max() < 1e-7 * np.abs(fd).max()
+
+
+def test_form_grad_nodes_translation_invariant():
+    rng = np.random.default_rng(22)
+    v = rng.standard_normal((40, 2)) + 100.0
+    a, b = rng.standard_normal(40), rng.standard_normal(40)
+    g = direct.form_grad_nodes(v, 0.9, a, b)
+    assert np.abs(g.sum(axis=0)).max() < 1e-12 * np.abs(g).sum()
+    g0 = direct.form_grad_nodes(v - 100.0, 0.9, a, b)
+    np.testing.assert_allclose(g, g0, rtol=1e-9, atol=1e-12 * np.abs(g).max())
+
+
+def test_form_grad_nodes_two_nodes_is_zero():
+    # n = 2: d_1 = d_2 = W_12, so A = [[0, 1], [1, 0]] whatever the nodes
+    v = np.array([[0.1, 0.2, 0.3], [0.5, -0.1, 0.0]])
+    a, b = np.array([1.3, -0.7]), np.array([0.2, 2.0])
+    g = direct.form_grad_nodes(v, 0.4, a, b)
+    # zero to rounding of its terms, each of size ~ (2 / sigma^2) |a| |b| ||v_1 - v_2||
+    scale = 2.0 / 0.4 ** 2 * np.abs(a).max() * np.abs(b).max() * np.linalg.norm(v[0] - v[1])
+    assert np.abs(g).max() < 1e-14 * scale

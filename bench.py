@@ -12,7 +12,9 @@ Workload (one "step" = one pass of the whole hot path over one batch):
 
 Reported: L_s matvecs/s (columns per second, all ranks), the same through
 host buffers (e2e), the plain FP64 single-vector form on the same data, the
-error of the product against the FP64 direct sum on sampled rows, the
+error of the product against the FP64 direct sum on sampled rows, a
+precision sweep (W x in FP64, FP32, FP32C and BF16W, each against the direct
+sum on the sampled rows and the GPU FP64 form on all rows), the
 roofline of the dominant kernel from CUDA events recorded around each stage
 inside the timed region, and the direct-sum oracle timed on the host cores.
 
@@ -56,6 +58,7 @@ def parse():
     ap.add_argument("--baseline-rows", type=int, default=1024)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the W x precision sweep (FP32, FP32C, BF16W)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -328,6 +331,7 @@ def main():
     if fp64 is not None:
         err["vs_gpu_fp64_all_rows"] = float(np.linalg.norm(wmix - w64) / np.linalg.norm(w64))
     cpu_baseline = None
+    rows, ref = None, None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         rows = np.random.default_rng(3).choice(n, args.baseline_rows, replace=False)
         ref, secs, cores = oracle_rows(v, X[:, 0].copy(), rows)
@@ -338,6 +342,36 @@ def main():
                         "sample": "direct FP64 sum of W x for %d of %d target rows over all %d sources "
                                   "(plain C, OpenMP), %.1f s; extrapolated as rows/s / n" % (
                                       args.baseline_rows, n, n, secs)}
+
+    # precision sweep: W x (one column) in every form on the same nodes, each against the
+    # direct FP64 sum on the sampled rows and the GPU FP64 form on all rows
+    sweep = None
+    if not args.no_sweep:
+        sweep = {args.precision: {"rel_err_vs_gpu_fp64": err.get("vs_gpu_fp64_all_rows"),
+                                  "rel_err_vs_direct_sample": err.get("vs_direct_sample")}}
+        if fp64 is not None and ref is not None:
+            sweep["fp64"] = {"rel_err_vs_direct_sample": float(np.linalg.norm(w64[rows] - ref) / np.linalg.norm(ref))}
+        for form in ("fp32", "fp32c", "bf16w"):
+            if form == args.precision:
+                continue
+            pf = Plan(vg, CFG["sigma"], CFG["N"], CFG["m"], CFG["p"], -1.0, form)
+            yf = pf.apply_W(x0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                pf.apply_W(x0, out=yf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wf = yf.cpu().numpy()
+            entry = {"ms_per_matvec_W": e0.elapsed_time(e1) / 3}
+            if fp64 is not None:
+                entry["rel_err_vs_gpu_fp64"] = float(np.linalg.norm(wf - w64) / np.linalg.norm(w64))
+            if ref is not None:
+                entry["rel_err_vs_direct_sample"] = float(np.linalg.norm(wf[rows] - ref) / np.linalg.norm(ref))
+            sweep[form] = entry
+            pf.close()
 
     if rank == 0:
         out = {
@@ -356,6 +390,7 @@ def main():
             "fp64_plain": fp64,
             "speedup_vs_fp64_plain": (value / world) / fp64["value"] * world if fp64 else None,
             "rel_err_W": err,
+            "precision_sweep": sweep,
             "roofline": roofline,
             "cpu_baseline": cpu_baseline,
             "e2e": e2e,

@@ -82,7 +82,13 @@ enum {
  *           on the tensor cores with FP32-accurate (three-term TF32) products.
  *           Results vary in the last FP32 bits from run to run (the order
  *           in which the partial sums meet is not fixed).                   */
-enum { NFL_PREC_FP64 = 0, NFL_PREC_FP32 = 1, NFL_PREC_FP32C = 2 };
+/*   BF16W : FP32, with every window tap rounded to BF16 (round to nearest,
+ *           ties to even) where it is produced, i.e. the accuracy of a design
+ *           that stores the per-node 1-D window weights phi / phi(0) in BF16
+ *           and accumulates in FP32.  The kernels evaluate the taps instead
+ *           of storing them, so BF16 storage would save nothing here; the
+ *           form exists to report that accuracy (about 1e-3 relative).      */
+enum { NFL_PREC_FP64 = 0, NFL_PREC_FP32 = 1, NFL_PREC_FP32C = 2, NFL_PREC_BF16W = 3 };
 
 typedef struct {
     int64_t n;            /* number of nodes                                   */
@@ -124,7 +130,7 @@ typedef struct {
  *   m         window cut-off, 1 <= m <= 12.
  *   p         regularization smoothness; p <= 0 selects the default p = m.
  *   eps_B     regularization width in [0, 1/2); eps_B < 0 selects p / N.
- *   precision NFL_PREC_FP64, NFL_PREC_FP32 or NFL_PREC_FP32C.
+ *   precision NFL_PREC_FP64, NFL_PREC_FP32, NFL_PREC_FP32C or NFL_PREC_BF16W.
  *   stream    a cudaStream_t (0 = legacy default stream).
  *   out       receives the plan.
  *

@@ -60,11 +60,11 @@ def scale_nodes(v, eps_B):
     return (v - c) * rho, rho, c
 
 
-def fastsum(vt, x, bhat, N, m, alpha=2):
+def fastsum(vt, x, bhat, N, m, alpha=2, taps="fp64"):
     """Alg. 1: complex f_RF at the (already scaled) nodes vt."""
-    xhat = _nfft.adjoint_nfft(vt, x, N, m, alpha)   # step 1
-    fhat = bhat * xhat                              # step 2
-    return _nfft.nfft(vt, fhat, N, m, alpha)        # step 3
+    xhat = _nfft.adjoint_nfft(vt, x, N, m, alpha, taps)   # step 1
+    fhat = bhat * xhat                                    # step 2
+    return _nfft.nfft(vt, fhat, N, m, alpha, taps)        # step 3
 
 
 def trig_polynomial_sum(vt, x, bhat, N):
@@ -76,12 +76,13 @@ def trig_polynomial_sum(vt, x, bhat, N):
 class NormalizedFastsum:
     """Alg. 2: setup (steps 1-4) and products (step 5) for the kernels of Sec. 2."""
 
-    def __init__(self, v, sigma, N, m, p=None, eps_B=None, alpha=2, kernel="gaussian"):
+    def __init__(self, v, sigma, N, m, p=None, eps_B=None, alpha=2, kernel="gaussian", taps="fp64"):
         if N % 2:
             raise ValueError("N must be even")
         if kernel not in _kernel.KERNELS:
             raise ValueError("unknown kernel %r" % (kernel,))
         self.kernel = kernel
+        self.taps = taps                 # "bf16": window taps rounded to BF16 (not a paper construct)
         self.N, self.m, self.alpha = int(N), int(m), int(alpha)
         self.p = int(m if p is None else p)
         self.eps_B = float(self.p / self.N if eps_B is None else eps_B)
@@ -102,7 +103,7 @@ class NormalizedFastsum:
 
     def apply_Wtilde(self, x):
         """W~_E x, the real part of Alg. 1's output in the original coordinates."""
-        return self.out_scale * fastsum(self.vt, x, self.bhat, self.N, self.m, self.alpha).real
+        return self.out_scale * fastsum(self.vt, x, self.bhat, self.N, self.m, self.alpha, self.taps).real
 
     def apply_W(self, x):
         """W_E x = W~_E x - K(0) x (Sec. 3, the diagonal identity)."""

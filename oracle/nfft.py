@@ -19,6 +19,11 @@ Adjoint NFFT:  h_t = sum_i x_i prod_a phi(n v_ia - t_a)  (periodic in t),
 NFFT:          g_t = sum_{l in I_N} fhat_l / prod_a (n phi_hat(l_a)) exp(2 pi i l.t / n),
                f(v_j) = sum_t g_t prod_a phi(n v_ja - t_a).
 
+BF16 taps (``taps="bf16"``, not a paper construct: the accuracy of storing
+the window weights in BF16): every normalized tap phi(delta) / phi(0) is
+rounded to FP32 and then to the nearest BF16 value (ties to even) before it
+is used, and multiplied back by phi(0).
+
 Pins (tests/test_oracle_nfft.py): phi_hat equals the numerically integrated
 Fourier transform of the truncated window to the truncation level; I_0's
 power series equals the textbook routine; both transforms equal the direct
@@ -69,17 +74,30 @@ def kb_window_hat(k, n, m, b):
     return bessel_i0(m * np.sqrt(arg)) / n
 
 
-def _taps(v, n, m, b):
+def round_bf16(w):
+    """Nearest BF16 value (8-bit significand, ties to even) of FP32(w), as FP64."""
+    f = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _taps(v, n, m, b, taps="fp64"):
     """Per-axis tap indices (unwrapped) and window values: two (npts, d, 2m) arrays."""
     u = n * v
     base = np.floor(u).astype(np.int64)
     offs = np.arange(-m + 1, m + 1, dtype=np.int64)
     t = base[:, :, None] + offs[None, None, :]
     w = kb_window(u[:, :, None] - t, m, b)
+    if taps == "bf16":
+        phi0 = float(kb_window(0.0, m, b))
+        w = phi0 * round_bf16(w / phi0)
+    elif taps != "fp64":
+        raise ValueError("taps must be 'fp64' or 'bf16'")
     return t, w
 
 
-def adjoint_nfft(v, x, N, m, alpha=2):
+def adjoint_nfft(v, x, N, m, alpha=2, taps="fp64"):
     """xhat_l ~ sum_i x_i exp(-2 pi i l.v_i), l in I_N (index l + N/2 per axis).
 
     v: (npts, d) nodes in [-1/2, 1/2)^d;  x: (npts,) real or complex.
@@ -88,7 +106,7 @@ def adjoint_nfft(v, x, N, m, alpha=2):
     npts, d = v.shape
     n = alpha * N
     b = kb_shape(alpha)
-    t, w = _taps(v, n, m, b)
+    t, w = _taps(v, n, m, b, taps)
     h = np.zeros((n,) * d, dtype=np.complex128)
     x = np.asarray(x, dtype=np.complex128)
     for tap in itertools.product(range(2 * m), repeat=d):
@@ -108,7 +126,7 @@ def adjoint_nfft(v, x, N, m, alpha=2):
     return sub
 
 
-def nfft(v, fhat, N, m, alpha=2):
+def nfft(v, fhat, N, m, alpha=2, taps="fp64"):
     """f(v_j) ~ sum_{l in I_N} fhat_l exp(2 pi i l.v_j); complex output."""
     v = np.atleast_2d(np.asarray(v, dtype=np.float64))
     npts, d = v.shape
@@ -124,7 +142,7 @@ def nfft(v, fhat, N, m, alpha=2):
     full = np.zeros((n,) * d, dtype=np.complex128)
     full[np.ix_(*([l % n] * d))] = G
     g = np.fft.ifftn(full) * float(n) ** d      # sum_k G_k exp(+2 pi i k.t/n)
-    t, w = _taps(v, n, m, b)
+    t, w = _taps(v, n, m, b, taps)
     f = np.zeros(npts, dtype=np.complex128)
     for tap in itertools.product(range(2 * m), repeat=d):
         idx = tuple(t[:, a, tap[a]] % n for a in range(d))

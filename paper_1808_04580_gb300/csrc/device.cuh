@@ -1,6 +1,7 @@
 // Device helpers shared by the spread and gather kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +45,10 @@ __device__ __forceinline__ float kb_weight<float>(float delta, float m, float b,
 }
 
 // Two FP32 lanes in one 64-bit register: lane 0 in the low half.
+// w rounded to the nearest BF16 value (ties to even), returned in FP32: the
+// window taps of the BF16W form.
+__device__ __forceinline__ float round_bf16(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
+
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));

@@ -9,6 +9,8 @@
 // the nodes of one chunk of that tile.  The tap sum is nested per axis
 // (sum_a w_a sum_b w_b sum_c w_c g), which keeps FP32 rounding to a few
 // ulps of each partial sum.
+#include <type_traits>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -33,6 +35,7 @@ struct GatherArgs {
     int op;
     double out_scale, k0;   // W x = out_scale f - K(0) x (caller's coordinates)
     double b, inv_sinh_bm;
+    int bf16;                    // BF16W: FP32 taps rounded to BF16
 };
 
 // MT > 0: the cut-off m fixed at compile time; MT = 0: m from the arguments.
@@ -86,8 +89,11 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a) {
                 s[ax] = cell_axis(pt.cell, ax) - tc[ax] * a.tile_edge;
                 const T fr = T(pt.f[ax]);
 #pragma unroll
-                for (int j = 0; j < taps; ++j)
+                for (int j = 0; j < taps; ++j) {
                     wt[ax][j] = kb_weight<T>(fr + T(m - 1) - T(j), tm, tb, tinv);
+                    if constexpr (std::is_same<T, float>::value)
+                        if (a.bf16) wt[ax][j] = round_bf16(wt[ax][j]);
+                }
             }
             T f = T(0);
             if (D == 1) {
@@ -193,6 +199,7 @@ cudaError_t launch_gather(Plan &P, int op, const double *x, double *y) {
     a.k0 = P.k0;
     a.b = P.kb_b;
     a.inv_sinh_bm = P.kb_inv_sinh_bm;
+    a.bf16 = P.bf16_taps ? 1 : 0;
     switch (P.prec * 4 + P.d) {
         case NFL_PREC_FP64 * 4 + 1: return launch_gather_t<double, double, 1>(P, a);
         case NFL_PREC_FP64 * 4 + 2: return launch_gather_t<double, double, 2>(P, a);

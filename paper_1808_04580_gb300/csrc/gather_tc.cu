@@ -83,7 +83,8 @@ struct TCGeom {
     static constexpr int B_BYTES = NH * N * 64;           // all halves
 };
 
-template <int M, int TE>
+// BF16: the window taps are rounded to BF16 (the BF16W form)
+template <int M, int TE, bool BF16>
 __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     using G = TCGeom<M, TE>;
     constexpr int PA = G::PA, N = G::N, NH = G::NH, NCOL = G::NCOL, TAPS = 2 * M;
@@ -213,6 +214,13 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                         tap2[2 * q] = lane_of(h2, 0);
                         tap2[2 * q + 1] = lane_of(h2, 1);
                     }
+                    if constexpr (BF16) {
+#pragma unroll
+                        for (int j = 0; j < TAPS; ++j) {
+                            tap1[j] = round_bf16(tap1[j]);
+                            tap2[j] = round_bf16(tap2[j]);
+                        }
+                    }
                     place_taps<TAPS, PA, TE>(tap1, s1, w1p);
                     place_taps<TAPS, PA, TE>(tap2, s2, w2p);
                 }
@@ -233,6 +241,10 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                         }
                         tap0[2 * q] = live ? lane_of(h0, 0) : 0.f;
                         tap0[2 * q + 1] = live ? lane_of(h0, 1) : 0.f;
+                    }
+                    if constexpr (BF16) {
+#pragma unroll
+                        for (int j = 0; j < TAPS; ++j) tap0[j] = round_bf16(tap0[j]);
                     }
                     float v0[16];
                     place_taps<TAPS, 16, TE>(tap0, s0, v0);
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
 template <int M, int TE>
 static cudaError_t launch_tc(Plan &P, const GatherTCArgs &a) {
     using G = TCGeom<M, TE>;
-    auto kern = gather3_tc<M, TE>;
+    auto kern = P.bf16_taps ? gather3_tc<M, TE, true> : gather3_tc<M, TE, false>;
     // 52 KB of dynamic shared memory (and <= 128 registers from the launch bounds)
     // keep at most four CTAs, 4 x TMEM_COLS = 512 columns, per SM
     const int smem = 52 * 1024;

@@ -41,6 +41,7 @@ struct Plan {
     int64_t n = 0;
     int d = 0, N = 0, m = 0, p = 0, prec = 0;
     int kernel = NFL_KERNEL_GAUSSIAN;
+    bool bf16_taps = false;     // BF16W: window taps rounded to BF16 (prec is then FP32)
     double out_scale = 1.0;     // scaled fast sum -> caller's coordinates (multiquadrics: 1/rho, rho)
     double k0 = 1.0;            // K(0) in the caller's coordinates
     double sigma = 0, sigma_t = 0, rho = 1, eps_B = 0;

@@ -586,6 +586,9 @@ static void window_poly(Plan &P) {
 
 static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel, double sigma, int N, int m, int p,
                                    double eps_B, int prec, cudaStream_t stream, Plan *P) {
+    // BF16W is the FP32 form with BF16-rounded window taps
+    P->bf16_taps = prec == NFL_PREC_BF16W;
+    if (P->bf16_taps) prec = NFL_PREC_FP32;
     P->n = n; P->d = d; P->N = N; P->m = m; P->p = p; P->prec = prec;
     P->sigma = sigma; P->eps_B = eps_B; P->stream = stream;
     P->ngrid = 2 * N;
@@ -824,7 +827,8 @@ nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double
     if (p > 16) return NFL_ERR_INVALID_ARG;
     if (eps_B < 0.0) eps_B = double(p) / N;
     if (!(eps_B < 0.5)) return NFL_ERR_INVALID_ARG;
-    if (precision != NFL_PREC_FP64 && precision != NFL_PREC_FP32 && precision != NFL_PREC_FP32C)
+    if (precision != NFL_PREC_FP64 && precision != NFL_PREC_FP32 && precision != NFL_PREC_FP32C &&
+        precision != NFL_PREC_BF16W)
         return NFL_ERR_INVALID_ARG;
     Plan *P = new (std::nothrow) Plan();
     if (!P) return NFL_ERR_OUT_OF_MEMORY;
@@ -860,7 +864,7 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->N = P->N;
     info->m = P->m;
     info->p = P->p;
-    info->precision = P->prec;
+    info->precision = P->bf16_taps ? NFL_PREC_BF16W : P->prec;
     info->sigma = P->sigma;
     info->eps_B = P->eps_B;
     info->rho = P->rho;

@@ -32,6 +32,7 @@ struct SpreadArgs {
     const double *abs_sum;       // fixed point: device sum_i |x~_i|
     int ones;
     double b, inv_sinh_bm;
+    int bf16;                    // BF16W: FP32 taps rounded to BF16
 };
 
 // 2^k with k the largest integer such that sum|x~| * 2^k < 2^62.
@@ -85,8 +86,11 @@ __global__ void __launch_bounds__(256) spread_kernel(SpreadArgs a) {
                 s[ax] = cell_axis(pt.cell, ax) - tc[ax] * a.tile_edge;
                 const T fr = T(pt.f[ax]);
 #pragma unroll
-                for (int j = 0; j < taps; ++j)
+                for (int j = 0; j < taps; ++j) {
                     wt[ax][j] = kb_weight<T>(fr + T(m - 1) - T(j), tm, tb, tinv);
+                    if constexpr (std::is_same<T, float>::value)
+                        if (a.bf16) wt[ax][j] = round_bf16(wt[ax][j]);
+                }
             }
             const T xt = T(xv);
             if (D == 1) {
@@ -249,6 +253,7 @@ cudaError_t launch_spread(Plan &P, const double *x, int64_t, bool ones, bool sca
     a.ones = ones ? 1 : 0;
     a.b = P.kb_b;
     a.inv_sinh_bm = P.kb_inv_sinh_bm;
+    a.bf16 = P.bf16_taps ? 1 : 0;
 
     switch (P.prec * 4 + P.d) {
         case NFL_PREC_FP64 * 4 + 1: return launch_spread_t<double, 1, false>(P, a);

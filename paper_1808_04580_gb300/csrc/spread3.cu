@@ -47,6 +47,7 @@ struct Spread3Args {
     void *grid;
     const double *abs_sum;
     double b, inv_den;
+    int bf16;                       // BF16W: FP32 taps rounded to BF16
     float poly[2 * kMaxM][kPolyCoef];
 };
 
@@ -254,8 +255,13 @@ __global__ void __launch_bounds__(CellGeom<M, TE>::NT, (cells_min_blocks<T, M, T
                         unsigned long long h = pc[q * kPolyCoef + kPolyCoef - 1];
 #pragma unroll
                         for (int k = kPolyCoef - 2; k >= 0; --k) h = ffma2(h, t2, pc[q * kPolyCoef + k]);
-                        dst[2 * q] = lane_of(h, 0) * sc;
-                        dst[2 * q + 1] = lane_of(h, 1) * sc;
+                        float w0 = lane_of(h, 0), w1 = lane_of(h, 1);
+                        if (a.bf16) {
+                            w0 = round_bf16(w0);
+                            w1 = round_bf16(w1);
+                        }
+                        dst[2 * q] = w0 * sc;
+                        dst[2 * q + 1] = w1 * sc;
                     }
                 }
             } else {
@@ -419,6 +425,7 @@ cudaError_t launch_spread3_columns(Plan &P, const double *, bool, bool) {
     a.abs_sum = P.scratch;
     a.b = P.kb_b;
     a.inv_den = P.kb_inv_sinh_bm;
+    a.bf16 = P.bf16_taps ? 1 : 0;
     for (int j = 0; j < 2 * kMaxM; ++j)
         for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
     if (P.prec == NFL_PREC_FP64) return dispatch_cols<double, false>(P, a);

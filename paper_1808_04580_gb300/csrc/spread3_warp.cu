@@ -47,6 +47,7 @@ struct SpreadWarpArgs {
     void *grid;
     const double *abs_sum;
     unsigned *counter;              // next work item, shared by all CTAs
+    int bf16;                       // BF16W: taps rounded to BF16
     float poly[2 * kMaxM][kPolyCoef];
 };
 
@@ -224,9 +225,15 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     }
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
-                        t0[2 * q + u] = lane_of(h0, u);
-                        t1[2 * q + u] = lane_of(h1, u) * xv;
-                        t2[2 * q + u] = lane_of(h2, u);
+                        float w0 = lane_of(h0, u), w1 = lane_of(h1, u), w2 = lane_of(h2, u);
+                        if (a.bf16) {
+                            w0 = round_bf16(w0);
+                            w1 = round_bf16(w1);
+                            w2 = round_bf16(w2);
+                        }
+                        t0[2 * q + u] = w0;
+                        t1[2 * q + u] = w1 * xv;
+                        t2[2 * q + u] = w2;
                     }
                 }
                 // 16-byte stores of this lane's rows
@@ -368,6 +375,7 @@ cudaError_t launch_spread3_warp(Plan &P) {
     a.grid = P.grid;
     a.abs_sum = P.scratch;
     a.counter = P.work_counter;
+    a.bf16 = P.bf16_taps ? 1 : 0;
     for (int j = 0; j < 2 * kMaxM; ++j)
         for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = P.kb_poly[j][k];
     const bool fixed = P.prec == NFL_PREC_FP32C;

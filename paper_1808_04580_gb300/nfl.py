@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libnfl.so")
 
 NFL_OK = 0
 NOALLOC_MAX_N = 262144   # NFL_NOALLOC_MAX_N in include/nfl.h
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32c": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32c": 2, "bf16w": 3}
 
 _STATUS = {
     0: "NFL_OK", 1: "NFL_ERR_INVALID_ARG", 2: "NFL_ERR_NONPOSITIVE_DEGREE", 3: "NFL_ERR_BREAKDOWN",

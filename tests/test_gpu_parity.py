@@ -282,3 +282,22 @@ def test_repeat_products_agree(prec, tol):
     ys = [plan.apply_W(xt) for _ in range(3)]
     for y in ys[1:]:
         assert float(torch.linalg.norm(y - ys[0]) / torch.linalg.norm(ys[0])) < tol
+
+
+@pytest.mark.parametrize("m,N,d", [(6, 32, 3), (4, 32, 3), (8, 32, 3), (4, 32, 2), (2, 16, 3)])
+def test_bf16w_matches_bf16_tap_oracle(m, N, d):
+    """BF16W (taps rounded to BF16) against the oracle's Alg. 2 with BF16 taps: the
+    same approximation, up to FP32 arithmetic and rare rounding-boundary flips;
+    the rounding itself moves the product by ~1e-3 (checked to be in effect)."""
+    v = _cloud("clusters", 2500, d, seed=40 + m)
+    x = np.random.default_rng(41).standard_normal(2500)
+    p = Plan(gpu(v), 0.3, N, m, m, -1.0, "bf16w")
+    assert p.info()["precision"] == 3
+    y = p.apply_W(gpu(x)).cpu().numpy()
+    ref = fastsum.NormalizedFastsum(v, 0.3, N, m, m, taps="bf16").apply_W(x)
+    ref64 = fastsum.NormalizedFastsum(v, 0.3, N, m, m).apply_W(x)
+    assert rel(y, ref) < 2e-5
+    assert rel(y, ref64) > 1e-4
+    ya = p.apply_A(gpu(x)).cpu().numpy()
+    refa = fastsum.NormalizedFastsum(v, 0.3, N, m, m, taps="bf16").apply_A(x)
+    assert rel(ya, refa) < 2e-5

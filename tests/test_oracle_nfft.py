@@ -58,3 +58,31 @@ def test_transforms_match_direct_sums(d, N, m, tol):
     f = nfft.nfft(v, fh, N, m)
     g = nfft.ndft(v, fh, N)
     assert np.abs(f - g).max() / np.abs(g).max() < tol
+
+
+# ---------------------------------------------------------------- BF16 taps
+def test_round_bf16_matches_torch_cast():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    w = np.concatenate([rng.uniform(0, 1, 20000), rng.uniform(0, 1e-5, 2000), 10.0 ** rng.uniform(-30, 3, 2000)])
+    ref = torch.from_numpy(w.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(nfft.round_bf16(w), ref)
+
+
+def test_round_bf16_ties_to_even():
+    assert nfft.round_bf16(1.0 + 2.0 ** -8) == 1.0                       # tie, even neighbour 1
+    assert nfft.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6       # tie, even neighbour above
+    assert nfft.round_bf16(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7           # representable
+    assert nfft.round_bf16(0.5 + 3 * 2.0 ** -10) == 0.5 + 2.0 ** -8           # above the tie: up
+
+
+def test_bf16_taps_perturb_adjoint_within_rounding():
+    """Each tap moves by at most 2^-9 relative, a product of d = 3 taps by < 3.01 * 2^-9."""
+    rng = np.random.default_rng(9)
+    v = rng.uniform(-0.25, 0.25, (200, 3))
+    x = rng.uniform(0.5, 1.5, 200)                  # positive: |sum| = sum |terms|
+    a = nfft.adjoint_nfft(v, x, 16, 4)
+    b = nfft.adjoint_nfft(v, x, 16, 4, taps="bf16")
+    # compare the spread grids through l = 0 (the plain sum of all window products)
+    i0 = (8, 8, 8)
+    assert 0.0 < abs(b[i0] - a[i0]) <= 3.01 * 2.0 ** -9 * abs(a[i0])

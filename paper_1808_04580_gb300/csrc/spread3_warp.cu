@@ -300,29 +300,30 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         if (cur >= 0) flush(cur);
         __syncthreads();
 
-        // sum the tile copies -> global grid (c fastest, matching the grid's x2 axis), clear
-        // them; four consecutive positions per thread and 16-byte shared accesses
-        for (int e4 = threadIdx.x; e4 < G::TILE / 4; e4 += NG * 32) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        // sum the tile copies -> global grid, clear them.  Consecutive threads take
+        // consecutive positions (c fastest, the grid's x2 axis), so the atomics of a
+        // warp fall on a few contiguous rows of the grid rather than one per sector.
+        {
+            constexpr int STEP = NG * 32;
+            int e = threadIdx.x;
+            int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
+            const int b0 = tc[0] * TE - (M - 1), b1 = tc[1] * TE - (M - 1), b2 = tc[2] * TE - (M - 1);
+            for (; e < PA3; e += STEP) {
+                float v = 0.f;
 #pragma unroll
-            for (int gg = 0; gg < NG; ++gg) {
-                float4 *t = reinterpret_cast<float4 *>(smem_raw + gg * G::WARP_BYTES) + e4;
-                const float4 tv = *t;
-                v.x += tv.x;
-                v.y += tv.y;
-                v.z += tv.z;
-                v.w += tv.w;
-                *t = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = 4 * e4 + u;
-                if (vv[u] == 0.f || e >= PA3) continue;
-                const int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
-                int p0 = tc[0] * TE - (M - 1) + q0;
-                int p1 = tc[1] * TE - (M - 1) + q1;
-                int p2 = tc[2] * TE - (M - 1) + q2;
+                for (int gg = 0; gg < NG; ++gg) {
+                    float *t = reinterpret_cast<float *>(smem_raw + gg * G::WARP_BYTES) + e;
+                    v += *t;
+                    *t = 0.f;
+                }
+                int p0 = b0 + q0, p1 = b1 + q1, p2 = b2 + q2;
+                // advance (q0, q1, q2) by STEP positions
+                q2 += STEP % PA;
+                q1 += (STEP / PA) % PA;
+                q0 += STEP / (PA * PA);
+                if (q2 >= PA) { q2 -= PA; ++q1; }
+                if (q1 >= PA) { q1 -= PA; ++q0; }
+                if (v == 0.f) continue;
                 if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
                 if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
                 if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
@@ -330,9 +331,9 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                 const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
                 if (FIXED)
                     atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
-                              (unsigned long long)to_fixed(vv[u] * fscale));
+                              (unsigned long long)to_fixed(v * fscale));
                 else
-                    atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, vv[u]);
+                    atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
             }
         }
         __syncthreads();

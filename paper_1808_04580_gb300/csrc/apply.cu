@@ -27,7 +27,7 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y) {
     const bool ones = (op == OP_DEGREE);
     const bool scale = (op == OP_A || op == OP_LS);
     NFL_STATUS_TRY(mark(P, 0));
-    NFL_STATUS_TRY(prepare_spread(P, x, ones, scale));
+    NFL_STATUS_TRY(prepare_spread(P, op, x, ones, scale));
     NFL_STATUS_TRY(mark(P, 1));
     NFL_STATUS_TRY(launch_spread(P, x, 0, ones, scale));
     NFL_STATUS_TRY(mark(P, 2));

@@ -35,7 +35,7 @@ namespace nfl {
 struct GatherTCArgs {
     const PointF *pts;
     const int32_t *perm;
-    const double *xd;     // x in sorted order
+    const double *zd;     // z in sorted order: y = z + s f (W: s = out_scale; A, L_s: s = +-out_scale dinv)
     double *y;
     const double *dinv;
     double *degree_out;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
             const bool live = tid < nb;
             float w1p[PA], w2p[PA];
             int kq = 0, iq = 0;
-            double xq = 0.0, dq = 0.0;
+            double zq = 0.0, dq = 0.0;
             {
                 float f0 = 0.f, f1 = 0.f, f2 = 0.f;
                 int s0 = 0, s1 = 0, s2 = 0;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                     const PointF p = a.pts[kq];
                     // epilogue operands, loaded now and used after the contraction
                     iq = a.perm[kq];
-                    if (a.op != OP_DEGREE) xq = a.xd[kq];
+                    if (a.op != OP_DEGREE) zq = a.zd[kq];
                     if (a.op == OP_A || a.op == OP_LS) dq = a.dinv[kq];
                     s0 = cell_axis(p.cell, 0) - tc[0] * TE;
                     s1 = cell_axis(p.cell, 1) - tc[1] * TE;
@@ -343,11 +343,9 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                         const double dd = a.out_scale * fd - a.k0;
                         a.degree_out[iq] = dd;
                         a.dinv_out[kq] = dd > 0.0 ? 1.0 / sqrt(dd) : 0.0;
-                    } else if (a.op == OP_W) {
-                        a.y[iq] = a.out_scale * fd - a.k0 * xq;
                     } else {
-                        const double ax = dq * (a.out_scale * fd - a.k0 * dq * xq);
-                        a.y[iq] = a.op == OP_A ? ax : xq - ax;
+                        const double s = a.op == OP_W ? a.out_scale : (a.op == OP_A ? a.out_scale : -a.out_scale) * dq;
+                        a.y[iq] = fma(s, fd, zq);
                     }
                 }
             }
@@ -391,7 +389,7 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
     GatherTCArgs a;
     a.pts = reinterpret_cast<const PointF *>(P.pts);
     a.perm = P.perm;
-    a.xd = P.xsorted;
+    a.zd = P.xsorted;
     a.y = y;
     a.dinv = P.dinv_sorted;
     a.degree_out = P.degree;

@@ -67,7 +67,7 @@ struct Plan {
     int32_t *perm = nullptr;    // sorted position -> input index
     double *dinv_sorted = nullptr;  // D_E^{-1/2} in sorted order
     void *xsort = nullptr;      // x~ of the current column in sorted order (spread type; 3-D cell kernels)
-    double *xsorted = nullptr;  // x of the current column in sorted order (interpolation epilogue)
+    double *xsorted = nullptr;  // z of the current column in sorted order: y = z + s f (interpolation epilogue)
     double *degree = nullptr;   // d_E in input order
     double min_deg = 0, max_deg = 0;
     bool degree_ok = false;
@@ -112,7 +112,7 @@ inline bool fft_is_double(int prec) { return prec == NFL_PREC_FP64; }
 inline bool points_are_double(int prec) { return prec == NFL_PREC_FP64; }
 
 // launchers (stream-ordered, no host sync)
-cudaError_t prepare_spread(Plan &P, const double *x, bool ones, bool scale_dinv);
+cudaError_t prepare_spread(Plan &P, int op, const double *x, bool ones, bool scale_dinv);
 cudaError_t launch_spread(Plan &P, const double *x, int64_t col_off, bool ones, bool scale_dinv);
 cudaError_t launch_fft(Plan &P);
 cudaError_t launch_gather(Plan &P, int op, const double *x, double *y);
@@ -124,7 +124,7 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y);
 // 3-D atomic-free spreading (spread3.cu): tile edge it needs for cut-off m (0: not available)
 int column_tile_edge(int m);
 cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool scale_dinv);
-cudaError_t stage_spread3_values(Plan &P, const double *x, bool ones, bool scale_dinv);
+cudaError_t stage_spread3_values(Plan &P, int op, const double *x, bool ones, bool scale_dinv);
 bool spread_warp_available(const Plan &P);
 cudaError_t launch_spread3_warp(Plan &P);
 

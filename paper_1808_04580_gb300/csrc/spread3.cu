@@ -52,18 +52,24 @@ struct Spread3Args {
 };
 
 // x~_k = x[perm[k]] * dinv[k] (or dinv[k] / 1 for the all-ones vector) in sorted
-// order, and x[perm[k]] itself (for the interpolation epilogue); with
-// abs_sum, also sum_k |x~_k| (the fixed-point scale of FP32C).
+// order; with abs_sum, also sum_k |x~_k| (the fixed-point scale of FP32C).
+// z_k, the x-only part of the interpolation epilogue y = z + s f (Alg. 2 step 5,
+// K(0) = k0, d = dinv):
+//   W: z = -k0 x,  A: z = -k0 d^2 x,  L_s: z = x + k0 d^2 x   (none for the degree).
 template <typename T>
 __global__ void __launch_bounds__(256) stage_values(const double *x, const int32_t *perm, const double *dinv,
-                                                    int64_t n, int ones, T *out, double *xs_out, double *abs_sum) {
+                                                    int64_t n, int ones, T *out, double *z_out, int op, double k0,
+                                                    double *abs_sum) {
     __shared__ double red[256];
     double acc = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const double xv = ones ? 1.0 : x[perm[k]];
-        const double v = dinv ? xv * dinv[k] : xv;
+        const double dk = dinv ? dinv[k] : 1.0;
+        const double v = dinv ? xv * dk : xv;
         out[k] = T(v);
-        xs_out[k] = xv;
+        if (op == OP_W) z_out[k] = -k0 * xv;
+        else if (op == OP_A) z_out[k] = -k0 * dk * v;
+        else if (op == OP_LS) z_out[k] = fma(k0 * dk, v, xv);
         acc += fabs(v);
     }
     if (!abs_sum) return;
@@ -392,7 +398,7 @@ static cudaError_t dispatch_cols(Plan &P, const Spread3Args &a) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t stage_spread3_values(Plan &P, const double *x, bool ones, bool scale_dinv) {
+cudaError_t stage_spread3_values(Plan &P, int op, const double *x, bool ones, bool scale_dinv) {
     const double *dinv = scale_dinv ? P.dinv_sorted : nullptr;
     double *abs_sum = nullptr;
     if (P.prec == NFL_PREC_FP32C) {
@@ -402,10 +408,12 @@ cudaError_t stage_spread3_values(Plan &P, const double *x, bool ones, bool scale
     const int blocks = P.num_sms * 4;
     if (P.prec == NFL_PREC_FP64)
         stage_values<double><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
-                                                           static_cast<double *>(P.xsort), P.xsorted, abs_sum);
+                                                           static_cast<double *>(P.xsort), P.xsorted, op, P.k0,
+                                                           abs_sum);
     else
         stage_values<float><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
-                                                          static_cast<float *>(P.xsort), P.xsorted, abs_sum);
+                                                          static_cast<float *>(P.xsort), P.xsorted, op, P.k0,
+                                                          abs_sum);
     return cudaGetLastError();
 }
 

@@ -220,16 +220,19 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
 template <typename T, typename TIN, int MODE>
 static cudaError_t run_pass(Plan &P, PassArgs a) {
     using C = typename Cplx<T>::type;
-    const int cap = std::is_same<T, float>::value ? 4096 : 2048;
+    // few lines per CTA and one radix-4 butterfly per thread and stage: small CTAs,
+    // many of them resident per SM to hide the global-memory latency of load and store
+    const int cap = 512;
     int BB = cap / a.n;
     BB = BB > 16 ? 16 : (BB < 1 ? 1 : BB);
-    if (!std::is_same<T, float>::value && BB > 8) BB = 8;
     a.BB = BB;
     a.lin_magic = (unsigned)((0x100000000ull + (unsigned)a.Lin - 1) / (unsigned)a.Lin);
     const int smem = 2 * BB * a.n * (int)sizeof(C);
+    int threads = BB * a.n / 4;
+    threads = threads < 64 ? 64 : (threads > 256 ? 256 : threads);
     NFL_CUDA_TRY(cudaFuncSetAttribute(fft_pass<T, TIN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid((a.nB + BB - 1) / BB, a.nA);
-    fft_pass<T, TIN, MODE><<<grid, 256, smem, P.stream>>>(a);
+    fft_pass<T, TIN, MODE><<<grid, threads, smem, P.stream>>>(a);
     return cudaGetLastError();
 }
 

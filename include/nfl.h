@@ -77,11 +77,11 @@ enum {
  *   FP64  : everything in FP64.
  *   FP32  : window weights, spreading grid, FFT and interpolation in FP32.
  *   FP32C : FP32 window weights and products; FP32 partial sums over at
- *           most 256 nodes are carried into 64-bit fixed point and
+ *           most 512 nodes are carried into 64-bit fixed point and
  *           accumulated exactly from there on; FFT in FP32; interpolation
  *           on the tensor cores with FP32-accurate (three-term TF32) products.
- *           Results vary in the last FP32 bits from run to run (the order
- *           in which the partial sums meet is not fixed).                   */
+ *           Results may vary in the last FP32 bits from run to run where a
+ *           kernel's partial sums meet in an order that is not fixed.      */
 /*   BF16W : FP32, with every window tap rounded to BF16 (round to nearest,
  *           ties to even) where it is produced, i.e. the accuracy of a design
  *           that stores the per-node 1-D window weights phi / phi(0) in BF16

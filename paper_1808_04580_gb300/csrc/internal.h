@@ -60,7 +60,12 @@ struct Plan {
     int ntile[3] = {1, 1, 1};
     int64_t tiles_total = 0, tiles_nonempty = 0;
     int64_t nitems = 0;
-    WorkItem *items = nullptr;
+    WorkItem *items = nullptr;          // chunks of one tile (interpolation, other spreads)
+    // warp-slice spread: runs of consecutive tiles along axis 2 of one row (pad = number
+    // of tiles) or, for tiles with more than one chunk, single chunks (pad = 1)
+    int64_t nsitems = 0;
+    WorkItem *sitems = nullptr;
+    int32_t *tile_start = nullptr;      // first sorted node of each tile; [tiles_total] = n
 
     // tile-sorted nodes
     void *pts = nullptr;        // PointF or PointD

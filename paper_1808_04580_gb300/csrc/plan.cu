@@ -196,6 +196,49 @@ __global__ void exclusive_scan(const int32_t *in, int64_t n, int64_t *out) {
     }
 }
 
+// First sorted node of every tile (and n at index ntiles), from the per-key offsets.
+__global__ void tile_starts(const int64_t *kstart, int64_t ntiles, int cells_per_tile, int32_t *out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (int32_t)kstart[t * cells_per_tile];
+}
+
+// Work items of the warp-slice spread from the per-tile chunks (in tile order): a tile
+// with several chunks keeps them as items of one tile; runs of single-chunk tiles that
+// follow each other along axis 2 in one row are joined while they hold at most kChunk
+// nodes together (pad = tiles in the run), so the spread slides one tile window along
+// the run and merges only the planes that leave it.
+static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2, int max_tiles) {
+    std::vector<WorkItem> s;
+    size_t i = 0;
+    while (i < h.size()) {
+        size_t j = i;
+        while (j < h.size() && h[j].tile == h[i].tile) ++j;
+        if (j - i > 1) {
+            for (size_t k = i; k < j; ++k) {
+                WorkItem w = h[k];
+                w.pad = 1;
+                s.push_back(w);
+            }
+            i = j;
+            continue;
+        }
+        WorkItem g = h[i];
+        g.pad = 1;
+        ++i;
+        while (i < h.size() && g.pad < max_tiles) {
+            const WorkItem &x = h[i];
+            if (x.tile != g.tile + g.pad || x.tile % nt2 == 0) break;        // not the next tile of the row
+            if (i + 1 < h.size() && h[i + 1].tile == x.tile) break;          // a tile of several chunks
+            if (g.count + x.count > kChunk) break;
+            g.count += x.count;
+            ++g.pad;
+            ++i;
+        }
+        s.push_back(g);
+    }
+    return s;
+}
+
 __global__ void chunks_per_tile(const int32_t *count, int64_t ntiles, int32_t *chunks, unsigned long long *nonempty) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
         const int c = count[t];
@@ -520,6 +563,8 @@ static void free_plan(Plan *P) {
     if (P->d2h) cudaStreamDestroy(P->d2h);
     cudaFree(P->host_stage);
     cudaFree(P->items);
+    cudaFree(P->sitems);
+    cudaFree(P->tile_start);
     cudaFree(P->pts);
     cudaFree(P->perm);
     cudaFree(P->dinv_sorted);
@@ -716,11 +761,13 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
     if (ce != cudaSuccess) { cleanup(); return NFL_ERR_CUDA; }
     P->tiles_nonempty = (int64_t)h_nonempty;
-    if (cudaMalloc(&P->items, std::max<int64_t>(P->nitems, 1) * sizeof(WorkItem)) != cudaSuccess) {
+    if (cudaMalloc(&P->items, std::max<int64_t>(P->nitems, 1) * sizeof(WorkItem)) != cudaSuccess ||
+        cudaMalloc(&P->tile_start, (nt + 1) * sizeof(int32_t)) != cudaSuccess) {
         cleanup();
         return NFL_ERR_OUT_OF_MEMORY;
     }
     fill_items<<<blocks, 256, 0, stream>>>(count, start, item_off, nt, P->items);
+    tile_starts<<<blocks, 256, 0, stream>>>(kstart, nt, cpt, P->tile_start);
     ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
     cleanup();
@@ -729,10 +776,17 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
         // largest chunks first: the kernels that take items from a shared counter
         // then end with small ones (longest-processing-time order)
         std::vector<WorkItem> h(P->nitems);
+        const auto by_size = [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; };
         if (P->nitems > 0) {
             ce = cudaMemcpy(h.data(), P->items, P->nitems * sizeof(WorkItem), cudaMemcpyDeviceToHost);
             if (ce != cudaSuccess) return NFL_ERR_CUDA;
-            std::stable_sort(h.begin(), h.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
+            std::vector<WorkItem> s = slide_items(h, P->ntile[d - 1], 8);
+            std::stable_sort(s.begin(), s.end(), by_size);
+            P->nsitems = (int64_t)s.size();
+            if (cudaMalloc(&P->sitems, s.size() * sizeof(WorkItem)) != cudaSuccess) return NFL_ERR_OUT_OF_MEMORY;
+            ce = cudaMemcpy(P->sitems, s.data(), s.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) return NFL_ERR_CUDA;
+            std::stable_sort(h.begin(), h.end(), by_size);
             ce = cudaMemcpy(P->items, h.data(), P->nitems * sizeof(WorkItem), cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) return NFL_ERR_CUDA;
         }

@@ -28,6 +28,13 @@
 // 64-bit fixed point (scale 2^k from sum |x~|, so nothing can overflow) and
 // adds it with an integer atomic.  So FP32C sums at most 2048 / NG nodes of a
 // tile position in FP32 (512 for NG = 4) before the exact integer part.
+//
+// A work item may also be a run of tiles that follow each other along axis 2
+// (at most 2048 nodes together).  The tile copies then slide along the run:
+// axis 2 of a copy is addressed circularly (slot = (q2 + woff) mod PA), and
+// between two tiles the CTA merges only the TE planes q2 < TE that the next
+// tile's window does not cover, clears them (they become its last TE planes)
+// and advances woff by TE.  The full merge follows the last tile.
 #include <type_traits>
 
 #include "device.cuh"
@@ -46,6 +53,7 @@ struct SpreadWarpArgs {
     int ngrid;
     void *grid;
     const double *abs_sum;
+    const int32_t *tile_start;      // first sorted node of each tile
     unsigned *counter;              // next work item, shared by all CTAs
     int bf16;                       // BF16W: taps rounded to BF16
     float poly[2 * kMaxM][kPolyCoef];
@@ -113,19 +121,23 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
     unsigned long long acc[RP][CPL];              // (ja, ja + 1) pairs for each column jc
     bool fresh = true;                            // the next node starts the accumulators
 
+    int woff = 0;                                 // circular offset of axis 2 in the tile copies
     // add the accumulators of cell o to this warp's tile copy
     auto flush = [&](int o) {
         __syncwarp();
         if (acc_lane) {
             const int s0 = o & 255, s1 = G::FULLB ? 0 : (o >> 8) & 255, s2 = o >> 16;
-            float *col = tile + (s0 * PA + s1 + jb) * PA + s2 + hseg;
+            float *row = tile + (s0 * PA + s1 + jb) * PA;
 #pragma unroll
-            for (int p = 0; p < RP; ++p)
+            for (int c = 0; c < CPL; ++c) {
+                int q = s2 + hseg + c * G::LPB + woff;   // < 2 PA
+                if (q >= PA) q -= PA;
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                    col[(2 * p) * PA * PA + c * G::LPB] += lane_of(acc[p][c], 0);
-                    col[(2 * p + 1) * PA * PA + c * G::LPB] += lane_of(acc[p][c], 1);
+                for (int p = 0; p < RP; ++p) {
+                    row[(2 * p) * PA * PA + q] += lane_of(acc[p][c], 0);
+                    row[(2 * p + 1) * PA * PA + q] += lane_of(acc[p][c], 1);
                 }
+            }
         }
         fresh = true;
     };
@@ -174,169 +186,217 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         if (it >= a.nitems) break;
         const WorkItem w = a.items[it];
         const int wend = w.start + w.count;
-        int tc[3];
-        tile_coords<3>(w.tile, a.ntile, tc);
-        int cur = -1;
-        // this warp's share of the chunk; this lane's node of the next slice, loaded one slice ahead
-        const int share = (w.count + NG - 1) / NG;
-        int base = w.start + g * share;
-        const int gend = min(wend, base + share);
-        PointF pn = {{0.f, 0.f, 0.f}, 0};
-        float xn = 0.f;
-        if (base + lane < gend) {
-            pn = a.pts[base + lane];
-            xn = a.xs[base + lane];
-        }
-        for (; base < gend; base += S) {
-            const int cnt = min(S, gend - base);
-            const bool valid = lane < cnt;
-            int o = 0;
-            {
-                // stage node `lane` of the slice
-                float f[3];
-                int s1 = 0;
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    const int sa = valid ? cell_axis(pn.cell, ax) - tc[ax] * TE : 0;
-                    if (ax == 1) s1 = sa;
-                    if (ax != 1 || !G::FULLB) o |= sa << (8 * ax);     // FULLB runs ignore axis 1
-                    f[ax] = valid ? pn.f[ax] : 0.f;
-                }
-                const float xv = xn;
-                const int kn = base + S + lane;
-                if (kn < gend) {
-                    pn = a.pts[kn];
-                    xn = a.xs[kn];
-                }
-                const unsigned long long T0 = pack2(fmaf(2.f, f[0], -1.f), fmaf(2.f, f[0], -1.f));
-                const unsigned long long T1 = pack2(fmaf(2.f, f[1], -1.f), fmaf(2.f, f[1], -1.f));
-                const unsigned long long T2 = pack2(fmaf(2.f, f[2], -1.f), fmaf(2.f, f[2], -1.f));
-                const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
-                float t0[TAPS], t1[TAPS], t2[TAPS];
-#pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    unsigned long long h0 = pc[q * kPolyCoef + kPolyCoef - 1], h1 = h0, h2 = h0;
-#pragma unroll
-                    for (int k = kPolyCoef - 2; k >= 0; --k) {
-                        const unsigned long long c = pc[q * kPolyCoef + k];
-                        h0 = ffma2(h0, T0, c);
-                        h1 = ffma2(h1, T1, c);
-                        h2 = ffma2(h2, T2, c);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        float w0 = lane_of(h0, u), w1 = lane_of(h1, u), w2 = lane_of(h2, u);
-                        if (a.bf16) {
-                            w0 = round_bf16(w0);
-                            w1 = round_bf16(w1);
-                            w2 = round_bf16(w2);
-                        }
-                        t0[2 * q + u] = w0;
-                        t1[2 * q + u] = w1 * xv;
-                        t2[2 * q + u] = w2;
-                    }
-                }
-                // 16-byte stores of this lane's rows
-                float4 *r0 = reinterpret_cast<float4 *>(w0s + lane * R1);
-                float4 *r1 = reinterpret_cast<float4 *>(w1s + lane * RB);
-                float4 *r2 = reinterpret_cast<float4 *>(w2s + lane * R1);
-#pragma unroll
-                for (int j = 0; j < (TAPS + 3) / 4; ++j) {
-                    float v0[4], v2[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const bool in = 4 * j + u < TAPS;
-                        v0[u] = in ? t0[(4 * j + u) % TAPS] : 0.f;
-                        // axis 2 de-interleaved: position h CPL + c holds tap c LPB + h
-                        const int r = (4 * j + u) % TAPS;
-                        v2[u] = in ? t2[(r % CPL) * G::LPB + r / CPL] : 0.f;
-                    }
-                    r0[j] = make_float4(v0[0], v0[1], v0[2], v0[3]);
-                    r2[j] = make_float4(v2[0], v2[1], v2[2], v2[3]);
-                }
-                // axis 1: FULLB places the taps at the node's tile row s1 (selects, no indexing)
-#pragma unroll
-                for (int j = 0; j < RB / 4; ++j) {
-                    float v1[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int row = 4 * j + u;
-                        float val = 0.f;
-                        if (G::FULLB) {
-#pragma unroll
-                            for (int d = 0; d < TE; ++d)
-                                if (row - d >= 0 && row - d < TAPS) val = (s1 == d) ? t1[row - d] : val;
-                        } else if (row < TAPS) {
-                            val = t1[row];
-                        }
-                        v1[u] = val;
-                    }
-                    r1[j] = make_float4(v1[0], v1[1], v1[2], v1[3]);
-                }
+        const int ntl = w.pad;                    // tiles in the item (a run along axis 2), or 1
+        // lane l holds the first node of tile w.tile + l of a run (l <= ntl <= 31)
+        const int lane_start = (ntl > 1 && lane <= ntl) ? a.tile_start[w.tile + lane] : 0;
+        woff = 0;
+        for (int jt = 0; jt < ntl; ++jt) {
+            const int tile_id = w.tile + jt;
+            int tc[3];
+            tile_coords<3>(tile_id, a.ntile, tc);
+            int cur = -1;
+            // this tile's nodes: the chunk, or the whole tile within a run
+            const int run_s = __shfl_sync(0xffffffffu, lane_start, jt);
+            const int run_e = __shfl_sync(0xffffffffu, lane_start, jt + 1);
+            const int tstart = ntl == 1 ? w.start : run_s;
+            const int tend = ntl == 1 ? wend : run_e;
+            // this warp's share of them; this lane's node of the next slice, loaded one slice ahead
+            const int share = (tend - tstart + NG - 1) / NG;
+            int base = tstart + g * share;
+            const int gend = min(tend, base + share);
+            PointF pn = {{0.f, 0.f, 0.f}, 0};
+            float xn = 0.f;
+            if (base + lane < gend) {
+                pn = a.pts[base + lane];
+                xn = a.xs[base + lane];
             }
-            const int prev = __shfl_up_sync(0xffffffffu, o, 1);
-            const unsigned runs = __ballot_sync(0xffffffffu, valid && (lane == 0 || o != prev));
-            __syncwarp();
-            int i = 0;
-            while (i < cnt) {
-                const unsigned rest = i + 1 < 32 ? (runs >> (i + 1)) : 0u;
-                const int j = rest ? min(cnt, i + __ffs(rest)) : cnt;
-                const int oi = __shfl_sync(0xffffffffu, o, i);
-                if (oi != cur) {
-                    if (cur >= 0) flush(cur);
-                    cur = oi;
+            for (; base < gend; base += S) {
+                const int cnt = min(S, gend - base);
+                const bool valid = lane < cnt;
+                int o = 0;
+                {
+                    // stage node `lane` of the slice
+                    float f[3];
+                    int s1 = 0;
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const int sa = valid ? cell_axis(pn.cell, ax) - tc[ax] * TE : 0;
+                        if (ax == 1) s1 = sa;
+                        if (ax != 1 || !G::FULLB) o |= sa << (8 * ax);     // FULLB runs ignore axis 1
+                        f[ax] = valid ? pn.f[ax] : 0.f;
+                    }
+                    const float xv = xn;
+                    const int kn = base + S + lane;
+                    if (kn < gend) {
+                        pn = a.pts[kn];
+                        xn = a.xs[kn];
+                    }
+                    const unsigned long long T0 = pack2(fmaf(2.f, f[0], -1.f), fmaf(2.f, f[0], -1.f));
+                    const unsigned long long T1 = pack2(fmaf(2.f, f[1], -1.f), fmaf(2.f, f[1], -1.f));
+                    const unsigned long long T2 = pack2(fmaf(2.f, f[2], -1.f), fmaf(2.f, f[2], -1.f));
+                    const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
+                    float t0[TAPS], t1[TAPS], t2[TAPS];
+#pragma unroll
+                    for (int q = 0; q < M; ++q) {
+                        unsigned long long h0 = pc[q * kPolyCoef + kPolyCoef - 1], h1 = h0, h2 = h0;
+#pragma unroll
+                        for (int k = kPolyCoef - 2; k >= 0; --k) {
+                            const unsigned long long c = pc[q * kPolyCoef + k];
+                            h0 = ffma2(h0, T0, c);
+                            h1 = ffma2(h1, T1, c);
+                            h2 = ffma2(h2, T2, c);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            float w0 = lane_of(h0, u), w1 = lane_of(h1, u), w2 = lane_of(h2, u);
+                            if (a.bf16) {
+                                w0 = round_bf16(w0);
+                                w1 = round_bf16(w1);
+                                w2 = round_bf16(w2);
+                            }
+                            t0[2 * q + u] = w0;
+                            t1[2 * q + u] = w1 * xv;
+                            t2[2 * q + u] = w2;
+                        }
+                    }
+                    // 16-byte stores of this lane's rows
+                    float4 *r0 = reinterpret_cast<float4 *>(w0s + lane * R1);
+                    float4 *r1 = reinterpret_cast<float4 *>(w1s + lane * RB);
+                    float4 *r2 = reinterpret_cast<float4 *>(w2s + lane * R1);
+#pragma unroll
+                    for (int j = 0; j < (TAPS + 3) / 4; ++j) {
+                        float v0[4], v2[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const bool in = 4 * j + u < TAPS;
+                            v0[u] = in ? t0[(4 * j + u) % TAPS] : 0.f;
+                            // axis 2 de-interleaved: position h CPL + c holds tap c LPB + h
+                            const int r = (4 * j + u) % TAPS;
+                            v2[u] = in ? t2[(r % CPL) * G::LPB + r / CPL] : 0.f;
+                        }
+                        r0[j] = make_float4(v0[0], v0[1], v0[2], v0[3]);
+                        r2[j] = make_float4(v2[0], v2[1], v2[2], v2[3]);
+                    }
+                    // axis 1: FULLB places the taps at the node's tile row s1 (selects, no indexing)
+#pragma unroll
+                    for (int j = 0; j < RB / 4; ++j) {
+                        float v1[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int row = 4 * j + u;
+                            float val = 0.f;
+                            if (G::FULLB) {
+#pragma unroll
+                                for (int d = 0; d < TE; ++d)
+                                    if (row - d >= 0 && row - d < TAPS) val = (s1 == d) ? t1[row - d] : val;
+                            } else if (row < TAPS) {
+                                val = t1[row];
+                            }
+                            v1[u] = val;
+                        }
+                        r1[j] = make_float4(v1[0], v1[1], v1[2], v1[3]);
+                    }
                 }
-                if (acc_lane) {
-                    int q = i;
-                    if (fresh) node(q++, std::true_type{});
+                const int prev = __shfl_up_sync(0xffffffffu, o, 1);
+                const unsigned runs = __ballot_sync(0xffffffffu, valid && (lane == 0 || o != prev));
+                __syncwarp();
+                int i = 0;
+                while (i < cnt) {
+                    const unsigned rest = i + 1 < 32 ? (runs >> (i + 1)) : 0u;
+                    const int j = rest ? min(cnt, i + __ffs(rest)) : cnt;
+                    const int oi = __shfl_sync(0xffffffffu, o, i);
+                    if (oi != cur) {
+                        if (cur >= 0) flush(cur);
+                        cur = oi;
+                    }
+                    if (acc_lane) {
+                        int q = i;
+                        if (fresh) node(q++, std::true_type{});
 #pragma unroll 2
-                    for (; q < j; ++q) node(q, std::false_type{});
+                        for (; q < j; ++q) node(q, std::false_type{});
+                    }
+                    fresh = false;
+                    i = j;
                 }
-                fresh = false;
-                i = j;
+                __syncwarp();                         // the next slice overwrites the staged taps
             }
-            __syncwarp();                         // the next slice overwrites the staged taps
-        }
-        if (cur >= 0) flush(cur);
-        __syncthreads();
-
-        // sum the tile copies -> global grid, clear them.  Consecutive threads take
-        // consecutive positions (c fastest, the grid's x2 axis), so the atomics of a
-        // warp fall on a few contiguous rows of the grid rather than one per sector.
-        {
-            constexpr int STEP = NG * 32;
-            int e = threadIdx.x;
-            int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
-            const int b0 = tc[0] * TE - (M - 1), b1 = tc[1] * TE - (M - 1), b2 = tc[2] * TE - (M - 1);
-            for (; e < PA3; e += STEP) {
-                float v = 0.f;
+            if (cur >= 0) flush(cur);
+            __syncthreads();
+            if (jt + 1 < ntl) {
+                // the TE planes q2 < TE leave the window: merge and clear them, slide by TE
+                constexpr int NLEAVE = PA * PA * TE;
+                const int b0 = tc[0] * TE - (M - 1), b1 = tc[1] * TE - (M - 1), b2 = tc[2] * TE - (M - 1);
+                for (int e = threadIdx.x; e < NLEAVE; e += NG * 32) {
+                    const int q = e % TE, r = e / TE;
+                    const int q1 = r % PA, q0 = r / PA;
+                    int slot = woff + q;
+                    if (slot >= PA) slot -= PA;
+                    const int pos = (q0 * PA + q1) * PA + slot;
+                    float v = 0.f;
 #pragma unroll
-                for (int gg = 0; gg < NG; ++gg) {
-                    float *t = reinterpret_cast<float *>(smem_raw + gg * G::WARP_BYTES) + e;
-                    v += *t;
-                    *t = 0.f;
+                    for (int gg = 0; gg < NG; ++gg) {
+                        float *t = reinterpret_cast<float *>(smem_raw + gg * G::WARP_BYTES) + pos;
+                        v += *t;
+                        *t = 0.f;
+                    }
+                    if (v == 0.f) continue;
+                    int p0 = b0 + q0, p1 = b1 + q1, p2 = b2 + q;
+                    if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
+                    const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+                    if (FIXED)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
+                                  (unsigned long long)to_fixed(v * fscale));
+                    else
+                        atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
                 }
-                int p0 = b0 + q0, p1 = b1 + q1, p2 = b2 + q2;
-                // advance (q0, q1, q2) by STEP positions
-                q2 += STEP % PA;
-                q1 += (STEP / PA) % PA;
-                q0 += STEP / (PA * PA);
-                if (q2 >= PA) { q2 -= PA; ++q1; }
-                if (q1 >= PA) { q1 -= PA; ++q0; }
-                if (v == 0.f) continue;
-                if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-                if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-                if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-                if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
-                const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
-                if (FIXED)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
-                              (unsigned long long)to_fixed(v * fscale));
-                else
-                    atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
+                woff += TE;
+                if (woff >= PA) woff -= PA;
+                __syncthreads();
+                continue;
             }
+            // sum the tile copies -> global grid, clear them.  Consecutive threads take
+            // consecutive positions (c fastest, the grid's x2 axis), so the atomics of a
+            // warp fall on a few contiguous rows of the grid rather than one per sector.
+            {
+                constexpr int STEP = NG * 32;
+                int e = threadIdx.x;
+                int q2 = e % PA, q1 = (e / PA) % PA, q0 = e / (PA * PA);
+                const int b0 = tc[0] * TE - (M - 1), b1 = tc[1] * TE - (M - 1), b2 = tc[2] * TE - (M - 1);
+                for (; e < PA3; e += STEP) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int gg = 0; gg < NG; ++gg) {
+                        float *t = reinterpret_cast<float *>(smem_raw + gg * G::WARP_BYTES) + e;
+                        v += *t;
+                        *t = 0.f;
+                    }
+                    int lq2 = q2 - woff;                      // local axis-2 plane of this slot
+                    if (lq2 < 0) lq2 += PA;
+                    int p0 = b0 + q0, p1 = b1 + q1, p2 = b2 + lq2;
+                    // advance (q0, q1, q2) by STEP positions
+                    q2 += STEP % PA;
+                    q1 += (STEP / PA) % PA;
+                    q0 += STEP / (PA * PA);
+                    if (q2 >= PA) { q2 -= PA; ++q1; }
+                    if (q1 >= PA) { q1 -= PA; ++q0; }
+                    if (v == 0.f) continue;
+                    if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
+                    const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+                    if (FIXED)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
+                                  (unsigned long long)to_fixed(v * fscale));
+                    else
+                        atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -350,7 +410,7 @@ static cudaError_t launch_warp(Plan &P, const SpreadWarpArgs &a) {
     NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NG * 32, G::SMEM));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * P.num_sms;
-    if (grid > P.nitems) grid = P.nitems;
+    if (grid > P.nsitems) grid = P.nsitems;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, G::NG * 32, G::SMEM, P.stream>>>(a);
     return cudaGetLastError();
@@ -365,8 +425,9 @@ cudaError_t launch_spread3_warp(Plan &P) {
     SpreadWarpArgs a;
     a.pts = reinterpret_cast<const PointF *>(P.pts);
     a.xs = static_cast<const float *>(P.xsort);
-    a.items = P.items;
-    a.nitems = P.nitems;
+    a.items = P.sitems;
+    a.nitems = P.nsitems;
+    a.tile_start = P.tile_start;
     for (int i = 0; i < 3; ++i) {
         a.ntile[i] = P.ntile[i];
         a.L[i] = P.L[i];

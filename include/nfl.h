@@ -193,10 +193,15 @@ nfl_status nfl_apply_host(nfl_plan *plan, int op, const double *x, int64_t ldx,
 /*
  * Products for many independent graphs in one call (a batch of plans):
  * y_g = op(x_g) for g < G with op 0 = W, 1 = A, 2 = L_s, each x_g / y_g a
- * device block of nrhs columns with leading dimension ld[g] >= n_g.  All
- * work is issued on the stream of plans[0] (every plan is moved to it), in
- * plan order, without host synchronization, so the whole batch can be
- * captured into one CUDA graph and replayed as a single launch.
+ * device block of nrhs columns with leading dimension ld[g] >= n_g.  The
+ * work forks from the stream of plans[0] onto library streams (16 per
+ * device, made on first use; plans largest first to the least loaded
+ * stream), so the products of different plans run concurrently, and joins
+ * back: the stream of plans[0] is ordered after every product, and every
+ * plan's stream is set to it on return.  No host synchronization, so the
+ * whole batch can be captured into one CUDA graph (a DAG of parallel
+ * chains) and replayed as a single launch; make one uncaptured call first,
+ * which creates the library streams.
  *   plans, x, y, ld: host arrays of G entries; plans must be distinct.
  * Returns the first failing plan's status (earlier products are issued).
  */

@@ -1,5 +1,9 @@
 // Products with W, A and L_s: Alg. 1 (spread, FFT/multiply/inverse FFT,
 // interpolate) with the Alg. 2 step 5 scalings fused into spread and gather.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "internal.h"
 
 namespace nfl {
@@ -48,6 +52,25 @@ static nfl_status apply(nfl_plan *plan, int op, const double *x, int64_t ldx, do
         if (st != NFL_OK) return st;
     }
     return NFL_OK;
+}
+
+// Library streams for batched products, one set per device, made on first use and
+// kept for the life of the process (a captured CUDA graph may refer to them).
+BatchStreams *batch_streams() {
+    static std::mutex mu;
+    static BatchStreams pools[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    BatchStreams &b = pools[dev];
+    if (b.ready) return &b;
+    for (int k = 0; k < kBatchStreams; ++k) {
+        if (!b.s[k] && cudaStreamCreateWithFlags(&b.s[k], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (!b.join[k] && cudaEventCreateWithFlags(&b.join[k], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    }
+    if (!b.fork && cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    b.ready = true;
+    return &b;
 }
 
 // Products with host-resident blocks.  Column c goes through device slot
@@ -136,16 +159,43 @@ nfl_status nfl_apply_batched(nfl_plan *const *plans, int G, int op, const double
                              const int64_t *ld, int nrhs) {
     if (!plans || !x || !y || !ld || G < 0 || op < 0 || op > 2) return NFL_ERR_INVALID_ARG;
     if (G == 0) return NFL_OK;
-    if (!plans[0]) return NFL_ERR_INVALID_ARG;
-    const cudaStream_t s = reinterpret_cast<nfl::Plan *>(plans[0])->stream;
-    const int ops[3] = {nfl::OP_W, nfl::OP_A, nfl::OP_LS};
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < G; ++g)
         if (!plans[g]) return NFL_ERR_INVALID_ARG;
-        reinterpret_cast<nfl::Plan *>(plans[g])->stream = s;
-        const nfl_status st = nfl::apply(plans[g], ops[op], x[g], ld[g], y[g], ld[g], nrhs);
-        if (st != NFL_OK) return st;
+    nfl::BatchStreams *pool = nfl::batch_streams();
+    if (!pool) return NFL_ERR_CUDA;
+    const cudaStream_t origin = reinterpret_cast<nfl::Plan *>(plans[0])->stream;
+    const int K = G < nfl::kBatchStreams ? G : nfl::kBatchStreams;
+    // plans to streams, largest first to the least loaded (longest-processing-time order)
+    std::vector<int> order(G), lane(G);
+    std::vector<int64_t> load(K, 0);
+    for (int g = 0; g < G; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return reinterpret_cast<nfl::Plan *>(plans[a])->n > reinterpret_cast<nfl::Plan *>(plans[b])->n;
+    });
+    for (int g : order) {
+        const int k = int(std::min_element(load.begin(), load.end()) - load.begin());
+        lane[g] = k;
+        load[k] += reinterpret_cast<nfl::Plan *>(plans[g])->n;
     }
-    return NFL_OK;
+    // fork from the origin stream, issue, join back (also after an error, so that the
+    // origin stream is ordered after everything issued)
+    if (cudaEventRecord(pool->fork, origin) != cudaSuccess) return NFL_ERR_CUDA;
+    for (int k = 0; k < K; ++k)
+        if (cudaStreamWaitEvent(pool->s[k], pool->fork, 0) != cudaSuccess) return NFL_ERR_CUDA;
+    const int ops[3] = {nfl::OP_W, nfl::OP_A, nfl::OP_LS};
+    nfl_status st = NFL_OK;
+    for (int g = 0; g < G && st == NFL_OK; ++g) {
+        nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plans[g]);
+        P.stream = pool->s[lane[g]];
+        st = nfl::apply(plans[g], ops[op], x[g], ld[g], y[g], ld[g], nrhs);
+    }
+    for (int k = 0; k < K; ++k) {
+        if (cudaEventRecord(pool->join[k], pool->s[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(origin, pool->join[k], 0) != cudaSuccess)
+            return NFL_ERR_CUDA;
+    }
+    for (int g = 0; g < G; ++g) reinterpret_cast<nfl::Plan *>(plans[g])->stream = origin;
+    return st;
 }
 
 nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable) {

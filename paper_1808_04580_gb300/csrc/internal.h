@@ -137,6 +137,17 @@ cudaError_t launch_spread3_warp(Plan &P);
 bool gather_tc_available(const Plan &P);
 cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y);
 
+// streams of nfl_apply_batched: plans are spread over them, forked from and joined
+// back to the caller's stream
+constexpr int kBatchStreams = 16;
+struct BatchStreams {
+    bool ready = false;
+    cudaStream_t s[kBatchStreams] = {};
+    cudaEvent_t join[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr;
+};
+BatchStreams *batch_streams();
+
 // number of kernels one column launches
 int kernels_per_column(const Plan &P);
 

@@ -55,3 +55,45 @@ def test_batched_equals_per_plan_and_graph_replay():
     ref = fastsum.NormalizedFastsum(v, 0.5, 32, 4, 4).apply_Ls(x)
     got = ys[0][:, 3].cpu().numpy()
     assert np.linalg.norm(got - ref) / np.linalg.norm(x - ref) < 2e-6
+
+
+def test_batched_256_uneven_graphs_full_size():
+    """256 Gaussian-mixture graphs, n log-uniform in [1e3, 2e5] (sum ~1.2e7), 8 columns
+    each, FP32C, sigma 0.5, N 64, m 4, one captured CUDA graph: every degree positive,
+    the replay equal to the eager batch, small members against the oracle's Alg. 2 on
+    all rows, large members against the direct sum on sampled rows."""
+    from oracle import direct
+    clouds = workloads.many_graphs(256, seed=0)
+    sizes = [c.shape[0] for c in clouds]
+    plans = [Plan(gpu(v), 0.5, 64, 4, 4, -1.0, "fp32c") for v in clouds]
+    assert all(p.info()["degree_ok"] for p in plans)
+    xs = [gpu(workloads.rhs(n, nrhs=8, seed=g + 7)) for g, n in enumerate(sizes)]
+    eager = [y.clone() for y in apply_batched(plans, xs, "Ls")]
+    outs = [torch.empty((8, n), dtype=torch.float64, device=DEV) for n in sizes]
+    apply_batched(plans, xs, "Ls", outs=outs)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        apply_batched(plans, xs, "Ls", outs=outs)
+    for o in outs:
+        o.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, x, e in zip(outs, xs, eager):
+        a, b = x - o.t(), x - e
+        assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) < 1e-6
+    order = np.argsort(sizes)
+    for g in order[:3]:                                   # smallest: oracle Alg. 2, all rows
+        ref = fastsum.NormalizedFastsum(clouds[g], 0.5, 64, 4, 4)
+        for c in (0, 5):
+            x = xs[g][:, c].cpu().numpy()
+            r = ref.apply_Ls(x)
+            got = outs[g][c].cpu().numpy()
+            assert np.linalg.norm(got - r) / np.linalg.norm(x - r) < 2e-6
+    rows = np.random.default_rng(3).choice(int(sizes[order[-1]]), 128, replace=False)
+    for g in order[-2:]:                                  # largest: direct sum on sampled rows
+        rows_g = rows[rows < sizes[g]]
+        x = xs[g][:, 2].contiguous()
+        w = plans[g].apply_W(x).cpu().numpy()
+        ref = direct.rows_W(clouds[g], 0.5, x.cpu().numpy(), rows_g)
+        assert np.linalg.norm(w[rows_g] - ref) / np.linalg.norm(ref) < 1e-5

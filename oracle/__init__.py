@@ -24,6 +24,9 @@ by eye (Alfke, Potts, Stoll, Volkmer, "NFFT meets Krylov methods", 2018):
 * ``spectral`` -- O4/O5: dense symmetric eigendecomposition and dense solves
                   for the Lanczos (Sec. 4) and CG (Sec. 6.2.2, eq.
                   (ssl::system)) checks.
+* ``apps``     -- the consumers of the eigenpairs in Sec. 6.2: spectral
+                  clustering (k-means on normalized eigenvector rows) and
+                  phase-field SSL (the Allen-Cahn convexity-splitting step).
 
 Parity status of each function is stated in its module docstring.
 """

@@ -115,6 +115,16 @@ def ball_plus_clusters(n=10_000_000, clusters=5, radius=0.6, std=0.04, seed=0):
     return pts[perm]
 
 
+def five_centres(n=2000, std=0.6, spread=3.0, seed=0):
+    """Normal clouds around five centres in U[-spread, spread]^3, each node labelled by
+    its nearest centre (the semi-supervised data of the phase-field experiment)."""
+    rng = np.random.default_rng(seed)
+    cent = rng.uniform(-spread, spread, (5, 3))
+    v = cent[rng.integers(0, 5, n)] + rng.standard_normal((n, 3)) * std
+    lab = ((v[:, None, :] - cent[None, :, :]) ** 2).sum(axis=2).argmin(axis=1)
+    return v, lab
+
+
 def two_moons(n=500_000, noise=0.05, seed=0):
     rng = np.random.default_rng(seed)
     lab = rng.integers(0, 2, n)
@@ -129,7 +139,7 @@ def two_moons(n=500_000, noise=0.05, seed=0):
 CONFIGS = {
     "spiral5k": dict(n=5000, sigma=0.5, N=32, m=4, p=4),
     "image1M": dict(n=1_000_000, sigma=0.1, N=64, m=4, p=4),
-    "graphs256": dict(graphs=256, sigma=0.5, N=32, m=4, p=4, nrhs=8),
+    "graphs256": dict(graphs=256, sigma=0.5, N=64, m=4, p=4, nrhs=8),
     "ball10M": dict(n=10_000_000, sigma=0.08, N=128, m=6, p=6),
     "moons500k": dict(n=500_000, sigma=0.2, N=128, m=4, p=4),
 }

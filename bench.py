@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-sweep", action="store_true", help="skip the W x precision sweep (FP32, FP32C, BF16W)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch parameters")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -232,6 +233,7 @@ def main():
     vg = torch.from_numpy(v).to(dev)
     xg = torch.from_numpy(np.asfortranarray(X)).to(dev)
     plan = Plan(vg, CFG["sigma"], CFG["N"], CFG["m"], CFG["p"], -1.0, args.precision)
+    tuned = plan.autotune() if not args.no_autotune else None   # launch parameters, outside the timed region
     info = plan.info()
     ycols = torch.empty((nrhs, n), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
@@ -383,7 +385,9 @@ def main():
                        "l2": "inputs larger than L2 (x block %d MB, node records %d MB)" % (
                            n * nrhs * 8 // 2**20, n * 16 // 2**20),
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "box": info["box"], "work_items": info["work_items"]},
+                       "box": info["box"], "work_items": info["work_items"],
+                       "launch_params": {"fft_lines_cap": info["fft_lines_cap"], "slide_tiles": info["slide_tiles"],
+                                         "autotuned": tuned is not None}},
             "point_rhs_per_s": value * n,
             "stage_ms_per_column": {"prep": stages["prep"] / max(1, stages["columns"]), "spread": spread_ms,
                                     "fft": fft_ms, "gather": gather_ms},

@@ -111,6 +111,8 @@ typedef struct {
     int kernel;           /* NFL_KERNEL_*                                      */
     double k0;            /* K(0) in the caller's coordinates                  */
     double out_scale;     /* factor from the scaled fast sum to the caller's   */
+    int fft_lines_cap;    /* FFT passes: grid points per CTA (lines x length)  */
+    int slide_tiles;      /* 3-D warp spread: most tiles in one sliding run    */
 } nfl_info;
 
 /*
@@ -147,6 +149,22 @@ void nfl_plan_destroy(nfl_plan *plan);
 /* Copy the plan's parameters, degree summary and device error flag into *info
  * (synchronizes the plan's stream to read the flag). */
 nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info);
+
+/*
+ * Pick the launch parameters of the plan's products by timing them on the
+ * plan's own nodes (a W product with x = 1, CUDA events on the plan's
+ * stream), one parameter at a time, keeping the fastest:
+ *   fft_lines_cap  grid points per CTA of the FFT passes (lines of length
+ *                  2N per CTA = cap / 2N), from {256, 512, 1024, 2048};
+ *   slide_tiles    3-D warp-slice spread: most tiles of one axis-2 run that
+ *                  the tile copies slide along (1 = no sliding), from
+ *                  {1, 4, 8, 16}.
+ * Results are unchanged up to the FP32 summation order of the mixed forms.
+ * The chosen values are in nfl_info; best_ms (host, may be NULL) receives
+ * the fastest time of one product.  Synchronizes the plan's stream;
+ * allocates 2 n FP64 of device scratch for the call.
+ */
+nfl_status nfl_plan_autotune(nfl_plan *plan, double *best_ms);
 
 /* Move subsequent work of the plan to another stream. */
 nfl_status nfl_set_stream(nfl_plan *plan, void *stream);

@@ -198,6 +198,100 @@ nfl_status nfl_apply_batched(nfl_plan *const *plans, int G, int op, const double
     return st;
 }
 
+nfl_status nfl_plan_autotune(nfl_plan *plan, double *best_ms) {
+    if (!plan) return NFL_ERR_INVALID_ARG;
+    nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plan);
+    const int64_t n = P.n;
+    double *x = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto release = [&]() {
+        cudaFree(x);
+        cudaFree(y);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&x, n * 8) != cudaSuccess || cudaMalloc(&y, n * 8) != cudaSuccess) {
+        release();
+        return NFL_ERR_OUT_OF_MEMORY;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        release();
+        return NFL_ERR_CUDA;
+    }
+    nfl_status st = NFL_OK;
+    // x = 1 (the degree product's input), on the plan's stream
+    {
+        const double one = 1.0;
+        std::vector<double> h(std::min<int64_t>(n, 1 << 20), one);
+        for (int64_t o = 0; o < n && st == NFL_OK; o += (int64_t)h.size()) {
+            const int64_t c = std::min<int64_t>((int64_t)h.size(), n - o);
+            if (cudaMemcpyAsync(x + o, h.data(), c * 8, cudaMemcpyHostToDevice, P.stream) != cudaSuccess ||
+                cudaStreamSynchronize(P.stream) != cudaSuccess)
+                st = NFL_ERR_CUDA;
+        }
+    }
+    const bool prof = P.profile;
+    P.profile = false;
+    // fastest of three timed products after one untimed one
+    auto time_config = [&](double &ms) -> nfl_status {
+        float best = 1e30f;
+        for (int r = 0; r < 4; ++r) {
+            if (cudaEventRecord(e0, P.stream) != cudaSuccess) return NFL_ERR_CUDA;
+            const nfl_status rs = nfl::run_column(P, nfl::OP_W, x, y);
+            if (rs != NFL_OK) return rs;
+            if (cudaEventRecord(e1, P.stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return NFL_ERR_CUDA;
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return NFL_ERR_CUDA;
+            if (r > 0 && t < best) best = t;
+        }
+        ms = best;
+        return NFL_OK;
+    };
+    double best = 1e30;
+    if (st == NFL_OK) {
+        const int caps[4] = {256, 512, 1024, 2048};
+        int best_cap = P.fft_cap;
+        for (int c : caps) {
+            P.fft_cap = c;
+            double ms = 0.0;
+            st = time_config(ms);
+            if (st != NFL_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_cap = c;
+            }
+        }
+        P.fft_cap = best_cap;
+    }
+    if (st == NFL_OK && nfl::spread_warp_available(P)) {
+        const int runs[4] = {1, 4, 8, 16};
+        const int before = P.slide_tiles;
+        int best_run = before;
+        best = 1e30;
+        for (int r : runs) {
+            P.slide_tiles = r;
+            st = nfl::rebuild_spread_items(P);
+            if (st != NFL_OK) break;
+            double ms = 0.0;
+            st = time_config(ms);
+            if (st != NFL_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_run = r;
+            }
+        }
+        P.slide_tiles = best_run;
+        const nfl_status rs = nfl::rebuild_spread_items(P);
+        if (st == NFL_OK) st = rs;
+    }
+    P.profile = prof;
+    if (st == NFL_OK && best_ms) *best_ms = best;
+    if (cudaStreamSynchronize(P.stream) != cudaSuccess && st == NFL_OK) st = NFL_ERR_CUDA;
+    release();
+    return st;
+}
+
 nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable) {
     if (!plan) return NFL_ERR_INVALID_ARG;
     nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plan);

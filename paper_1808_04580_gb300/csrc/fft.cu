@@ -222,7 +222,7 @@ static cudaError_t run_pass(Plan &P, PassArgs a) {
     using C = typename Cplx<T>::type;
     // few lines per CTA and one radix-4 butterfly per thread and stage: small CTAs,
     // many of them resident per SM to hide the global-memory latency of load and store
-    const int cap = 512;
+    const int cap = P.fft_cap;
     int BB = cap / a.n;
     BB = BB > 16 ? 16 : (BB < 1 ? 1 : BB);
     a.BB = BB;

@@ -66,6 +66,9 @@ struct Plan {
     int64_t nsitems = 0;
     WorkItem *sitems = nullptr;
     int32_t *tile_start = nullptr;      // first sorted node of each tile; [tiles_total] = n
+    std::vector<WorkItem> tile_items;   // host copy of the per-tile chunks, in tile order
+    int slide_tiles = 8;                // most tiles in one sliding run of the warp spread
+    int fft_cap = 512;                  // FFT passes: grid points per CTA
 
     // tile-sorted nodes
     void *pts = nullptr;        // PointF or PointD
@@ -150,6 +153,9 @@ BatchStreams *batch_streams();
 
 // number of kernels one column launches
 int kernels_per_column(const Plan &P);
+
+// warp-spread work items from tile_items with runs of at most slide_tiles tiles
+nfl_status rebuild_spread_items(Plan &P);
 
 // plan-time pieces
 nfl_status compute_coefficients(Plan &P);

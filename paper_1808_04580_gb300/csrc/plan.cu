@@ -239,6 +239,24 @@ static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2
     return s;
 }
 
+nfl_status rebuild_spread_items(Plan &P) {
+    std::vector<WorkItem> s = slide_items(P.tile_items, P.ntile[P.d - 1], P.slide_tiles);
+    std::stable_sort(s.begin(), s.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
+    if ((int64_t)s.size() > P.nsitems || !P.sitems) {
+        cudaFree(P.sitems);
+        P.sitems = nullptr;
+        P.nsitems = 0;
+        if (cudaMalloc(&P.sitems, std::max<size_t>(s.size(), 1) * sizeof(WorkItem)) != cudaSuccess)
+            return NFL_ERR_OUT_OF_MEMORY;
+    }
+    // ordered after any product already queued that reads the old list
+    if (cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
+    if (!s.empty() && cudaMemcpy(P.sitems, s.data(), s.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
+        return NFL_ERR_CUDA;
+    P.nsitems = (int64_t)s.size();
+    return NFL_OK;
+}
+
 __global__ void chunks_per_tile(const int32_t *count, int64_t ntiles, int32_t *chunks, unsigned long long *nonempty) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
         const int c = count[t];
@@ -780,12 +798,9 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
         if (P->nitems > 0) {
             ce = cudaMemcpy(h.data(), P->items, P->nitems * sizeof(WorkItem), cudaMemcpyDeviceToHost);
             if (ce != cudaSuccess) return NFL_ERR_CUDA;
-            std::vector<WorkItem> s = slide_items(h, P->ntile[d - 1], 8);
-            std::stable_sort(s.begin(), s.end(), by_size);
-            P->nsitems = (int64_t)s.size();
-            if (cudaMalloc(&P->sitems, s.size() * sizeof(WorkItem)) != cudaSuccess) return NFL_ERR_OUT_OF_MEMORY;
-            ce = cudaMemcpy(P->sitems, s.data(), s.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
-            if (ce != cudaSuccess) return NFL_ERR_CUDA;
+            P->tile_items = h;
+            const nfl_status sst = rebuild_spread_items(*P);
+            if (sst != NFL_OK) return sst;
             std::stable_sort(h.begin(), h.end(), by_size);
             ce = cudaMemcpy(P->items, h.data(), P->nitems * sizeof(WorkItem), cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) return NFL_ERR_CUDA;
@@ -926,6 +941,8 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->kernel = P->kernel;
     info->k0 = P->k0;
     info->out_scale = P->out_scale;
+    info->fft_lines_cap = P->fft_cap;
+    info->slide_tiles = P->slide_tiles;
     for (int a = 0; a < 3; ++a) {
         info->center[a] = P->center[a];
         info->box[a] = a < P->d ? P->L[a] : 1;

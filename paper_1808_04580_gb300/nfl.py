@@ -43,6 +43,7 @@ class Info(ctypes.Structure):
         ("work_items", ctypes.c_int64), ("min_degree", ctypes.c_double), ("max_degree", ctypes.c_double),
         ("degree_ok", ctypes.c_int), ("device_error", ctypes.c_int), ("kernel", ctypes.c_int),
         ("k0", ctypes.c_double), ("out_scale", ctypes.c_double),
+        ("fft_lines_cap", ctypes.c_int), ("slide_tiles", ctypes.c_int),
     ]
 
 
@@ -71,6 +72,7 @@ SIGNATURES = {
     "nfl_form_grad_nodes": (_I, [_P, _P, _P, _P, _P]),
     "nfl_cg_solve_backward": (_I, [_P, _P, _D, _P, _P, _P, _D, _I, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D),
                                    ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nfl_plan_autotune": (_I, [_P, ctypes.POINTER(_D)]),
     "nfl_plan_set_profiling": (_I, [_P, _I]),
     "nfl_plan_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
     "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
@@ -170,6 +172,15 @@ class Plan:
         out["center"] = list(inf.center)
         out["box"] = list(inf.box)
         return out
+
+    def autotune(self):
+        """Time the plan's products under candidate launch parameters and keep the
+        fastest (nfl_plan_autotune): dict(fft_lines_cap, slide_tiles, best_ms)."""
+        self._sync_stream()
+        ms = ctypes.c_double(0.0)
+        _check(_lib().nfl_plan_autotune(self._h, ctypes.byref(ms)), "nfl_plan_autotune")
+        inf = self.info()
+        return dict(fft_lines_cap=inf["fft_lines_cap"], slide_tiles=inf["slide_tiles"], best_ms=ms.value)
 
     def set_profiling(self, enable=True):
         _check(_lib().nfl_plan_set_profiling(self._h, 1 if enable else 0), "nfl_plan_set_profiling")

@@ -81,3 +81,10 @@ def test_host_products_reject_bad_arguments_without_gpu(lib):
     assert f(ctypes.c_void_p(16), 3, buf, 4, buf, 4, 1) == 1       # unknown op
     assert f(ctypes.c_void_p(16), -1, buf, 4, buf, 4, 1) == 1      # unknown op
     assert f(ctypes.c_void_p(16), 2, buf, 4, buf, 4, 0) == 1       # no columns
+
+
+def test_autotune_rejects_missing_plan_without_gpu(lib):
+    f = lib.nfl_plan_autotune
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert f(None, None) == 1

@@ -67,6 +67,8 @@ def test_batched_256_uneven_graphs_full_size():
     sizes = [c.shape[0] for c in clouds]
     plans = [Plan(gpu(v), 0.5, 64, 4, 4, -1.0, "fp32c") for v in clouds]
     assert all(p.info()["degree_ok"] for p in plans)
+    for p in plans:                                       # launch parameters per graph
+        p.autotune()
     xs = [gpu(workloads.rhs(n, nrhs=8, seed=g + 7)) for g, n in enumerate(sizes)]
     eager = [y.clone() for y in apply_batched(plans, xs, "Ls")]
     outs = [torch.empty((8, n), dtype=torch.float64, device=DEV) for n in sizes]

@@ -301,3 +301,20 @@ def test_bf16w_matches_bf16_tap_oracle(m, N, d):
     ya = p.apply_A(gpu(x)).cpu().numpy()
     refa = fastsum.NormalizedFastsum(v, 0.3, N, m, m, taps="bf16").apply_A(x)
     assert rel(ya, refa) < 2e-5
+
+
+@pytest.mark.parametrize("prec,m,tol", [("fp32c", 6, 2e-6), ("fp32", 4, 1e-5), ("fp64", 4, 1e-10)])
+def test_autotune_keeps_the_products(prec, m, tol):
+    """nfl_plan_autotune picks FFT CTA size and sliding-run length among its
+    candidates; the products stay those of the oracle's Alg. 2."""
+    v = _cloud("clusters", 6000, 3, seed=77)
+    x = np.random.default_rng(78).standard_normal(6000)
+    p = Plan(gpu(v), 0.3, 32, m, m, -1.0, prec)
+    before = p.info()
+    assert before["fft_lines_cap"] == 512 and before["slide_tiles"] == 8
+    t = p.autotune()
+    assert t["fft_lines_cap"] in (256, 512, 1024, 2048)
+    assert t["slide_tiles"] in (1, 4, 8, 16)
+    assert t["best_ms"] > 0.0
+    ref = fastsum.NormalizedFastsum(v, 0.3, 32, m, m).apply_W(x)
+    assert rel(p.apply_W(gpu(x)).cpu().numpy(), ref) < tol

@@ -276,18 +276,22 @@ def main():
     gather_ms = stages["gather"] / max(1, stages["columns"])
     fft_ms = stages["fft"] / max(1, stages["columns"])
     dom = "spread" if spread_ms >= gather_ms else "gather"
-    dom_ms = max(spread_ms, gather_ms)
-    flops = 2.0 * taps * n
+    # columns one spread / gather launch takes (blocks of up to 8 on the tensor-core path)
+    cpl = min(nrhs, info["block_cols"]) if plan.kernels(nrhs) < nrhs * plan.kernels_per_column() else 1
+    dom_ms = max(spread_ms, gather_ms) * cpl
+    flops = 2.0 * taps * n * cpl
     achieved = flops / (dom_ms / 1000.0) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     kname, src, summary = (("spread3_warp", "spread3_warp.cu", "spread3_warp_ball10M.md") if dom == "spread"
                            else ("gather3_tc", "gather_tc.cu", "gather3_tc_ball10M.md"))
     kernel_file = os.path.join(ROOT, "paper_1808_04580_gb300", "csrc", src)
     traffic = profiled_traffic(summary, kernel_file) if n == 10_000_000 else None
-    hbm_bytes = n * (16 + 8 + 4 + 8)  # node record, x, perm, dinv read once per column
+    if traffic is not None:
+        traffic *= cpl                # the profile is of a one-column launch
+    hbm_bytes = n * (16 + 8 + 4 + 8) * cpl  # node record, x, perm, dinv read once per column
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname,
-                "flops_per_launch": flops, "ms_per_launch": dom_ms,
+                "flops_per_launch": flops, "ms_per_launch": dom_ms, "columns_per_launch": cpl,
                 "hbm_achieved_gbs": hbm_bytes / (dom_ms / 1000.0) / 1e9,
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no measured FP32 peak)"}
 
@@ -387,6 +391,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "box": info["box"], "work_items": info["work_items"],
                        "launch_params": {"fft_lines_cap": info["fft_lines_cap"], "slide_tiles": info["slide_tiles"],
+                                         "block_cols": info["block_cols"],
                                          "autotuned": tuned is not None}},
             "point_rhs_per_s": value * n,
             "stage_ms_per_column": {"prep": stages["prep"] / max(1, stages["columns"]), "spread": spread_ms,
@@ -398,7 +403,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu_baseline,
             "e2e": e2e,
-            "gpu_launches": plan.kernels_per_column() * columns,
+            "gpu_launches": plan.kernels(nrhs) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(out))

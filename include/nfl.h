@@ -113,6 +113,7 @@ typedef struct {
     double out_scale;     /* factor from the scaled fast sum to the caller's   */
     int fft_lines_cap;    /* FFT passes: grid points per CTA (lines x length)  */
     int slide_tiles;      /* 3-D warp spread: most tiles in one sliding run    */
+    int block_cols;       /* columns per launch of a block product (1: none)   */
 } nfl_info;
 
 /*
@@ -176,6 +177,12 @@ nfl_status nfl_degree(const nfl_plan *plan, double *d);
 /*
  * y = W_E x = W~_E x - K(0) x   (Alg. 1 and Sec. 3, W = W~ - K(0) I).
  * x, y: device FP64 blocks of nrhs >= 1 columns, leading dims ldx, ldy >= n.
+ * On the 3-D FP32 / FP32C / BF16W path with m in {2, 3, 4, 6} the columns go
+ * through each stage in blocks of nfl_info.block_cols per launch: as many
+ * (up to 8) as keep a column's staged values, grids and FFT buffers within
+ * half of L2 together, 1 for large plans (the plan's buffers grow to the
+ * block's width on first use); elsewhere one column at a time.  The same
+ * holds for nfl_apply_A and nfl_apply_Ls.
  */
 nfl_status nfl_apply_W(nfl_plan *plan, const double *x, int64_t ldx,
                        double *y, int64_t ldy, int nrhs);
@@ -381,6 +388,11 @@ nfl_status nfl_plan_inject_fault(nfl_plan *plan, int kind);
 
 /* Number of kernel launches one product column makes (for launch accounting). */
 nfl_status nfl_plan_kernels_per_column(const nfl_plan *plan, int *kernels);
+
+/* Number of kernel launches one product of nrhs >= 1 columns makes: blocks of
+ * nfl_info.block_cols columns take one launch per stage on the 3-D
+ * tensor-core path. */
+nfl_status nfl_plan_kernels(const nfl_plan *plan, int nrhs, int *kernels);
 
 /* Human-readable name of a status code. */
 const char *nfl_status_string(int status);

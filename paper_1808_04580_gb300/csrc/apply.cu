@@ -14,7 +14,9 @@ int kernels_per_column(const Plan &P) {
     return (staged || P.prec == NFL_PREC_FP32C ? 1 : 0) + 1 + passes + 1;
 }
 
-static cudaError_t mark(Plan &P, int stage) {
+// stage events: 5 per timed product (before prep, spread, fft, gather, after); a
+// product of nc columns (a block) counts nc columns
+static cudaError_t mark(Plan &P, int stage, int nc = 1) {
     if (!P.profile) return cudaSuccess;
     const size_t idx = P.events_used + stage;
     while (P.events.size() <= idx) {
@@ -23,7 +25,10 @@ static cudaError_t mark(Plan &P, int stage) {
         P.events.push_back(e);
     }
     NFL_CUDA_TRY(cudaEventRecord(P.events[idx], P.stream));
-    if (stage == 4) P.events_used += 5;
+    if (stage == 4) {
+        P.events_used += 5;
+        P.event_cols.push_back(nc);
+    }
     return cudaSuccess;
 }
 
@@ -31,7 +36,7 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y) {
     const bool ones = (op == OP_DEGREE);
     const bool scale = (op == OP_A || op == OP_LS);
     NFL_STATUS_TRY(mark(P, 0));
-    NFL_STATUS_TRY(prepare_spread(P, op, x, ones, scale));
+    NFL_STATUS_TRY(prepare_spread(P, op, x, P.n, 1, ones, scale));
     NFL_STATUS_TRY(mark(P, 1));
     NFL_STATUS_TRY(launch_spread(P, x, 0, ones, scale));
     NFL_STATUS_TRY(mark(P, 2));
@@ -42,11 +47,38 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y) {
     return NFL_OK;
 }
 
+bool block_path_available(const Plan &P) { return spread_warp_available(P) && gather_tc_available(P); }
+
+// nc <= kBlockCols columns (x + c ldx -> y + c ldy) through each stage in one launch
+static nfl_status run_block(Plan &P, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nc) {
+    const bool scale = (op == OP_A || op == OP_LS);
+    const nfl_status st = ensure_columns(P, nc);
+    if (st != NFL_OK) return st;
+    NFL_STATUS_TRY(mark(P, 0));
+    NFL_STATUS_TRY(prepare_spread(P, op, x, ldx, nc, false, scale));
+    NFL_STATUS_TRY(mark(P, 1));
+    NFL_STATUS_TRY(launch_spread3_warp(P, nc));
+    NFL_STATUS_TRY(mark(P, 2));
+    NFL_STATUS_TRY(launch_fft(P, nc));
+    NFL_STATUS_TRY(mark(P, 3));
+    NFL_STATUS_TRY(launch_gather_tc(P, op, x, y, ldy, nc));
+    NFL_STATUS_TRY(mark(P, 4, nc));
+    return NFL_OK;
+}
+
 static nfl_status apply(nfl_plan *plan, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
     if (!plan || !x || !y || nrhs < 1) return NFL_ERR_INVALID_ARG;
     Plan &P = *reinterpret_cast<Plan *>(plan);
     if (ldx < P.n || ldy < P.n) return NFL_ERR_INVALID_ARG;
     if (op != OP_W && !P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
+    if (nrhs > 1 && P.block_cols > 1 && block_path_available(P)) {
+        for (int c = 0; c < nrhs; c += P.block_cols) {
+            const int nc = nrhs - c < P.block_cols ? nrhs - c : P.block_cols;
+            const nfl_status st = run_block(P, op, x + c * ldx, ldx, y + c * ldy, ldy, nc);
+            if (st != NFL_OK) return st;
+        }
+        return NFL_OK;
+    }
     for (int c = 0; c < nrhs; ++c) {
         nfl_status st = run_column(P, op, x + c * ldx, y + c * ldy);
         if (st != NFL_OK) return st;
@@ -297,6 +329,7 @@ nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable) {
     nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plan);
     P.profile = enable != 0;
     P.events_used = 0;
+    P.event_cols.clear();
     return NFL_OK;
 }
 
@@ -305,16 +338,32 @@ nfl_status nfl_plan_stage_times(nfl_plan *plan, double *ms, int64_t *columns) {
     nfl::Plan &P = *reinterpret_cast<nfl::Plan *>(plan);
     if (cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
     for (int s = 0; s < 4; ++s) ms[s] = 0.0;
-    const size_t cols = P.events_used / 5;
-    for (size_t c = 0; c < cols; ++c)
+    const size_t sets = P.events_used / 5;
+    int64_t cols = 0;
+    for (size_t c = 0; c < sets; ++c) {
         for (int s = 0; s < 4; ++s) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, P.events[5 * c + s], P.events[5 * c + s + 1]) != cudaSuccess)
                 return NFL_ERR_CUDA;
             ms[s] += t;
         }
-    if (columns) *columns = (int64_t)cols;
+        cols += c < P.event_cols.size() ? P.event_cols[c] : 1;
+    }
+    if (columns) *columns = cols;
     P.events_used = 0;
+    P.event_cols.clear();
+    return NFL_OK;
+}
+
+nfl_status nfl_plan_kernels(const nfl_plan *plan, int nrhs, int *kernels) {
+    if (!plan || !kernels || nrhs < 1) return NFL_ERR_INVALID_ARG;
+    const nfl::Plan &P = *reinterpret_cast<const nfl::Plan *>(plan);
+    if (nrhs > 1 && P.block_cols > 1 && nfl::block_path_available(P)) {
+        const int blocks = (nrhs + P.block_cols - 1) / P.block_cols;
+        *kernels = blocks * nfl::kernels_per_column(P);   // one launch per stage and block
+    } else {
+        *kernels = nrhs * nfl::kernels_per_column(P);
+    }
     return NFL_OK;
 }
 

@@ -50,7 +50,8 @@ struct PassArgs {
     const void *tw;       // e^{-2 pi i q / n}, q < n/2
     const void *M;        // fused multiplier, index ((b * nA) + a) * (N + 1) + (k + N/2)
     int real_in, real_out;
-    const double *abs_sum;  // int64 fixed-point input: sum |x~| of the spread call
+    const double *abs_sum;  // int64 fixed-point input: sum |x~| of the spread call, per column
+    int64_t in_cstride, out_cstride;   // elements between the columns of a block (grid.z)
 };
 
 // Grid value as a real of the FFT type.  int64 fixed point to FP32 through its
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *bx = reinterpret_cast<C *>(smem_raw);
     C *by = bx + a.BB * a.n;
+    const int col = blockIdx.z;
     const int ai = blockIdx.y;
     const int b0 = blockIdx.x * a.BB;
     const int nb = min(a.BB, a.nB - b0);
@@ -152,13 +154,13 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     __syncthreads();
 
     T in_scale = T(1);
-    if (std::is_same<TIN, long long>::value) in_scale = T(fixed_point_unscale(*a.abs_sum));
+    if (std::is_same<TIN, long long>::value) in_scale = T(fixed_point_unscale(a.abs_sum[col]));
 
     // load
     for (int e = threadIdx.x; e < nb * a.Lin; e += blockDim.x) {
         const int bb = (int)__umulhi((unsigned)e, a.lin_magic);
         const int c = e - bb * a.Lin;
-        const int64_t src = ai * a.sA + (int64_t)(b0 + bb) * a.sB + c;
+        const int64_t src = col * a.in_cstride + ai * a.sA + (int64_t)(b0 + bb) * a.sB + c;
         C v;
         if (MODE == P_FWD_R2C || (MODE == P_FUSED && a.real_in)) {
             const TIN *in = reinterpret_cast<const TIN *>(a.in);
@@ -211,14 +213,14 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
         else if (MODE == P_FWD_C2C) idx = (cc - N / 2 + n) & (n - 1);
         else idx = cc;
         const C v = res[bb * n + idx];
-        const int64_t dst = cc * a.oC + (int64_t)ai * a.oA + b0 + bb;
+        const int64_t dst = col * a.out_cstride + cc * a.oC + (int64_t)ai * a.oA + b0 + bb;
         if (MODE == P_INV_C2R || (MODE == P_FUSED && a.real_out)) reinterpret_cast<T *>(a.out)[dst] = v.x;
         else reinterpret_cast<C *>(a.out)[dst] = v;
     }
 }
 
 template <typename T, typename TIN, int MODE>
-static cudaError_t run_pass(Plan &P, PassArgs a) {
+static cudaError_t run_pass(Plan &P, PassArgs a, int nc) {
     using C = typename Cplx<T>::type;
     // few lines per CTA and one radix-4 butterfly per thread and stage: small CTAs,
     // many of them resident per SM to hide the global-memory latency of load and store
@@ -231,13 +233,13 @@ static cudaError_t run_pass(Plan &P, PassArgs a) {
     int threads = BB * a.n / 4;
     threads = threads < 64 ? 64 : (threads > 256 ? 256 : threads);
     NFL_CUDA_TRY(cudaFuncSetAttribute(fft_pass<T, TIN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    dim3 grid((a.nB + BB - 1) / BB, a.nA);
+    dim3 grid((a.nB + BB - 1) / BB, a.nA, nc);
     fft_pass<T, TIN, MODE><<<grid, threads, smem, P.stream>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, typename TIN>
-static cudaError_t launch_fft_t(Plan &P) {
+static cudaError_t launch_fft_t(Plan &P, int nc) {
     const int N = P.N, n = P.ngrid;
     int logn = 0;
     while ((1 << logn) < n) ++logn;
@@ -248,6 +250,16 @@ static cudaError_t launch_fft_t(Plan &P) {
     base.tw = P.twiddle;
     base.M = P.mult;
     base.abs_sum = P.scratch;
+    // column strides (elements) of the block buffers
+    const int64_t sg = P.box_elems, sa = P.bufA_elems, sb = P.bufB_elems;
+    auto stride_of = [&](const void *buf) -> int64_t {
+        return buf == P.grid || buf == P.g ? sg : (buf == P.bufA ? sa : sb);
+    };
+    auto with_strides = [&](PassArgs a) {
+        a.in_cstride = stride_of(a.in);
+        a.out_cstride = stride_of(a.out);
+        return a;
+    };
     const int64_t L0 = P.L[0], L1 = P.L[1], L2 = P.L[2];
     if (P.d == 1) {
         PassArgs a = base;
@@ -255,7 +267,7 @@ static cudaError_t launch_fft_t(Plan &P) {
         a.nA = 1; a.nB = 1; a.sA = 0; a.sB = 0; a.Lin = (int)L0;
         a.oC = 1; a.oA = 0; a.Lout = (int)L0;
         a.real_in = 1; a.real_out = 1;
-        return run_pass<T, TIN, P_FUSED>(P, a);
+        return run_pass<T, TIN, P_FUSED>(P, with_strides(a), nc);
     }
     if (P.d == 2) {
         const int64_t K1 = N / 2 + 1;
@@ -263,50 +275,50 @@ static cudaError_t launch_fft_t(Plan &P) {
         f1.in = P.grid; f1.out = P.bufA;
         f1.nA = 1; f1.nB = (int)L0; f1.sA = 0; f1.sB = L1; f1.Lin = (int)L1;
         f1.oC = L0; f1.oA = 0; f1.Lout = (int)K1;
-        NFL_CUDA_TRY((run_pass<T, TIN, P_FWD_R2C>(P, f1)));
+        NFL_CUDA_TRY((run_pass<T, TIN, P_FWD_R2C>(P, with_strides(f1), nc)));
         PassArgs f3 = base;
         f3.in = P.bufA; f3.out = P.bufB;
         f3.nA = 1; f3.nB = (int)K1; f3.sA = 0; f3.sB = L0; f3.Lin = (int)L0;
         f3.oC = K1; f3.oA = 0; f3.Lout = (int)L0;
-        NFL_CUDA_TRY((run_pass<T, T, P_FUSED>(P, f3)));
+        NFL_CUDA_TRY((run_pass<T, T, P_FUSED>(P, with_strides(f3), nc)));
         PassArgs i1 = base;
         i1.in = P.bufB; i1.out = P.g;
         i1.nA = 1; i1.nB = (int)L0; i1.sA = 0; i1.sB = K1; i1.Lin = (int)K1;
         i1.oC = L0; i1.oA = 0; i1.Lout = (int)L1;
-        return run_pass<T, T, P_INV_C2R>(P, i1);
+        return run_pass<T, T, P_INV_C2R>(P, with_strides(i1), nc);
     }
     const int64_t K2 = N / 2 + 1, K1 = N + 1;
     PassArgs f1 = base;
     f1.in = P.grid; f1.out = P.bufA;
     f1.nA = (int)L0; f1.nB = (int)L1; f1.sA = L1 * L2; f1.sB = L2; f1.Lin = (int)L2;
     f1.oC = L0 * L1; f1.oA = L1; f1.Lout = (int)K2;
-    NFL_CUDA_TRY((run_pass<T, TIN, P_FWD_R2C>(P, f1)));
+    NFL_CUDA_TRY((run_pass<T, TIN, P_FWD_R2C>(P, with_strides(f1), nc)));
     PassArgs f2 = base;
     f2.in = P.bufA; f2.out = P.bufB;
     f2.nA = (int)K2; f2.nB = (int)L0; f2.sA = L0 * L1; f2.sB = L1; f2.Lin = (int)L1;
     f2.oC = K2 * L0; f2.oA = L0; f2.Lout = (int)K1;
-    NFL_CUDA_TRY((run_pass<T, T, P_FWD_C2C>(P, f2)));
+    NFL_CUDA_TRY((run_pass<T, T, P_FWD_C2C>(P, with_strides(f2), nc)));
     PassArgs f3 = base;
     f3.in = P.bufB; f3.out = P.bufA;
     f3.nA = (int)K2; f3.nB = (int)K1; f3.sA = L0; f3.sB = K2 * L0; f3.Lin = (int)L0;
     f3.oC = K2 * K1; f3.oA = K1; f3.Lout = (int)L0;
-    NFL_CUDA_TRY((run_pass<T, T, P_FUSED>(P, f3)));
+    NFL_CUDA_TRY((run_pass<T, T, P_FUSED>(P, with_strides(f3), nc)));
     PassArgs i2 = base;
     i2.in = P.bufA; i2.out = P.bufB;
     i2.nA = (int)L0; i2.nB = (int)K2; i2.sA = K2 * K1; i2.sB = K1; i2.Lin = (int)K1;
     i2.oC = L0 * K2; i2.oA = K2; i2.Lout = (int)L1;
-    NFL_CUDA_TRY((run_pass<T, T, P_INV_C2C>(P, i2)));
+    NFL_CUDA_TRY((run_pass<T, T, P_INV_C2C>(P, with_strides(i2), nc)));
     PassArgs i1 = base;
     i1.in = P.bufB; i1.out = P.g;
     i1.nA = (int)L1; i1.nB = (int)L0; i1.sA = L0 * K2; i1.sB = K2; i1.Lin = (int)K2;
     i1.oC = L1 * L0; i1.oA = L0; i1.Lout = (int)L2;
-    return run_pass<T, T, P_INV_C2R>(P, i1);
+    return run_pass<T, T, P_INV_C2R>(P, with_strides(i1), nc);
 }
 
-cudaError_t launch_fft(Plan &P) {
-    if (P.prec == NFL_PREC_FP32) return launch_fft_t<float, float>(P);
-    if (P.prec == NFL_PREC_FP32C) return launch_fft_t<float, long long>(P);
-    return launch_fft_t<double, double>(P);
+cudaError_t launch_fft(Plan &P, int nc) {
+    if (P.prec == NFL_PREC_FP32) return launch_fft_t<float, float>(P, nc);
+    if (P.prec == NFL_PREC_FP32C) return launch_fft_t<float, long long>(P, nc);
+    return launch_fft_t<double, double>(P, nc);
 }
 
 }  // namespace nfl

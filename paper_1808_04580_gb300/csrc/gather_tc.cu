@@ -41,7 +41,9 @@ struct GatherTCArgs {
     double *degree_out;
     double *dinv_out;
     const WorkItem *items;
-    int64_t nitems;
+    int64_t nitems;   // items of one column; the grid takes nitems * ncol
+    int ncol;         // columns of a block product (item it: item it / ncol, column it % ncol)
+    int64_t g_stride, z_stride, ldy;   // column strides of g, zd and y
     int ntile[3];
     int L[3];
     int wrap[3];
@@ -129,8 +131,13 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
         // the CTA's next work item (largest first: the plan sorts them by size)
         if (tid == 0) next_item = atomicAdd(a.counter, 1u);
         __syncthreads();
-        const int64_t it = next_item;
-        if (it >= a.nitems) break;
+        const unsigned itc = next_item;
+        if (itc >= (unsigned)(a.nitems * a.ncol)) break;
+        const unsigned it = a.ncol == 1 ? itc : itc / (unsigned)a.ncol;
+        const int col = (int)(itc - it * (unsigned)a.ncol);
+        const float *gc = a.g + col * a.g_stride;
+        const double *zc = a.zd + col * a.z_stride;
+        double *yc = a.y + col * a.ldy;
         const WorkItem w = a.items[it];
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
@@ -144,7 +151,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
             if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
             if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
             const bool ok12 = used && p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2];
-            const float *src = a.g + ((int64_t)(ok12 ? p2 : 0) * a.L[1] + (ok12 ? p1 : 0)) * a.L[0];
+            const float *src = gc + ((int64_t)(ok12 ? p2 : 0) * a.L[1] + (ok12 ? p1 : 0)) * a.L[0];
             float v[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                     const PointF p = a.pts[kq];
                     // epilogue operands, loaded now and used after the contraction
                     iq = a.perm[kq];
-                    if (a.op != OP_DEGREE) zq = a.zd[kq];
+                    if (a.op != OP_DEGREE) zq = zc[kq];
                     if (a.op == OP_A || a.op == OP_LS) dq = a.dinv[kq];
                     s0 = cell_axis(p.cell, 0) - tc[0] * TE;
                     s1 = cell_axis(p.cell, 1) - tc[1] * TE;
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                         a.dinv_out[kq] = dd > 0.0 ? 1.0 / sqrt(dd) : 0.0;
                     } else {
                         const double s = a.op == OP_W ? a.out_scale : (a.op == OP_A ? a.out_scale : -a.out_scale) * dq;
-                        a.y[iq] = fma(s, fd, zq);
+                        yc[iq] = fma(s, fd, zq);
                     }
                 }
             }
@@ -374,7 +381,7 @@ static cudaError_t launch_tc(Plan &P, const GatherTCArgs &a) {
     static_assert(2 * G::A_BYTES + 2 * G::B_BYTES + 1024 <= 52 * 1024, "operands fit");
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int64_t grid = 4LL * P.num_sms;
-    if (grid > P.nitems) grid = P.nitems;
+    if (grid > P.nitems * a.ncol) grid = P.nitems * a.ncol;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, 128, smem, P.stream>>>(a);
     return cudaGetLastError();
@@ -385,8 +392,12 @@ bool gather_tc_available(const Plan &P) {
     return P.m == 2 || P.m == 3 || P.m == 4 || P.m == 6 || P.m == 7;
 }
 
-cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y) {
+cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y, int64_t ldy, int nc) {
     GatherTCArgs a;
+    a.ncol = nc;
+    a.g_stride = P.box_elems;
+    a.z_stride = P.n;
+    a.ldy = ldy;
     a.pts = reinterpret_cast<const PointF *>(P.pts);
     a.perm = P.perm;
     a.zd = P.xsorted;

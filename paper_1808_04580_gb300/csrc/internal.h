@@ -34,6 +34,7 @@ struct WorkItem {
 
 constexpr int kMaxM = 12;
 constexpr int kHostSlots = 3;   // device staging slots per direction for host-buffer products
+constexpr int kBlockCols = 8;   // columns a block product takes through each stage in one launch
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 
 struct Plan {
@@ -90,6 +91,13 @@ struct Plan {
 
     // FFT data
     int K[3] = {1, 1, 1};       // kept frequencies per axis (R2C axis N/2+1, others N+1)
+    // per-column buffers below hold `cols` columns (1 until a block product needs more):
+    // grid, bufA, bufB, g with column strides box_elems, bufA_elems, bufB_elems, box_elems;
+    // xsort, xsorted with stride n; column c's FP32C scale sum |x~| at scratch[c]
+    int cols = 1;
+    int block_cols = 1;                 // columns per block product (1: column by column)
+    int l2_bytes = 0;
+    int64_t bufA_elems = 0, bufB_elems = 0;
     void *grid = nullptr;       // spreading grid: float, double or int64 (FP32C)
     void *bufA = nullptr;       // complex FFT intermediates
     void *bufB = nullptr;
@@ -113,6 +121,7 @@ struct Plan {
     bool profile = false;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
+    std::vector<int> event_cols;        // columns covered by each timed product
 };
 
 // Precision-dependent element types.
@@ -120,9 +129,9 @@ inline bool fft_is_double(int prec) { return prec == NFL_PREC_FP64; }
 inline bool points_are_double(int prec) { return prec == NFL_PREC_FP64; }
 
 // launchers (stream-ordered, no host sync)
-cudaError_t prepare_spread(Plan &P, int op, const double *x, bool ones, bool scale_dinv);
+cudaError_t prepare_spread(Plan &P, int op, const double *x, int64_t ldx, int nc, bool ones, bool scale_dinv);
 cudaError_t launch_spread(Plan &P, const double *x, int64_t col_off, bool ones, bool scale_dinv);
-cudaError_t launch_fft(Plan &P);
+cudaError_t launch_fft(Plan &P, int nc = 1);
 cudaError_t launch_gather(Plan &P, int op, const double *x, double *y);
 cudaError_t launch_fixed_scale(Plan &P, const double *x, bool ones, bool scale_dinv);
 
@@ -132,13 +141,14 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y);
 // 3-D atomic-free spreading (spread3.cu): tile edge it needs for cut-off m (0: not available)
 int column_tile_edge(int m);
 cudaError_t launch_spread3_columns(Plan &P, const double *x, bool ones, bool scale_dinv);
-cudaError_t stage_spread3_values(Plan &P, int op, const double *x, bool ones, bool scale_dinv);
+cudaError_t stage_spread3_values(Plan &P, int op, const double *x, int64_t ldx, int nc, bool ones,
+                                 bool scale_dinv);
 bool spread_warp_available(const Plan &P);
-cudaError_t launch_spread3_warp(Plan &P);
+cudaError_t launch_spread3_warp(Plan &P, int nc = 1);
 
 // 3-D interpolation on the tensor cores (gather_tc.cu)
 bool gather_tc_available(const Plan &P);
-cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y);
+cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y, int64_t ldy = 0, int nc = 1);
 
 // streams of nfl_apply_batched: plans are spread over them, forked from and joined
 // back to the caller's stream
@@ -153,6 +163,11 @@ BatchStreams *batch_streams();
 
 // number of kernels one column launches
 int kernels_per_column(const Plan &P);
+
+// block products: nc <= kBlockCols columns through each stage in one launch (3-D
+// warp spread + tensor-core gather only); the buffers grow to nc columns first
+bool block_path_available(const Plan &P);
+nfl_status ensure_columns(Plan &P, int nc);
 
 // warp-spread work items from tile_items with runs of at most slide_tiles tiles
 nfl_status rebuild_spread_items(Plan &P);

@@ -239,6 +239,29 @@ static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2
     return s;
 }
 
+// Grow the per-column buffers to nc columns (contents are not kept).
+nfl_status ensure_columns(Plan &P, int nc) {
+    if (nc <= P.cols) return NFL_OK;
+    if (cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
+    const bool fd = fft_is_double(P.prec);
+    const size_t real_sz = fd ? 8 : 4, cplx_sz = 2 * real_sz;
+    const size_t grid_sz = P.prec == NFL_PREC_FP32 ? 4 : 8;
+    void *grid = nullptr, *bufA = nullptr, *bufB = nullptr, *g = nullptr, *xsort = nullptr;
+    double *xsorted = nullptr;
+    if (cudaMalloc(&grid, P.box_elems * grid_sz * nc) != cudaSuccess ||
+        cudaMalloc(&bufA, P.bufA_elems * cplx_sz * nc) != cudaSuccess ||
+        cudaMalloc(&bufB, P.bufB_elems * cplx_sz * nc) != cudaSuccess ||
+        cudaMalloc(&g, P.box_elems * real_sz * nc) != cudaSuccess || cudaMalloc(&xsort, P.n * 8 * nc) != cudaSuccess ||
+        cudaMalloc(&xsorted, P.n * 8 * nc) != cudaSuccess) {
+        cudaFree(grid); cudaFree(bufA); cudaFree(bufB); cudaFree(g); cudaFree(xsort); cudaFree(xsorted);
+        return NFL_ERR_OUT_OF_MEMORY;
+    }
+    cudaFree(P.grid); cudaFree(P.bufA); cudaFree(P.bufB); cudaFree(P.g); cudaFree(P.xsort); cudaFree(P.xsorted);
+    P.grid = grid; P.bufA = bufA; P.bufB = bufB; P.g = g; P.xsort = xsort; P.xsorted = xsorted;
+    P.cols = nc;
+    return NFL_OK;
+}
+
 nfl_status rebuild_spread_items(Plan &P) {
     std::vector<WorkItem> s = slide_items(P.tile_items, P.ntile[P.d - 1], P.slide_tiles);
     std::stable_sort(s.begin(), s.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
@@ -661,6 +684,7 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
     int dev = 0;
     NFL_STATUS_TRY(cudaGetDevice(&dev));
     NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->l2_bytes, cudaDevAttrL2CacheSize, dev));
     NFL_STATUS_TRY(cudaMalloc(&P->scratch, 64 * sizeof(double)));
     NFL_STATUS_TRY(cudaMalloc(&P->error_flag, sizeof(int)));
     NFL_STATUS_TRY(cudaMalloc(&P->work_counter, 2 * sizeof(unsigned)));
@@ -820,6 +844,17 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
         mult = K0 * Kh * K0;
     }
     const size_t grid_sz = prec == NFL_PREC_FP32 ? 4 : 8;
+    P->bufA_elems = bufA;
+    P->bufB_elems = bufB;
+    {
+        // block width: as many columns as keep their staged values, grids and FFT
+        // buffers within half of L2 (so consecutive stages find their inputs there)
+        const double per_col = double(n) * (4 + 8) + double(P->box_elems) * (grid_sz + real_sz) +
+                               double(bufA + bufB) * cplx_sz;
+        const double budget = 0.5 * double(P->l2_bytes > 0 ? P->l2_bytes : (64 << 20));
+        const int w = int(budget / per_col);
+        P->block_cols = w < 1 ? 1 : (w > kBlockCols ? kBlockCols : w);
+    }
     if (cudaMalloc(&P->grid, P->box_elems * grid_sz) != cudaSuccess ||
         cudaMalloc(&P->bufA, bufA * cplx_sz) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz) != cudaSuccess ||
         cudaMalloc(&P->g, P->box_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
@@ -943,6 +978,7 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->out_scale = P->out_scale;
     info->fft_lines_cap = P->fft_cap;
     info->slide_tiles = P->slide_tiles;
+    info->block_cols = P->block_cols;
     for (int a = 0; a < 3; ++a) {
         info->center[a] = P->center[a];
         info->box[a] = a < P->d ? P->L[a] : 1;

@@ -56,11 +56,17 @@ struct Spread3Args {
 // z_k, the x-only part of the interpolation epilogue y = z + s f (Alg. 2 step 5,
 // K(0) = k0, d = dinv):
 //   W: z = -k0 x,  A: z = -k0 d^2 x,  L_s: z = x + k0 d^2 x   (none for the degree).
+// Column blockIdx.y of a block: x + c ldx in, out + c n and z_out + c n out, abs_sum[c].
 template <typename T>
-__global__ void __launch_bounds__(256) stage_values(const double *x, const int32_t *perm, const double *dinv,
-                                                    int64_t n, int ones, T *out, double *z_out, int op, double k0,
-                                                    double *abs_sum) {
+__global__ void __launch_bounds__(256) stage_values(const double *x, int64_t ldx, const int32_t *perm,
+                                                    const double *dinv, int64_t n, int ones, T *out, double *z_out,
+                                                    int op, double k0, double *abs_sum) {
     __shared__ double red[256];
+    const int col = blockIdx.y;
+    x += col * ldx;
+    out += col * n;
+    z_out += col * n;
+    if (abs_sum) abs_sum += col;
     double acc = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const double xv = ones ? 1.0 : x[perm[k]];
@@ -398,20 +404,21 @@ static cudaError_t dispatch_cols(Plan &P, const Spread3Args &a) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t stage_spread3_values(Plan &P, int op, const double *x, bool ones, bool scale_dinv) {
+cudaError_t stage_spread3_values(Plan &P, int op, const double *x, int64_t ldx, int nc, bool ones,
+                                 bool scale_dinv) {
     const double *dinv = scale_dinv ? P.dinv_sorted : nullptr;
     double *abs_sum = nullptr;
     if (P.prec == NFL_PREC_FP32C) {
-        NFL_CUDA_TRY(cudaMemsetAsync(P.scratch, 0, sizeof(double), P.stream));
+        NFL_CUDA_TRY(cudaMemsetAsync(P.scratch, 0, nc * sizeof(double), P.stream));
         abs_sum = P.scratch;
     }
-    const int blocks = P.num_sms * 4;
+    const dim3 blocks((P.num_sms * 4 + nc - 1) / nc, nc);
     if (P.prec == NFL_PREC_FP64)
-        stage_values<double><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
+        stage_values<double><<<blocks, 256, 0, P.stream>>>(x, ldx, P.perm, dinv, P.n, ones ? 1 : 0,
                                                            static_cast<double *>(P.xsort), P.xsorted, op, P.k0,
                                                            abs_sum);
     else
-        stage_values<float><<<blocks, 256, 0, P.stream>>>(x, P.perm, dinv, P.n, ones ? 1 : 0,
+        stage_values<float><<<blocks, 256, 0, P.stream>>>(x, ldx, P.perm, dinv, P.n, ones ? 1 : 0,
                                                           static_cast<float *>(P.xsort), P.xsorted, op, P.k0,
                                                           abs_sum);
     return cudaGetLastError();

@@ -44,15 +44,17 @@ namespace nfl {
 
 struct SpreadWarpArgs {
     const PointF *pts;
-    const float *xs;                // x~ in sorted order
+    const float *xs;                // x~ in sorted order, column c at xs + c * xs_stride
     const WorkItem *items;
-    int64_t nitems;
+    int64_t nitems;                 // items of one column; the grid takes nitems * ncol
+    int ncol;                       // columns of a block product (item it: item it / ncol, column it % ncol)
+    int64_t xs_stride, grid_stride;
     int ntile[3];
     int L[3];
     int wrap[3];
     int ngrid;
     void *grid;
-    const double *abs_sum;
+    const double *abs_sum;          // column c: abs_sum[c]
     const int32_t *tile_start;      // first sorted node of each tile
     unsigned *counter;              // next work item, shared by all CTAs
     int bf16;                       // BF16W: taps rounded to BF16
@@ -89,7 +91,8 @@ struct WarpGeom {
     static_assert(WARP_BYTES % 16 == 0, "16-byte aligned per-warp areas");
 };
 
-template <int M, int TE, bool FIXED>
+// BLOCK: a block product of a.ncol columns (item, column pairs); otherwise one column
+template <int M, int TE, bool FIXED, bool BLOCK>
 __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(SpreadWarpArgs a) {
     using G = WarpGeom<M, TE>;
     constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, RP = G::RP, CPL = G::CPL, S = G::S, NG = G::NG,
@@ -114,8 +117,10 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         polys[q][k] = make_float2(a.poly[2 * q][k], a.poly[2 * q + 1][k]);
     }
     for (int e = lane; e < G::TILE; e += 32) tile[e] = 0.f;
-    float fscale = 1.f;
-    if (FIXED) fscale = float(fixed_scale_of(*a.abs_sum));
+    __shared__ float fscales[kBlockCols];           // FP32C scale 2^k of each column of a block
+    if (FIXED && BLOCK && threadIdx.x < a.ncol) fscales[threadIdx.x] = float(fixed_scale_of(a.abs_sum[threadIdx.x]));
+    float fscale1 = 1.f;                            // the one column's
+    if (FIXED && !BLOCK) fscale1 = float(fixed_scale_of(*a.abs_sum));
     __syncthreads();
 
     unsigned long long acc[RP][CPL];              // (ja, ja + 1) pairs for each column jc
@@ -182,8 +187,15 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
         // the CTA's next work item (largest first: the plan sorts them by size)
         if (threadIdx.x == 0) next_item = atomicAdd(a.counter, 1u);
         __syncthreads();
-        const int64_t it = next_item;
-        if (it >= a.nitems) break;
+        const int64_t itc = next_item;
+        if (itc >= a.nitems * (BLOCK ? a.ncol : 1)) break;
+        const int64_t it = BLOCK ? (int64_t)((unsigned)itc / (unsigned)a.ncol) : itc;
+        const int col = BLOCK ? (int)(itc - it * a.ncol) : 0;
+        const float *xs = BLOCK ? a.xs + col * a.xs_stride : a.xs;
+        const float fscale = !FIXED ? 1.f : (BLOCK ? fscales[col] : fscale1);
+        void *const gridc = !BLOCK ? a.grid
+                                   : FIXED ? (void *)(reinterpret_cast<unsigned long long *>(a.grid) + col * a.grid_stride)
+                                           : (void *)(reinterpret_cast<float *>(a.grid) + col * a.grid_stride);
         const WorkItem w = a.items[it];
         const int wend = w.start + w.count;
         const int ntl = w.pad;                    // tiles in the item (a run along axis 2), or 1
@@ -208,7 +220,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
             float xn = 0.f;
             if (base + lane < gend) {
                 pn = a.pts[base + lane];
-                xn = a.xs[base + lane];
+                xn = xs[base + lane];
             }
             for (; base < gend; base += S) {
                 const int cnt = min(S, gend - base);
@@ -229,7 +241,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     const int kn = base + S + lane;
                     if (kn < gend) {
                         pn = a.pts[kn];
-                        xn = a.xs[kn];
+                        xn = xs[kn];
                     }
                     const unsigned long long T0 = pack2(fmaf(2.f, f[0], -1.f), fmaf(2.f, f[0], -1.f));
                     const unsigned long long T1 = pack2(fmaf(2.f, f[1], -1.f), fmaf(2.f, f[1], -1.f));
@@ -347,10 +359,10 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
                     const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
                     if (FIXED)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
+                        atomicAdd(reinterpret_cast<unsigned long long *>(gridc) + gidx,
                                   (unsigned long long)to_fixed(v * fscale));
                     else
-                        atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
+                        atomicAdd(reinterpret_cast<float *>(gridc) + gidx, v);
                 }
                 woff += TE;
                 if (woff >= PA) woff -= PA;
@@ -389,10 +401,10 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
                     const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
                     if (FIXED)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.grid) + gidx,
+                        atomicAdd(reinterpret_cast<unsigned long long *>(gridc) + gidx,
                                   (unsigned long long)to_fixed(v * fscale));
                     else
-                        atomicAdd(reinterpret_cast<float *>(a.grid) + gidx, v);
+                        atomicAdd(reinterpret_cast<float *>(gridc) + gidx, v);
                 }
             }
             __syncthreads();
@@ -403,14 +415,14 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
 template <int M, int TE, bool FIXED>
 static cudaError_t launch_warp(Plan &P, const SpreadWarpArgs &a) {
     using G = WarpGeom<M, TE>;
-    auto kern = spread3_warp<M, TE, FIXED>;
+    auto kern = a.ncol > 1 ? spread3_warp<M, TE, FIXED, true> : spread3_warp<M, TE, FIXED, false>;
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 0;
     NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NG * 32, G::SMEM));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * P.num_sms;
-    if (grid > P.nsitems) grid = P.nsitems;
+    if (grid > P.nsitems * a.ncol) grid = P.nsitems * a.ncol;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, G::NG * 32, G::SMEM, P.stream>>>(a);
     return cudaGetLastError();
@@ -421,8 +433,11 @@ bool spread_warp_available(const Plan &P) {
     return P.m == 2 || P.m == 3 || P.m == 4 || P.m == 6;
 }
 
-cudaError_t launch_spread3_warp(Plan &P) {
+cudaError_t launch_spread3_warp(Plan &P, int nc) {
     SpreadWarpArgs a;
+    a.ncol = nc;
+    a.xs_stride = P.n;
+    a.grid_stride = P.box_elems;
     a.pts = reinterpret_cast<const PointF *>(P.pts);
     a.xs = static_cast<const float *>(P.xsort);
     a.items = P.sitems;

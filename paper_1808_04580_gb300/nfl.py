@@ -43,7 +43,7 @@ class Info(ctypes.Structure):
         ("work_items", ctypes.c_int64), ("min_degree", ctypes.c_double), ("max_degree", ctypes.c_double),
         ("degree_ok", ctypes.c_int), ("device_error", ctypes.c_int), ("kernel", ctypes.c_int),
         ("k0", ctypes.c_double), ("out_scale", ctypes.c_double),
-        ("fft_lines_cap", ctypes.c_int), ("slide_tiles", ctypes.c_int),
+        ("fft_lines_cap", ctypes.c_int), ("slide_tiles", ctypes.c_int), ("block_cols", ctypes.c_int),
     ]
 
 
@@ -75,6 +75,7 @@ SIGNATURES = {
     "nfl_plan_autotune": (_I, [_P, ctypes.POINTER(_D)]),
     "nfl_plan_set_profiling": (_I, [_P, _I]),
     "nfl_plan_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
+    "nfl_plan_kernels": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
     "nfl_plan_inject_fault": (_I, [_P, _I]),
     "nfl_status_string": (ctypes.c_char_p, [_I]),
@@ -195,6 +196,12 @@ class Plan:
     def inject_fault(self, kind):
         """Failure-detection test hook (nfl_plan_inject_fault)."""
         _check(_lib().nfl_plan_inject_fault(self._h, int(kind)), "nfl_plan_inject_fault")
+
+    def kernels(self, nrhs=1):
+        """Kernel launches one product of nrhs columns makes (nfl_plan_kernels)."""
+        k = ctypes.c_int(0)
+        _check(_lib().nfl_plan_kernels(self._h, int(nrhs), ctypes.byref(k)), "nfl_plan_kernels")
+        return k.value
 
     def kernels_per_column(self):
         k = ctypes.c_int(0)

@@ -366,11 +366,13 @@ nfl_status nfl_cg_solve_noalloc(nfl_plan *plan, double beta, const double *shift
 
 /*
  * Stage timing (tracing).  When enabled, CUDA events on the plan's stream
- * bracket the four stages of every product column: prep (grid clear and, for
- * FP32C, the fixed-point scale), spread, FFT (all passes, multiply fused) and
- * gather.  nfl_plan_stage_times synchronizes the stream, writes the
- * accumulated milliseconds per stage into ms[0..3] and the number of columns
- * timed into *columns, then clears the accumulators.  Disabled by default.
+ * bracket the four stages of every product column -- or of every block of
+ * columns that goes through the stages together: prep (grid clear, staging
+ * of x~ and the epilogue's z, for FP32C the fixed-point scale), spread, FFT
+ * (all passes, multiply fused) and gather.  nfl_plan_stage_times
+ * synchronizes the stream, writes the accumulated milliseconds per stage
+ * into ms[0..3] and the number of columns timed into *columns (a block
+ * counts its columns), then clears the accumulators.  Disabled by default.
  */
 nfl_status nfl_plan_set_profiling(nfl_plan *plan, int enable);
 nfl_status nfl_plan_stage_times(nfl_plan *plan, double *ms, int64_t *columns);

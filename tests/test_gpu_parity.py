@@ -318,3 +318,31 @@ def test_autotune_keeps_the_products(prec, m, tol):
     assert t["best_ms"] > 0.0
     ref = fastsum.NormalizedFastsum(v, 0.3, 32, m, m).apply_W(x)
     assert rel(p.apply_W(gpu(x)).cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("prec,m,tol", [("fp32c", 6, 1e-6), ("fp32", 4, 5e-6), ("bf16w", 3, 5e-6)])
+@pytest.mark.parametrize("op", ["W", "A", "Ls"])
+def test_block_products_equal_column_products(prec, m, tol, op):
+    """Block products (several columns per launch, each stage) against the same
+    columns one at a time and the oracle: 11 columns = a block of 8 and one of 3."""
+    v = _cloud("clusters", 5000, 3, seed=90 + m)
+    p = Plan(gpu(v), 0.3, 32, m, m, -1.0, prec)
+    inf = p.info()
+    assert inf["block_cols"] == 8
+    assert p.kernels(11) == 2 * p.kernels_per_column()
+    X = np.random.default_rng(91).standard_normal((5000, 11))
+    Xg = gpu(X)
+    fn = getattr(p, "apply_" + op)
+    Y = fn(Xg).cpu().numpy()
+    for c in (0, 5, 7, 8, 10):
+        yc = fn(gpu(X[:, c])).cpu().numpy()
+        # L_s x = x - A x: compare the A x parts
+        ref = (X[:, c] - yc) if op == "Ls" else yc
+        got = (X[:, c] - Y[:, c]) if op == "Ls" else Y[:, c]
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
+    o = fastsum.NormalizedFastsum(v, 0.3, 32, m, m, taps="bf16" if prec == "bf16w" else "fp64")
+    r = getattr(o, "apply_" + op)(X[:, 9])
+    got = Y[:, 9]
+    if op == "Ls":
+        r, got = X[:, 9] - r, X[:, 9] - got
+    assert np.linalg.norm(got - r) / np.linalg.norm(r) < max(tol, 2e-6)

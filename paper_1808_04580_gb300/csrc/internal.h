@@ -91,7 +91,7 @@ struct Plan {
 
     // FFT data
     int K[3] = {1, 1, 1};       // kept frequencies per axis (R2C axis N/2+1, others N+1)
-    // per-column buffers below hold `cols` columns (1 until a block product needs more):
+    // per-column buffers below hold `cols` = block_cols columns (sized at plan creation):
     // grid, bufA, bufB, g with column strides box_elems, bufA_elems, bufB_elems, box_elems;
     // xsort, xsorted with stride n; column c's FP32C scale sum |x~| at scratch[c]
     int cols = 1;
@@ -164,8 +164,8 @@ BatchStreams *batch_streams();
 // number of kernels one column launches
 int kernels_per_column(const Plan &P);
 
-// block products: nc <= kBlockCols columns through each stage in one launch (3-D
-// warp spread + tensor-core gather only); the buffers grow to nc columns first
+// block products: nc <= block_cols columns through each stage in one launch (3-D
+// warp spread + tensor-core gather only); the buffers hold block_cols columns
 bool block_path_available(const Plan &P);
 nfl_status ensure_columns(Plan &P, int nc);
 

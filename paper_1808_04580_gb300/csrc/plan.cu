@@ -239,28 +239,8 @@ static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2
     return s;
 }
 
-// Grow the per-column buffers to nc columns (contents are not kept).
-nfl_status ensure_columns(Plan &P, int nc) {
-    if (nc <= P.cols) return NFL_OK;
-    if (cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
-    const bool fd = fft_is_double(P.prec);
-    const size_t real_sz = fd ? 8 : 4, cplx_sz = 2 * real_sz;
-    const size_t grid_sz = P.prec == NFL_PREC_FP32 ? 4 : 8;
-    void *grid = nullptr, *bufA = nullptr, *bufB = nullptr, *g = nullptr, *xsort = nullptr;
-    double *xsorted = nullptr;
-    if (cudaMalloc(&grid, P.box_elems * grid_sz * nc) != cudaSuccess ||
-        cudaMalloc(&bufA, P.bufA_elems * cplx_sz * nc) != cudaSuccess ||
-        cudaMalloc(&bufB, P.bufB_elems * cplx_sz * nc) != cudaSuccess ||
-        cudaMalloc(&g, P.box_elems * real_sz * nc) != cudaSuccess || cudaMalloc(&xsort, P.n * 8 * nc) != cudaSuccess ||
-        cudaMalloc(&xsorted, P.n * 8 * nc) != cudaSuccess) {
-        cudaFree(grid); cudaFree(bufA); cudaFree(bufB); cudaFree(g); cudaFree(xsort); cudaFree(xsorted);
-        return NFL_ERR_OUT_OF_MEMORY;
-    }
-    cudaFree(P.grid); cudaFree(P.bufA); cudaFree(P.bufB); cudaFree(P.g); cudaFree(P.xsort); cudaFree(P.xsorted);
-    P.grid = grid; P.bufA = bufA; P.bufB = bufB; P.g = g; P.xsort = xsort; P.xsorted = xsorted;
-    P.cols = nc;
-    return NFL_OK;
-}
+// The per-column buffers hold P.cols = block_cols columns from plan creation on.
+nfl_status ensure_columns(Plan &P, int nc) { return nc <= P.cols ? NFL_OK : NFL_ERR_INVALID_ARG; }
 
 nfl_status rebuild_spread_items(Plan &P) {
     std::vector<WorkItem> s = slide_items(P.tile_items, P.ntile[P.d - 1], P.slide_tiles);
@@ -855,9 +835,21 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
         const int w = int(budget / per_col);
         P->block_cols = w < 1 ? 1 : (w > kBlockCols ? kBlockCols : w);
     }
-    if (cudaMalloc(&P->grid, P->box_elems * grid_sz) != cudaSuccess ||
-        cudaMalloc(&P->bufA, bufA * cplx_sz) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz) != cudaSuccess ||
-        cudaMalloc(&P->g, P->box_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
+    // every per-column buffer for block_cols columns, now: products never reallocate,
+    // so a captured CUDA graph stays valid whatever the plan computes later
+    const int64_t bc = P->block_cols;
+    P->cols = (int)bc;
+    if (bc > 1) {
+        cudaFree(P->xsort);
+        cudaFree(P->xsorted);
+        P->xsort = nullptr;
+        P->xsorted = nullptr;
+        if (cudaMalloc(&P->xsort, n * 8 * bc) != cudaSuccess || cudaMalloc(&P->xsorted, n * 8 * bc) != cudaSuccess)
+            return NFL_ERR_OUT_OF_MEMORY;
+    }
+    if (cudaMalloc(&P->grid, P->box_elems * grid_sz * bc) != cudaSuccess ||
+        cudaMalloc(&P->bufA, bufA * cplx_sz * bc) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz * bc) != cudaSuccess ||
+        cudaMalloc(&P->g, P->box_elems * real_sz * bc) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
         cudaMalloc(&P->twiddle, (P->ngrid / 2) * cplx_sz) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
     {

@@ -99,3 +99,27 @@ def test_batched_256_uneven_graphs_full_size():
         w = plans[g].apply_W(x).cpu().numpy()
         ref = direct.rows_W(clouds[g], 0.5, x.cpu().numpy(), rows_g)
         assert np.linalg.norm(w[rows_g] - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_captured_graph_survives_block_products():
+    """A one-column product captured into a CUDA graph still replays correctly after
+    block products on the same plan (the plan never reallocates its buffers)."""
+    v = workloads.gaussian_mixture(20000, seed=61)
+    p = Plan(gpu(v), 0.5, 32, 4, 4, -1.0, "fp32c")
+    assert p.info()["block_cols"] > 1
+    x = gpu(workloads.rhs(20000, seed=62))
+    y = torch.empty_like(x)
+    p.apply_Ls(x, out=y)                                  # warm-up before capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        p.apply_Ls(x, out=y)
+    ref = p.apply_Ls(x).clone()
+    X8 = gpu(workloads.rhs(20000, nrhs=8, seed=63))
+    Y8 = p.apply_Ls(X8)                                   # block product
+    y.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(torch.linalg.norm((x - y) - (x - ref)) / torch.linalg.norm(x - ref)) < 1e-6
+    assert float(torch.linalg.norm((X8[:, 3] - Y8[:, 3]) - (X8[:, 3] - p.apply_Ls(X8[:, 3].contiguous())))) \
+        < 1e-6 * float(torch.linalg.norm(X8[:, 3] - Y8[:, 3]))

@@ -77,7 +77,7 @@ enum {
  *   FP64  : everything in FP64.
  *   FP32  : window weights, spreading grid, FFT and interpolation in FP32.
  *   FP32C : FP32 window weights and products; FP32 partial sums over at
- *           most 512 nodes are carried into 64-bit fixed point and
+ *           most 2048 nodes are carried into 64-bit fixed point and
  *           accumulated exactly from there on; FFT in FP32; interpolation
  *           on the tensor cores with FP32-accurate (three-term TF32) products.
  *           Results may vary in the last FP32 bits from run to run where a

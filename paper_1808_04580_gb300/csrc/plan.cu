@@ -18,7 +18,7 @@
 
 namespace nfl {
 
-static constexpr int kChunk = 2048;  // nodes per work item
+static constexpr int kChunk = 8192;  // nodes per work item
 
 // ---------------------------------------------------------------- reductions
 __global__ void bbox_partials(const double *v, int64_t n, int d, double *part) {

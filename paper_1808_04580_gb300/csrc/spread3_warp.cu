@@ -26,11 +26,11 @@
 // At the end of the chunk the CTA sums the NG tile copies; FP32 adds each
 // non-zero sum to the global grid with an FP32 atomic, FP32C converts it to
 // 64-bit fixed point (scale 2^k from sum |x~|, so nothing can overflow) and
-// adds it with an integer atomic.  So FP32C sums at most 2048 / NG nodes of a
-// tile position in FP32 (512 for NG = 4) before the exact integer part.
+// adds it with an integer atomic.  So FP32C sums at most 8192 / NG nodes of a
+// tile position in FP32 (2048 for NG = 4) before the exact integer part.
 //
 // A work item may also be a run of tiles that follow each other along axis 2
-// (at most 2048 nodes together).  The tile copies then slide along the run:
+// (at most 8192 nodes together).  The tile copies then slide along the run:
 // axis 2 of a copy is addressed circularly (slot = (q2 + woff) mod PA), and
 // between two tiles the CTA merges only the TE planes q2 < TE that the next
 // tile's window does not cover, clears them (they become its last TE planes)

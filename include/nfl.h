@@ -102,7 +102,8 @@ typedef struct {
     double center[3];     /* bounding-box midpoint subtracted before scaling   */
     int box[3];           /* extent of the active oversampled grid per axis    */
     int64_t tiles;        /* non-empty spreading tiles                         */
-    int64_t work_items;   /* tile chunks processed by the spread/gather grids  */
+    int64_t work_items;   /* tile chunks (<= 8192 nodes) of the gather; the 3-D
+                             warp spread takes runs of tiles built from them  */
     double min_degree;    /* min_j d_E,j                                       */
     double max_degree;    /* max_j d_E,j                                       */
     int degree_ok;        /* 1 if min_degree > 0 (A, L_s and solvers usable)  */

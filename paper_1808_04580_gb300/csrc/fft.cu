@@ -137,12 +137,18 @@ __device__ C *stockham(C *x, C *y, int nl, int n, int logn, const C *tw, bool in
     return x;
 }
 
+// R2C and C2R transform two real lines as one complex line (PAIR): forward,
+// z = a + i b gives A_k = (Z_k + conj Z_{n-k}) / 2 and B_k = (Z_k - conj Z_{n-k}) / 2i;
+// inverse, Z = A + i B over the Hermitian extension of both half spectra gives
+// a = Re z, b = Im z.
 template <typename T, typename TIN, int MODE>
 __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     using C = typename Cplx<T>::type;
+    constexpr bool PAIR = (MODE == P_FWD_R2C || MODE == P_INV_C2R);
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NL = PAIR ? (a.BB + 1) / 2 : a.BB;     // complex lines in shared memory
     C *bx = reinterpret_cast<C *>(smem_raw);
-    C *by = bx + a.BB * a.n;
+    C *by = bx + NL * a.n;
     const int col = blockIdx.z;
     const int ai = blockIdx.y;
     const int b0 = blockIdx.x * a.BB;
@@ -150,14 +156,33 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     const int n = a.n, N = a.N;
     const C *tw = reinterpret_cast<const C *>(a.tw);
 
-    for (int e = threadIdx.x; e < a.BB * n; e += blockDim.x) bx[e] = C{T(0), T(0)};
+    for (int e = threadIdx.x; e < NL * n; e += blockDim.x) bx[e] = C{T(0), T(0)};
     __syncthreads();
 
     T in_scale = T(1);
     if (std::is_same<TIN, long long>::value) in_scale = T(fixed_point_unscale(a.abs_sum[col]));
 
     // load
-    for (int e = threadIdx.x; e < nb * a.Lin; e += blockDim.x) {
+    if (MODE == P_INV_C2R) {
+        // line pairs (2p, 2p + 1): Z_c = A_c + i B_c and Z_{n-c} = conj A_c + i conj B_c
+        // (c = 1 .. Lin - 1 < n / 2); the DC terms are real
+        const int np = (nb + 1) / 2;
+        const C *in = reinterpret_cast<const C *>(a.in);
+        for (int e = threadIdx.x; e < np * a.Lin; e += blockDim.x) {
+            const int pp = (int)__umulhi((unsigned)e, a.lin_magic);
+            const int c = e - pp * a.Lin;
+            const int64_t src = col * a.in_cstride + ai * a.sA + (int64_t)(b0 + 2 * pp) * a.sB + c;
+            const C A = in[src];
+            const C B = 2 * pp + 1 < nb ? in[src + a.sB] : C{T(0), T(0)};
+            if (c == 0) {
+                bx[pp * n] = C{A.x, B.x};
+            } else {
+                bx[pp * n + c] = C{A.x - B.y, A.y + B.x};
+                bx[pp * n + (n - c)] = C{A.x + B.y, B.x - A.y};
+            }
+        }
+    }
+    for (int e = threadIdx.x; e < (MODE == P_INV_C2R ? 0 : nb * a.Lin); e += blockDim.x) {
         const int bb = (int)__umulhi((unsigned)e, a.lin_magic);
         const int c = e - bb * a.Lin;
         const int64_t src = col * a.in_cstride + ai * a.sA + (int64_t)(b0 + bb) * a.sB + c;
@@ -171,9 +196,9 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
         if (MODE == P_INV_C2C) {
             const int k = c - N / 2;
             bx[bb * n + ((k + n) & (n - 1))] = v;
-        } else if (MODE == P_INV_C2R) {
-            bx[bb * n + c] = v;
-            if (c >= 1) bx[bb * n + (n - c)] = C{v.x, -v.y};
+        } else if (MODE == P_FWD_R2C) {
+            // line bb is the real (even bb) or imaginary (odd bb) part of pair line bb / 2
+            reinterpret_cast<T *>(&bx[(bb >> 1) * n + c])[bb & 1] = v.x;
         } else {
             bx[bb * n + c] = v;
         }
@@ -181,7 +206,7 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     __syncthreads();
 
     const bool inverse = (MODE == P_INV_C2C || MODE == P_INV_C2R);
-    C *res = stockham<C>(bx, by, a.BB, n, a.logn, tw, inverse);
+    C *res = stockham<C>(bx, by, NL, n, a.logn, tw, inverse);
 
     if (MODE == P_FUSED) {
         const T *M = reinterpret_cast<const T *>(a.M);
@@ -204,7 +229,7 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
     }
 
     // store, b fastest
-    const unsigned nb_magic = 0xFFFFFFFFu / (unsigned)nb + 1u;   // e / nb = umulhi(e, nb_magic), nb <= 16
+    const unsigned nb_magic = 0xFFFFFFFFu / (unsigned)nb + 1u;   // e / nb = umulhi(e, nb_magic), nb <= 32
     for (int e = threadIdx.x; e < nb * a.Lout; e += blockDim.x) {
         const int cc = nb == 1 ? e : (int)__umulhi((unsigned)e, nb_magic);
         const int bb = e - cc * nb;
@@ -212,10 +237,20 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
         if (MODE == P_FWD_R2C) idx = cc;
         else if (MODE == P_FWD_C2C) idx = (cc - N / 2 + n) & (n - 1);
         else idx = cc;
-        const C v = res[bb * n + idx];
         const int64_t dst = col * a.out_cstride + cc * a.oC + (int64_t)ai * a.oA + b0 + bb;
-        if (MODE == P_INV_C2R || (MODE == P_FUSED && a.real_out)) reinterpret_cast<T *>(a.out)[dst] = v.x;
-        else reinterpret_cast<C *>(a.out)[dst] = v;
+        if (MODE == P_FWD_R2C) {
+            const C zk = res[(bb >> 1) * n + idx], zm = res[(bb >> 1) * n + ((n - idx) & (n - 1))];
+            const C v = (bb & 1) == 0 ? C{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)}
+                                      : C{T(0.5) * (zk.y + zm.y), T(0.5) * (zm.x - zk.x)};
+            reinterpret_cast<C *>(a.out)[dst] = v;
+        } else if (MODE == P_INV_C2R) {
+            const C v = res[(bb >> 1) * n + idx];
+            reinterpret_cast<T *>(a.out)[dst] = (bb & 1) == 0 ? v.x : v.y;
+        } else {
+            const C v = res[bb * n + idx];
+            if (MODE == P_FUSED && a.real_out) reinterpret_cast<T *>(a.out)[dst] = v.x;
+            else reinterpret_cast<C *>(a.out)[dst] = v;
+        }
     }
 }
 
@@ -225,12 +260,14 @@ static cudaError_t run_pass(Plan &P, PassArgs a, int nc) {
     // few lines per CTA and one radix-4 butterfly per thread and stage: small CTAs,
     // many of them resident per SM to hide the global-memory latency of load and store
     const int cap = P.fft_cap;
-    int BB = cap / a.n;
-    BB = BB > 16 ? 16 : (BB < 1 ? 1 : BB);
+    constexpr bool PAIR = (MODE == P_FWD_R2C || MODE == P_INV_C2R);
+    int NL = cap / a.n;                        // complex lines per CTA
+    NL = NL > 16 ? 16 : (NL < 1 ? 1 : NL);
+    const int BB = PAIR ? 2 * NL : NL;          // real (PAIR) or complex lines per CTA
     a.BB = BB;
     a.lin_magic = (unsigned)((0x100000000ull + (unsigned)a.Lin - 1) / (unsigned)a.Lin);
-    const int smem = 2 * BB * a.n * (int)sizeof(C);
-    int threads = BB * a.n / 4;
+    const int smem = 2 * NL * a.n * (int)sizeof(C);
+    int threads = NL * a.n / 4;
     threads = threads < 64 ? 64 : (threads > 256 ? 256 : threads);
     NFL_CUDA_TRY(cudaFuncSetAttribute(fft_pass<T, TIN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid((a.nB + BB - 1) / BB, a.nA, nc);

@@ -25,7 +25,8 @@ def test_product_path_never_imports_the_oracle():
 def test_oracle_never_imports_the_product_path():
     for f in _files(ORACLE, (".py",)):
         text = open(f).read()
-        assert "paper_1808_04580_gb300" not in text, f
+        assert not re.search(r"^\s*(import|from)\s+paper_1808_04580_gb300\b", text, re.M), f
+        assert "libnfl" not in text, f          # nor loads the product's library
 
 
 def test_sources_include_nothing_across():

@@ -181,10 +181,11 @@ nfl_status nfl_degree(const nfl_plan *plan, double *d);
  * On the 3-D FP32 / FP32C / BF16W path with m in {2, 3, 4, 6} the columns go
  * through each stage in blocks of nfl_info.block_cols per launch: as many
  * (up to 8) as keep a column's staged values, grids and FFT buffers within
- * half of L2 together, 1 for large plans (the plan allocates its buffers
- * for that width when it is created and never reallocates them, so
- * products captured into a CUDA graph stay valid); elsewhere one column at
- * a time.  The same holds for nfl_apply_A and nfl_apply_Ls.
+ * half of L2 together, 1 for large plans; elsewhere one column at a time.
+ * The first block product allocates the plan's block buffers (make it
+ * before capturing products into a CUDA graph); no buffer of the plan is
+ * ever reallocated, so captured products stay valid.  The same holds for
+ * nfl_apply_A and nfl_apply_Ls.
  */
 nfl_status nfl_apply_W(nfl_plan *plan, const double *x, int64_t ldx,
                        double *y, int64_t ldy, int nrhs);

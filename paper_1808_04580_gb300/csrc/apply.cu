@@ -50,10 +50,8 @@ nfl_status run_column(Plan &P, int op, const double *x, double *y) {
 bool block_path_available(const Plan &P) { return spread_warp_available(P) && gather_tc_available(P); }
 
 // nc <= kBlockCols columns (x + c ldx -> y + c ldy) through each stage in one launch
-static nfl_status run_block(Plan &P, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nc) {
+static nfl_status run_block_stages(Plan &P, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nc) {
     const bool scale = (op == OP_A || op == OP_LS);
-    const nfl_status st = ensure_columns(P, nc);
-    if (st != NFL_OK) return st;
     NFL_STATUS_TRY(mark(P, 0));
     NFL_STATUS_TRY(prepare_spread(P, op, x, ldx, nc, false, scale));
     NFL_STATUS_TRY(mark(P, 1));
@@ -64,6 +62,20 @@ static nfl_status run_block(Plan &P, int op, const double *x, int64_t ldx, doubl
     NFL_STATUS_TRY(launch_gather_tc(P, op, x, y, ldy, nc));
     NFL_STATUS_TRY(mark(P, 4, nc));
     return NFL_OK;
+}
+
+static nfl_status run_block(Plan &P, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nc) {
+    const nfl_status st = ensure_columns(P, nc);
+    if (st != NFL_OK) return st;
+    // the launches of this block take the block buffers (kernel arguments are copied at
+    // launch, so the one-column pointers are restored right after)
+    const BlockBuffers one{P.grid, P.bufA, P.bufB, P.g, P.xsort, P.xsorted};
+    P.grid = P.blk.grid; P.bufA = P.blk.bufA; P.bufB = P.blk.bufB; P.g = P.blk.g;
+    P.xsort = P.blk.xsort; P.xsorted = P.blk.xsorted;
+    const nfl_status rs = run_block_stages(P, op, x, ldx, y, ldy, nc);
+    P.grid = one.grid; P.bufA = one.bufA; P.bufB = one.bufB; P.g = one.g;
+    P.xsort = one.xsort; P.xsorted = one.xsorted;
+    return rs;
 }
 
 static nfl_status apply(nfl_plan *plan, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {

@@ -37,6 +37,12 @@ constexpr int kHostSlots = 3;   // device staging slots per direction for host-b
 constexpr int kBlockCols = 8;   // columns a block product takes through each stage in one launch
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 
+// Per-column buffers of block products (see Plan::blk).
+struct BlockBuffers {
+    void *grid = nullptr, *bufA = nullptr, *bufB = nullptr, *g = nullptr, *xsort = nullptr;
+    double *xsorted = nullptr;
+};
+
 struct Plan {
     // problem
     int64_t n = 0;
@@ -91,10 +97,11 @@ struct Plan {
 
     // FFT data
     int K[3] = {1, 1, 1};       // kept frequencies per axis (R2C axis N/2+1, others N+1)
-    // per-column buffers below hold `cols` = block_cols columns (sized at plan creation):
-    // grid, bufA, bufB, g with column strides box_elems, bufA_elems, bufB_elems, box_elems;
-    // xsort, xsorted with stride n; column c's FP32C scale sum |x~| at scratch[c]
-    int cols = 1;
+    // one-column buffers: grid, bufA, bufB, g, xsort, xsorted (below); block products use
+    // blk, the same buffers for block_cols columns (column strides box_elems, bufA_elems,
+    // bufB_elems, box_elems and n), made on the first block product; column c's FP32C
+    // scale sum |x~| at scratch[c]
+    BlockBuffers blk;
     int block_cols = 1;                 // columns per block product (1: column by column)
     int l2_bytes = 0;
     int64_t bufA_elems = 0, bufB_elems = 0;

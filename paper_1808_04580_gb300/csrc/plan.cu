@@ -239,8 +239,30 @@ static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2
     return s;
 }
 
-// The per-column buffers hold P.cols = block_cols columns from plan creation on.
-nfl_status ensure_columns(Plan &P, int nc) { return nc <= P.cols ? NFL_OK : NFL_ERR_INVALID_ARG; }
+// The block buffers (block_cols columns of staged values, grids and FFT buffers),
+// allocated on the first block product and kept until the plan is destroyed: the
+// one-column buffers are never touched, and neither set is ever reallocated, so
+// products captured into a CUDA graph stay valid.
+nfl_status ensure_columns(Plan &P, int nc) {
+    if (nc > P.block_cols) return NFL_ERR_INVALID_ARG;
+    if (P.blk.grid) return NFL_OK;
+    const int64_t bc = P.block_cols;
+    const bool fd = fft_is_double(P.prec);
+    const size_t real_sz = fd ? 8 : 4, cplx_sz = 2 * real_sz;
+    const size_t grid_sz = P.prec == NFL_PREC_FP32 ? 4 : 8;
+    if (cudaMalloc(&P.blk.xsort, P.n * 8 * bc) != cudaSuccess ||
+        cudaMalloc(&P.blk.xsorted, P.n * 8 * bc) != cudaSuccess ||
+        cudaMalloc(&P.blk.bufA, P.bufA_elems * cplx_sz * bc) != cudaSuccess ||
+        cudaMalloc(&P.blk.bufB, P.bufB_elems * cplx_sz * bc) != cudaSuccess ||
+        cudaMalloc(&P.blk.g, P.box_elems * real_sz * bc) != cudaSuccess ||
+        cudaMalloc(&P.blk.grid, P.box_elems * grid_sz * bc) != cudaSuccess) {
+        cudaFree(P.blk.xsort); cudaFree(P.blk.xsorted); cudaFree(P.blk.bufA);
+        cudaFree(P.blk.bufB); cudaFree(P.blk.g); cudaFree(P.blk.grid);
+        P.blk = BlockBuffers{};
+        return NFL_ERR_OUT_OF_MEMORY;
+    }
+    return NFL_OK;
+}
 
 nfl_status rebuild_spread_items(Plan &P) {
     std::vector<WorkItem> s = slide_items(P.tile_items, P.ntile[P.d - 1], P.slide_tiles);
@@ -584,6 +606,8 @@ static void free_plan(Plan *P) {
     if (P->d2h) cudaStreamDestroy(P->d2h);
     cudaFree(P->host_stage);
     cudaFree(P->items);
+    cudaFree(P->blk.xsort); cudaFree(P->blk.xsorted); cudaFree(P->blk.bufA);
+    cudaFree(P->blk.bufB); cudaFree(P->blk.g); cudaFree(P->blk.grid);
     cudaFree(P->sitems);
     cudaFree(P->tile_start);
     cudaFree(P->pts);
@@ -835,21 +859,9 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
         const int w = int(budget / per_col);
         P->block_cols = w < 1 ? 1 : (w > kBlockCols ? kBlockCols : w);
     }
-    // every per-column buffer for block_cols columns, now: products never reallocate,
-    // so a captured CUDA graph stays valid whatever the plan computes later
-    const int64_t bc = P->block_cols;
-    P->cols = (int)bc;
-    if (bc > 1) {
-        cudaFree(P->xsort);
-        cudaFree(P->xsorted);
-        P->xsort = nullptr;
-        P->xsorted = nullptr;
-        if (cudaMalloc(&P->xsort, n * 8 * bc) != cudaSuccess || cudaMalloc(&P->xsorted, n * 8 * bc) != cudaSuccess)
-            return NFL_ERR_OUT_OF_MEMORY;
-    }
-    if (cudaMalloc(&P->grid, P->box_elems * grid_sz * bc) != cudaSuccess ||
-        cudaMalloc(&P->bufA, bufA * cplx_sz * bc) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz * bc) != cudaSuccess ||
-        cudaMalloc(&P->g, P->box_elems * real_sz * bc) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
+    if (cudaMalloc(&P->grid, P->box_elems * grid_sz) != cudaSuccess ||
+        cudaMalloc(&P->bufA, bufA * cplx_sz) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz) != cudaSuccess ||
+        cudaMalloc(&P->g, P->box_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
         cudaMalloc(&P->twiddle, (P->ngrid / 2) * cplx_sz) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
     {

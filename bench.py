@@ -46,6 +46,16 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 
 
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+PEAKS = _peaks()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,7 +232,7 @@ def main():
         return
     import numpy as np
     import torch
-    from paper_1808_04580_gb300 import Plan, workloads
+    from paper_1808_04580_gb300 import Plan, fma_rate, workloads
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -232,6 +242,13 @@ def main():
     X = X.reshape(n, nrhs)
     vg = torch.from_numpy(v).to(dev)
     xg = torch.from_numpy(np.asfortranarray(X)).to(dev)
+    # measured multiply-add rates of this GPU (the ALU roofline's denominator)
+    rates = {}
+    for kind in ("fp32", "fp32x2", "fp64"):
+        try:
+            rates[kind] = fma_rate(kind)[0]
+        except Exception:  # a refused measurement leaves the derived peak
+            rates[kind] = None
     plan = Plan(vg, CFG["sigma"], CFG["N"], CFG["m"], CFG["p"], -1.0, args.precision)
     tuned = plan.autotune() if not args.no_autotune else None   # launch parameters, outside the timed region
     info = plan.info()
@@ -272,6 +289,7 @@ def main():
 
     # dominant kernel and its roofline (ALU: one multiply-add per window tap)
     taps = (2 * CFG["m"]) ** 3
+    box_elems = int(np.prod(info["box"]))
     spread_ms = stages["spread"] / max(1, stages["columns"])
     gather_ms = stages["gather"] / max(1, stages["columns"])
     fft_ms = stages["fft"] / max(1, stages["columns"])
@@ -281,19 +299,50 @@ def main():
     dom_ms = max(spread_ms, gather_ms) * cpl
     flops = 2.0 * taps * n * cpl
     achieved = flops / (dom_ms / 1000.0) / 1e12
-    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # the measured FP32 multiply-add rate (the faster of scalar and packed fma), else the
+    # unit-count figure 152 SMs x 128 lanes x 2 flop x 2070 MHz
+    if rates.get("fp32") or rates.get("fp32x2"):
+        peak = max(rates.get("fp32") or 0.0, rates.get("fp32x2") or 0.0) / 1e12
+        peak_note = ("measured: nfl_fma_rate, max of fma.rn.f32 (%.1f TFLOP/s) and fma.rn.f32x2 (%.1f TFLOP/s) "
+                     "register-resident chains on all SMs, CUDA events" % ((rates.get("fp32") or 0.0) / 1e12,
+                                                                       (rates.get("fp32x2") or 0.0) / 1e12))
+    else:
+        peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak_note = "derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no measured FP32 rate)"
     kname, src, summary = (("spread3_warp", "spread3_warp.cu", "spread3_warp_ball10M.md") if dom == "spread"
                            else ("gather3_tc", "gather_tc.cu", "gather3_tc_ball10M.md"))
     kernel_file = os.path.join(ROOT, "paper_1808_04580_gb300", "csrc", src)
     traffic = profiled_traffic(summary, kernel_file) if n == 10_000_000 else None
     if traffic is not None:
         traffic *= cpl                # the profile is of a one-column launch
-    hbm_bytes = n * (16 + 8 + 4 + 8) * cpl  # node record, x, perm, dinv read once per column
+    # algorithmic HBM bytes per column: the spread reads the 16-byte node record and the
+    # FP32 x~ and adds into the 8-byte fixed-point grid of the active box; the gather reads
+    # the record, perm, the staged z, D^{-1/2} and the FP32 interpolation grid, writes y
+    spread_bytes = n * (16 + 4) + box_elems * 8
+    gather_bytes = n * (16 + 4 + 8 + 8 + 8) + box_elems * 4
+    dom_bytes = (spread_bytes if dom == "spread" else gather_bytes) * cpl
+    hbm_peak = float(PEAKS.get("hbm_gbs") or 6768.0)
+    peak_units = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_from_unit_counts": peak_units,
                 "traffic": traffic, "kernel": kname,
                 "flops_per_launch": flops, "ms_per_launch": dom_ms, "columns_per_launch": cpl,
-                "hbm_achieved_gbs": hbm_bytes / (dom_ms / 1000.0) / 1e9,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no measured FP32 peak)"}
+                "algorithmic_bytes_per_launch": dom_bytes,
+                "hbm_achieved_gbs": dom_bytes / (dom_ms / 1000.0) / 1e9,
+                "peak_note": peak_note}
+    # spread + gather together against both ceilings: the HBM fraction of their algorithmic
+    # bytes is far below 50 % because the taps, not the bytes, bound them
+    sg_ms = spread_ms + gather_ms
+    spread_gather = {"ms_per_column": sg_ms, "algorithmic_bytes_per_column": spread_bytes + gather_bytes,
+                     "hbm_gbs": (spread_bytes + gather_bytes) / (sg_ms / 1000.0) / 1e9,
+                     "hbm_frac": (spread_bytes + gather_bytes) / (sg_ms / 1000.0) / 1e9 / hbm_peak,
+                     "hbm_peak_gbs": hbm_peak,
+                     "alu_tflops": 2 * 2.0 * taps * n / (sg_ms / 1000.0) / 1e12,
+                     "alu_frac": 2 * 2.0 * taps * n / (sg_ms / 1000.0) / 1e12 / peak,
+                     "hbm_target_0.5_met": bool((spread_bytes + gather_bytes) / (sg_ms / 1000.0) / 1e9 / hbm_peak >= 0.5),
+                     "note": "arithmetic-bound: the taps need %.2f ms per column at the FP32 peak, the bytes %.3f ms "
+                             "at the HBM peak" % (2 * 2.0 * taps * n / (peak * 1e12) * 1e3,
+                                                  (spread_bytes + gather_bytes) / (hbm_peak * 1e9) * 1e3)}
 
     # end to end through the C ABI with page-locked host buffers (nfl_apply_host:
     # each step's columns go to the device and back inside the timed region)
@@ -401,6 +450,8 @@ def main():
             "rel_err_W": err,
             "precision_sweep": sweep,
             "roofline": roofline,
+            "spread_gather": spread_gather,
+            "fma_rates_tflops": {k: (v / 1e12 if v else None) for k, v in rates.items()},
             "cpu_baseline": cpu_baseline,
             "e2e": e2e,
             "gpu_launches": plan.kernels(nrhs) * args.steps,

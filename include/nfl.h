@@ -23,6 +23,9 @@
  *   - Work is ordered on the plan's stream.  Apply calls do not synchronize
  *     the host; plan creation and the solvers do (they read scalars back).
  *   - Inputs and outputs must not alias.
+ *   - A plan is not thread-safe: calls on one plan must not run concurrently
+ *     from several host threads (a block product switches the plan's
+ *     buffer set for the duration of the call).
  *   - Every call returns an nfl_status.  Errors never trap on the device:
  *     arguments are checked on the host, numerical failures are reported by
  *     status, CUDA errors map to NFL_ERR_CUDA.  After NFL_ERR_CUDA the plan
@@ -183,7 +186,8 @@ nfl_status nfl_degree(const nfl_plan *plan, double *d);
  * (up to 8) as keep a column's staged values, grids and FFT buffers within
  * half of L2 together, 1 for large plans; elsewhere one column at a time.
  * The first block product allocates the plan's block buffers (make it
- * before capturing products into a CUDA graph); no buffer of the plan is
+ * before capturing products into a CUDA graph: under capture it returns
+ * NFL_ERR_INVALID_ARG instead of allocating); no buffer of the plan is
  * ever reallocated, so captured products stay valid.  The same holds for
  * nfl_apply_A and nfl_apply_Ls.
  */
@@ -290,6 +294,39 @@ nfl_status nfl_cg_solve(nfl_plan *plan, double beta, const double *shift,
                         int *iters, double *relres);
 
 /*
+ * nfl_cg_solve to FP64 accuracy with nearly all products in a mixed form:
+ * mixed-precision iterative refinement (the refinement pass of the
+ * compensated form; Sec. 4 notes that Krylov methods tolerate inexact
+ * products, Sec. 6.2.2 gives the system).  With A_64 the operator
+ * beta L_s + diag(s) of `plan` (normally FP64) and A_in that of `inner`
+ * (normally the FP32C form of the same nodes and parameters):
+ *   r_k = f - A_64 u_k;  stop when ||r_k|| <= tol ||f||;
+ *   A_in c_k = r_k by CG from c_k = 0 to ||r_k - A_in c_k|| <= inner_tol ||r_k||;
+ *   u_{k+1} = u_k + c_k.
+ * Each outer step costs one product of `plan`; the inner CG steps use
+ * `inner`.  The answer is that of nfl_cg_solve on `plan`.
+ *
+ *   plan, inner  plans created from the same nodes with the same kernel and
+ *                sigma (checked through n, d, kernel, sigma and the nodes'
+ *                bounding-box centre; NFL_ERR_INVALID_ARG otherwise); N, m,
+ *                p and the precision may differ.  inner runs on plan's stream
+ *                for the call.
+ *   beta, shift, f, u, tol   as in nfl_cg_solve (u: initial guess in, solution out).
+ *   inner_tol    relative residual of each correction solve, 0 < inner_tol < 1.
+ *   maxit        most CG steps of one correction solve (a correction that
+ *                stops at maxit is still applied).
+ *   max_outer    most refinement steps (FP64 residuals: max_outer + 1).
+ *   iters        host (may be NULL): inner CG steps in total.
+ *   outer        host (may be NULL): refinement steps taken.
+ *   relres       host (may be NULL): final ||r|| / ||f|| with plan's products.
+ * Returns NFL_ERR_NOT_CONVERGED when max_outer steps do not reach tol.
+ * Synchronizes the stream; allocates 6 n FP64 of device scratch.
+ */
+nfl_status nfl_cg_solve_refined(nfl_plan *plan, nfl_plan *inner, double beta, const double *shift,
+                                const double *f, double *u, double tol, double inner_tol, int maxit,
+                                int max_outer, int *iters, int *outer, double *relres);
+
+/*
  * Gradients of a loss l(u) through the solve of nfl_cg_solve, given the
  * forward solution u and g = dl/du (the differentiable form of the system of
  * Sec. 6.2.2).  The operator beta L_s + diag(s) is symmetric, so one more
@@ -348,19 +385,21 @@ nfl_status nfl_form_grad_nodes(nfl_plan *plan, const double *v, const double *a,
 /*
  * nfl_cg_solve without device allocation.  The paper has no counterpart:
  * this is a deployment variant of nfl_cg_solve for callers that cannot
- * call cudaMalloc / cudaFree while they solve (work captured into a CUDA
- * graph, a process whose device footprint is fixed at start-up, an
- * allocator that must not see foreign allocations).  Arguments, results and
- * status codes are those of nfl_cg_solve.
+ * call cudaMalloc / cudaFree while they solve (a process whose device
+ * footprint is fixed at start-up, an allocator that must not see foreign
+ * allocations).  Arguments, results and status codes are those of
+ * nfl_cg_solve.  Like nfl_cg_solve it synchronizes the plan's stream in
+ * every iteration to read the reductions, so it cannot be captured into a
+ * CUDA graph.
  *
  * The four work vectors and the reduction partials live in one static
  * device array of this library, sized for n <= NFL_NOALLOC_MAX_N nodes
  * (4 x 262144 + 520 doubles, about 8 MiB, held by every GPU that loads the
  * library until the process exits).  A plan with more nodes returns
  * NFL_ERR_INVALID_ARG.  The plan's device must be current; the first call
- * on a device looks up the array's device address, so make that first call
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU (other streams, plans or threads) race on it.
+ * on a device looks up the array's device address.  All calls share the
+ * array: calls that overlap on the GPU (other streams, plans or threads)
+ * race on it.
  */
 #define NFL_NOALLOC_MAX_N 262144
 nfl_status nfl_cg_solve_noalloc(nfl_plan *plan, double beta, const double *shift,
@@ -398,6 +437,23 @@ nfl_status nfl_plan_kernels_per_column(const nfl_plan *plan, int *kernels);
  * nfl_info.block_cols columns take one launch per stage on the 3-D
  * tensor-core path. */
 nfl_status nfl_plan_kernels(const nfl_plan *plan, int nrhs, int *kernels);
+
+/*
+ * Measured arithmetic rate of the current device, the denominator of the ALU
+ * rooflines of the spread and gather kernels; the paper has no counterpart.
+ * kind selects the instruction:
+ *   NFL_RATE_FP32_FMA    fma.rn.f32 (one FP32 multiply-add per lane),
+ *   NFL_RATE_FP32X2_FMA  fma.rn.f32x2 (two FP32 multiply-adds per lane, the
+ *                        packed form the spread and gather use),
+ *   NFL_RATE_FP64_FMA    fma.rn.f64.
+ * Launches register-resident chains of fused multiply-adds over all SMs
+ * (64 warps per SM) on `stream`, and returns the best of five timed launches
+ * after one untimed one (CUDA events): *flops_per_s counts 2 flop per
+ * multiply-add, *ms (host, may be NULL) the launch time.  Synchronizes the
+ * stream; allocates 1 KB of device memory for the call.
+ */
+enum { NFL_RATE_FP32_FMA = 0, NFL_RATE_FP32X2_FMA = 1, NFL_RATE_FP64_FMA = 2 };
+nfl_status nfl_fma_rate(int kind, void *stream, double *flops_per_s, double *ms);
 
 /* Human-readable name of a status code. */
 const char *nfl_status_string(int status);

@@ -3,13 +3,16 @@
 //
 // nfl_cg_solve allocates its four work vectors and its reduction partials
 // with cudaMalloc on every call.  Some callers cannot do that at solve time:
-// code that runs while a stream is being captured into a CUDA graph, code
-// under an allocator that must not see foreign allocations, or services that
-// fix their device footprint at start-up.  This entry point takes the same
-// arguments and runs the same iteration, but its scratch lives in one
-// file-scope static device array (sized for n <= NFL_NOALLOC_MAX_N), whose
-// device address is looked up once per device.  The products with L_s use
-// the plan's buffers, which were allocated when the plan was created.
+// code under an allocator that must not see foreign allocations (a caching
+// allocator that owns the device's memory), or services that fix their
+// device footprint at start-up.  This entry point takes the same arguments
+// and runs the same iteration, but its scratch lives in one file-scope
+// static device array (sized for n <= NFL_NOALLOC_MAX_N), whose device
+// address is looked up once per device.  The products with L_s use the
+// plan's buffers, which were allocated when the plan was created.  Like
+// nfl_cg_solve it reads every reduction back to the host and synchronizes
+// the plan's stream in every iteration (the host decides convergence and
+// breakdown), so it cannot run while its stream is being captured.
 //
 // The array is shared by every call in the process and keeps the previous
 // call's contents; every word the solver reads is written first in the same

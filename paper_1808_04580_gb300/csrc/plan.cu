@@ -246,6 +246,11 @@ static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2
 nfl_status ensure_columns(Plan &P, int nc) {
     if (nc > P.block_cols) return NFL_ERR_INVALID_ARG;
     if (P.blk.grid) return NFL_OK;
+    // a stream under capture refuses cudaMalloc (and the capture would be invalidated):
+    // the first block product has to come before any capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(P.stream, &cap) != cudaSuccess) return NFL_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return NFL_ERR_INVALID_ARG;
     const int64_t bc = P.block_cols;
     const bool fd = fft_is_double(P.prec);
     const size_t real_sz = fd ? 8 : 4, cplx_sz = 2 * real_sz;

@@ -12,6 +12,17 @@
 //
 // CG (Sec. 6.2.2, eq. (ssl::system)): conjugate gradients on the SPD
 // operator u -> beta L_s u + diag(s) u, stopping at ||r|| <= tol ||f||.
+//
+// Refined CG: mixed-precision iterative refinement around it.  Sec. 4 notes
+// that Krylov methods tolerate inexact products (the relaxation results of
+// Simoncini and Szyld); here the inexact products are the mixed form's
+// (FP32 arithmetic, error ~3e-7 relative) and the outer loop restores FP64
+// accuracy: r_k = f - (beta L_s + S) u_k with the FP64 plan's products,
+// (beta L_s~ + S) c_k = r_k by CG with the mixed plan's products to a
+// relative residual inner_tol, u_{k+1} = u_k + c_k.  Each outer step shrinks
+// the FP64 residual by about max(inner_tol, kappa * eps_mixed), so a few
+// steps, each one FP64 product, reach FP64 accuracy while nearly all
+// products run in the mixed form.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -146,6 +157,11 @@ __global__ void cg_update(double *u, double *r, const double *p, const double *q
     }
 }
 
+__global__ void axpy(double *y, const double *x, int64_t n, double a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
 __global__ void cg_direction(double *p, const double *r, int64_t n, double gamma) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = r[i] + gamma * p[i];
@@ -252,6 +268,64 @@ static cudaError_t dot(Plan &P, const double *a, const double *b, double *part, 
 }
 
 static int vec_blocks(const Plan &P) { return std::max(1, P.num_sms * 8); }
+
+// Work vectors of one CG solve (n each) and its reduction space.
+struct CgWork {
+    double *r, *p, *q, *lp, *part, *sc;
+};
+
+// Conjugate gradients on u -> beta L_s u + diag(s) u with P's products (Sec. 6.2.2):
+// u holds the initial guess (zero_start: u is set to 0 and r = f without a product),
+// stops at ||r|| <= tol ||f||.  *iters, *relres: steps taken, final ||r|| / ||f||.
+static nfl_status cg_core(Plan &P, double beta, const double *shift, const double *f, double *u, bool zero_start,
+                          double tol, int maxit, const CgWork &w, int *iters, double *relres) {
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    const int vb = vec_blocks(P);
+    double *r = w.r, *p = w.p, *q = w.q, *lp = w.lp;
+    double fn2 = 0.0;
+    *iters = 0;
+    if (dot(P, f, f, w.part, w.sc, &fn2) != cudaSuccess) return NFL_ERR_CUDA;
+    const double fn = std::sqrt(fn2);
+    if (zero_start) {
+        if (cudaMemsetAsync(u, 0, n * 8, s) != cudaSuccess ||
+            cudaMemcpyAsync(r, f, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return NFL_ERR_CUDA;
+    } else {
+        // r = f - op(u)
+        const nfl_status st = run_column(P, OP_LS, u, lp);
+        if (st != NFL_OK) return st;
+        cg_operator<<<vb, 256, 0, s>>>(lp, u, shift, n, beta, q);
+        sub_into<<<vb, 256, 0, s>>>(f, q, n, r);
+    }
+    if (cudaMemcpyAsync(p, r, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return NFL_ERR_CUDA;
+    double rr = 0.0;
+    if (dot(P, r, r, w.part, w.sc, &rr) != cudaSuccess) return NFL_ERR_CUDA;
+    int it = 0;
+    nfl_status result = NFL_ERR_NOT_CONVERGED;
+    const double target = tol * fn;
+    for (; it <= maxit; ++it) {
+        if (!std::isfinite(rr)) return NFL_ERR_NAN;
+        if (std::sqrt(rr) <= target) { result = NFL_OK; break; }
+        if (it == maxit) break;
+        const nfl_status st = run_column(P, OP_LS, p, lp);
+        if (st != NFL_OK) return st;
+        cg_operator<<<vb, 256, 0, s>>>(lp, p, shift, n, beta, q);
+        double pq = 0.0;
+        if (dot(P, p, q, w.part, w.sc, &pq) != cudaSuccess) return NFL_ERR_CUDA;
+        if (!(pq > 0.0)) return std::isfinite(pq) ? NFL_ERR_BREAKDOWN : NFL_ERR_NAN;
+        const double alpha = rr / pq;
+        cg_update<<<vb, 256, 0, s>>>(u, r, p, q, n, alpha);
+        double rr_new = 0.0;
+        if (dot(P, r, r, w.part, w.sc, &rr_new) != cudaSuccess) return NFL_ERR_CUDA;
+        cg_direction<<<vb, 256, 0, s>>>(p, r, n, rr_new / rr);
+        rr = rr_new;
+    }
+    *iters = it;
+    *relres = fn > 0.0 ? std::sqrt(rr) / fn : std::sqrt(rr);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NFL_ERR_CUDA;
+    return result;
+}
 
 }  // namespace nfl
 
@@ -389,49 +463,79 @@ nfl_status nfl_cg_solve(nfl_plan *plan, double beta, const double *shift, const 
     Plan &P = *reinterpret_cast<Plan *>(plan);
     if (!P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
     const int64_t n = P.n;
-    const cudaStream_t s = P.stream;
-    Dev R, Pv, Qv, Lp, part, sc;
-    if (cudaMalloc(&R.buf, n * 8) != cudaSuccess || cudaMalloc(&Pv.buf, n * 8) != cudaSuccess ||
-        cudaMalloc(&Qv.buf, n * 8) != cudaSuccess || cudaMalloc(&Lp.buf, n * 8) != cudaSuccess ||
-        cudaMalloc(&part.buf, kRedBlocks * 8) != cudaSuccess || cudaMalloc(&sc.buf, 8 * 8) != cudaSuccess)
+    Dev W, part, sc;
+    if (cudaMalloc(&W.buf, 4 * n * 8) != cudaSuccess || cudaMalloc(&part.buf, kRedBlocks * 8) != cudaSuccess ||
+        cudaMalloc(&sc.buf, 8 * 8) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
-    const int vb = vec_blocks(P);
-    double *r = R.buf, *p = Pv.buf, *q = Qv.buf, *lp = Lp.buf;
-    double fn2 = 0.0;
-    if (dot(P, f, f, part.buf, sc.buf, &fn2) != cudaSuccess) return NFL_ERR_CUDA;
-    const double fn = std::sqrt(fn2);
-    // r = f - op(u)
-    nfl_status st = run_column(P, OP_LS, u, lp);
-    if (st != NFL_OK) return st;
-    cg_operator<<<vb, 256, 0, s>>>(lp, u, shift, n, beta, q);
-    sub_into<<<vb, 256, 0, s>>>(f, q, n, r);
-    if (cudaMemcpyAsync(p, r, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return NFL_ERR_CUDA;
-    double rr = 0.0;
-    if (dot(P, r, r, part.buf, sc.buf, &rr) != cudaSuccess) return NFL_ERR_CUDA;
+    const CgWork w{W.buf, W.buf + n, W.buf + 2 * n, W.buf + 3 * n, part.buf, sc.buf};
     int it = 0;
-    nfl_status result = NFL_ERR_NOT_CONVERGED;
-    const double target = tol * fn;
-    for (; it <= maxit; ++it) {
-        if (!std::isfinite(rr)) return NFL_ERR_NAN;
-        if (std::sqrt(rr) <= target) { result = NFL_OK; break; }
-        if (it == maxit) break;
-        st = run_column(P, OP_LS, p, lp);
-        if (st != NFL_OK) return st;
-        cg_operator<<<vb, 256, 0, s>>>(lp, p, shift, n, beta, q);
-        double pq = 0.0;
-        if (dot(P, p, q, part.buf, sc.buf, &pq) != cudaSuccess) return NFL_ERR_CUDA;
-        if (!(pq > 0.0)) return std::isfinite(pq) ? NFL_ERR_BREAKDOWN : NFL_ERR_NAN;
-        const double alpha = rr / pq;
-        cg_update<<<vb, 256, 0, s>>>(u, r, p, q, n, alpha);
-        double rr_new = 0.0;
-        if (dot(P, r, r, part.buf, sc.buf, &rr_new) != cudaSuccess) return NFL_ERR_CUDA;
-        cg_direction<<<vb, 256, 0, s>>>(p, r, n, rr_new / rr);
-        rr = rr_new;
-    }
+    double rel = 0.0;
+    const nfl_status st = cg_core(P, beta, shift, f, u, false, tol, maxit, w, &it, &rel);
     if (iters) *iters = it;
+    if (relres) *relres = rel;
+    return st;
+}
+
+/*
+ * Mixed-precision iterative refinement of the CG solve: residuals with the
+ * outer plan's products (FP64), corrections by CG with the inner plan's
+ * products (FP32C).
+ */
+nfl_status nfl_cg_solve_refined(nfl_plan *plan, nfl_plan *inner, double beta, const double *shift, const double *f,
+                                double *u, double tol, double inner_tol, int maxit, int max_outer, int *iters,
+                                int *outer, double *relres) {
+    using namespace nfl;
+    if (!plan || !inner || plan == inner || !f || !u || !(beta > 0.0) || !(tol > 0.0) || !(inner_tol > 0.0) ||
+        !(inner_tol < 1.0) || maxit < 1 || max_outer < 1)
+        return NFL_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    Plan &Q = *reinterpret_cast<Plan *>(inner);
+    if (Q.n != P.n || Q.d != P.d || Q.kernel != P.kernel || Q.sigma != P.sigma) return NFL_ERR_INVALID_ARG;
+    for (int a = 0; a < P.d; ++a)
+        if (Q.center[a] != P.center[a]) return NFL_ERR_INVALID_ARG;     // other nodes
+    if (!P.degree_ok || !Q.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;
+    const int64_t n = P.n;
+    const cudaStream_t s = P.stream;
+    const int vb = vec_blocks(P);
+    Dev W, part, sc;
+    if (cudaMalloc(&W.buf, 6 * n * 8) != cudaSuccess || cudaMalloc(&part.buf, kRedBlocks * 8) != cudaSuccess ||
+        cudaMalloc(&sc.buf, 8 * 8) != cudaSuccess)
+        return NFL_ERR_OUT_OF_MEMORY;
+    // inner CG work (4 n), the outer residual r and the correction c
+    const CgWork w{W.buf, W.buf + n, W.buf + 2 * n, W.buf + 3 * n, part.buf, sc.buf};
+    double *r = W.buf + 4 * n, *c = W.buf + 5 * n;
+    // the inner plan works on this plan's stream for the call
+    const cudaStream_t qs = Q.stream;
+    Q.stream = s;
+    double fn2 = 0.0, rr = 0.0;
+    int total = 0, k = 0;
+    nfl_status result = NFL_ERR_NOT_CONVERGED;
+    nfl_status st = dot(P, f, f, part.buf, sc.buf, &fn2) == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+    const double fn = std::sqrt(fn2);
+    for (; st == NFL_OK; ++k) {
+        // r = f - (beta L_s + S) u with the outer (FP64) products
+        st = run_column(P, OP_LS, u, w.lp);
+        if (st != NFL_OK) break;
+        cg_operator<<<vb, 256, 0, s>>>(w.lp, u, shift, n, beta, w.q);
+        sub_into<<<vb, 256, 0, s>>>(f, w.q, n, r);
+        if (dot(P, r, r, part.buf, sc.buf, &rr) != cudaSuccess) { st = NFL_ERR_CUDA; break; }
+        if (!std::isfinite(rr)) { st = NFL_ERR_NAN; break; }
+        if (std::sqrt(rr) <= tol * fn) { result = NFL_OK; break; }
+        if (k == max_outer) break;
+        // (beta L_s + S) c = r with the inner products, from c = 0, to inner_tol ||r||
+        int it = 0;
+        double rel = 0.0;
+        const nfl_status ist = cg_core(Q, beta, shift, r, c, true, inner_tol, maxit, w, &it, &rel);
+        total += it;
+        if (ist != NFL_OK && ist != NFL_ERR_NOT_CONVERGED) { st = ist; break; }
+        axpy<<<vb, 256, 0, s>>>(u, c, n, 1.0);
+    }
+    Q.stream = qs;
+    if (iters) *iters = total;
+    if (outer) *outer = k;
     if (relres) *relres = fn > 0.0 ? std::sqrt(rr) / fn : std::sqrt(rr);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return NFL_ERR_CUDA;
-    return result;
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == NFL_OK) st = NFL_ERR_CUDA;
+    return st != NFL_OK ? st : result;
 }
 
 }  // extern "C"

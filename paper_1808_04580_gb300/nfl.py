@@ -67,6 +67,8 @@ SIGNATURES = {
     "nfl_cg_solve": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_apply_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                ctypes.POINTER(_L), _I]),
+    "nfl_cg_solve_refined": (_I, [_P, _P, _D, _P, _P, _P, _D, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                  ctypes.POINTER(_D)]),
     "nfl_cg_solve_noalloc": (_I, [_P, _D, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nfl_nystrom_k_largest": (_I, [_P, _I, _I, _I, _P, ctypes.c_uint64, _P, _P]),
     "nfl_form_grad_nodes": (_I, [_P, _P, _P, _P, _P]),
@@ -78,6 +80,7 @@ SIGNATURES = {
     "nfl_plan_kernels": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
     "nfl_plan_inject_fault": (_I, [_P, _I]),
+    "nfl_fma_rate": (_I, [_I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "nfl_status_string": (ctypes.c_char_p, [_I]),
 }
 
@@ -321,6 +324,27 @@ class Plan:
             _check(st, "nfl_cg_solve_noalloc" if noalloc else "nfl_cg_solve")
         return u, it.value, rel.value, st
 
+    def cg_solve_refined(self, inner, f, beta=1.0, shift=None, u0=None, tol=1e-10, inner_tol=1e-4, maxit=1000,
+                         max_outer=10, check=True):
+        """Solve (beta L_s + diag(shift)) u = f to this plan's accuracy with the correction
+        solves on ``inner`` (nfl_cg_solve_refined): (u, inner_iters, outer_steps, relres, status)."""
+        self._sync_stream()
+        _cuda_f64(f, "f")
+        f = f.contiguous()
+        u = torch.zeros_like(f) if u0 is None else _cuda_f64(u0, "u0").clone()
+        sp = None
+        if shift is not None:
+            shift = _cuda_f64(shift, "shift").contiguous()
+            sp = shift.data_ptr()
+        it, outer = ctypes.c_int(0), ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = _lib().nfl_cg_solve_refined(self._h, inner._h, float(beta), sp, f.data_ptr(), u.data_ptr(), float(tol),
+                                         float(inner_tol), int(maxit), int(max_outer), ctypes.byref(it),
+                                         ctypes.byref(outer), ctypes.byref(rel))
+        if check:
+            _check(st, "nfl_cg_solve_refined")
+        return u, it.value, outer.value, rel.value, st
+
     def form_grad_nodes(self, v, a, b):
         """d(a^T A_E b)/dv for the nodes v (n, d) of this Gaussian plan (nfl_form_grad_nodes)."""
         self._sync_stream()
@@ -358,6 +382,14 @@ class Plan:
 
 
 _OPS = {"W": 0, "A": 1, "Ls": 2}
+RATE_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def fma_rate(kind="fp32"):
+    """Measured multiply-add rate of the current device (nfl_fma_rate): (flop/s, ms)."""
+    fl, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib().nfl_fma_rate(RATE_KINDS[kind], _stream(), ctypes.byref(fl), ctypes.byref(ms)), "nfl_fma_rate")
+    return fl.value, ms.value
 
 
 def apply_batched(plans, xs, op="Ls", outs=None):

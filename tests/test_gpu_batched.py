@@ -123,3 +123,30 @@ def test_captured_graph_survives_block_products():
     assert float(torch.linalg.norm((x - y) - (x - ref)) / torch.linalg.norm(x - ref)) < 1e-6
     assert float(torch.linalg.norm((X8[:, 3] - Y8[:, 3]) - (X8[:, 3] - p.apply_Ls(X8[:, 3].contiguous())))) \
         < 1e-6 * float(torch.linalg.norm(X8[:, 3] - Y8[:, 3]))
+
+
+def test_first_block_product_under_capture_is_refused():
+    """The first block product allocates the plan's block buffers; under stream capture
+    it returns NFL_ERR_INVALID_ARG instead (cudaMalloc would invalidate the capture),
+    and after one uncaptured block product the same call captures and replays."""
+    from paper_1808_04580_gb300 import NflError
+    n = 3000
+    plan = Plan(gpu(workloads.gaussian_mixture(n, seed=5)), 0.5, 32, 4, 4, -1.0, "fp32c")
+    assert plan.info()["block_cols"] == 8
+    x = gpu(workloads.rhs(n, nrhs=8, seed=6))
+    out = torch.empty((8, n), dtype=torch.float64, device=DEV)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with pytest.raises(NflError) as e:
+        with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+            plan.apply_Ls(x, out=out)
+    assert e.value.name == "NFL_ERR_INVALID_ARG"
+    ref = plan.apply_Ls(x).clone()                 # uncaptured: allocates the block buffers
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        plan.apply_Ls(x, out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(torch.linalg.norm((x - out.t()) - (x - ref)) / torch.linalg.norm(x - ref)) < 1e-6

@@ -9,6 +9,7 @@ mixed-precision budget of 1e-6.
 import numpy as np
 import pytest
 import torch
+from _norms import assert_close, errors
 
 from oracle import direct, spectral
 from paper_1808_04580_gb300 import Plan, workloads
@@ -46,9 +47,9 @@ def test_ball10m_products_against_direct_sum(ball10m):
         assert plan.info()["device_error"] == 0
         plan.close()
         # BF16W: taps rounded to BF16 (reported, not held to the mixed-form budget)
-        assert rel(out[prec][rows], ref) < (1e-2 if prec == "bf16w" else 1e-6), prec
-    assert rel(out["fp32c"], out["fp64"]) < 1e-6
-    assert rel(out["fp32"], out["fp64"]) < 1e-6
+        assert_close(out[prec][rows], ref, (1e-2 if prec == "bf16w" else 1e-6), what=prec)
+    assert_close(out["fp32c"], out["fp64"], 1e-6)
+    assert_close(out["fp32"], out["fp64"], 1e-6)
     assert 1e-5 < rel(out["bf16w"], out["fp64"]) < 1e-2
 
 
@@ -71,11 +72,11 @@ def test_image1m_mixed_against_fp64():
     y64 = p64.apply_Ls(xg).cpu().numpy()
     y32 = p32.apply_Ls(xg).cpu().numpy()
     # L_s x = x - A x: measure the error relative to ||A x||, which x would hide
-    assert rel(x - y32, x - y64) < 1e-6
+    assert_close(x - y32, x - y64, 1e-6)
     w64 = p64.apply_W(xg).cpu().numpy()
     rows = np.random.default_rng(7).choice(v.shape[0], 128, replace=False)
     ref = direct.rows_W(v, 0.1, x, rows)
-    assert rel(w64[rows], ref) < 1e-4   # N = 64 kernel approximation error
+    assert_close(w64[rows], ref, 1e-4)   # N = 64 kernel approximation error
 
 
 def test_lanczos_200k_fp32c_against_fp64():
@@ -107,7 +108,11 @@ def test_cg_moons500k():
         u, iters, relres, st = plan.cg_solve(gpu(f), beta=1.0, shift=gpu(10.0 * mask), tol=1e-6, maxit=3000)
         assert st == 0 and relres <= 1e-6, (prec, iters, relres)
         sols[prec] = u.cpu().numpy()
-    assert rel(sols["fp32c"], sols["fp64"]) < 1e-3
+    # both solves stop at a relative residual of 1e-6, which bounds their difference
+    # (measured 2.0e-6 in the 2-norm, 2.7e-6 element-wise); tests/test_gpu_refine.py
+    # takes the mixed form to FP64 accuracy
+    print("moons500k CG, FP32C vs FP64 solution:", errors(sols["fp32c"], sols["fp64"]))
+    assert_close(sols["fp32c"], sols["fp64"], 6e-6)
     # the labelled signs are reproduced on the labelled nodes
     lab_idx = np.nonzero(mask)[0]
     assert np.mean(np.sign(sols["fp64"][lab_idx]) == lab[lab_idx]) > 0.99
@@ -141,7 +146,9 @@ def test_image1m_20_smallest_fp32c_against_fp64():
         assert st == 0, (prec, it)
         out[prec] = e
         p.close()
-    assert np.abs(out["fp32c"] - out["fp64"]).max() < 1e-5
+    print("image1M 20 smallest, FP32C - FP64 eigenvalues: max %.3e" % np.abs(out["fp32c"] - out["fp64"]).max())
+    # measured 3.1e-8 (the eigenvalues of L_s lie in [0, 2]; the mixed products err by ~3e-7)
+    assert np.abs(out["fp32c"] - out["fp64"]).max() < 1e-7
 
 
 def test_moons500k_gradients_sigma_and_nodes():

@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 import torch
+from _norms import assert_close
 
 from oracle import direct, fastsum, spectral
 from paper_1808_04580_gb300 import KERNELS, NflError, Plan, workloads
@@ -64,7 +65,7 @@ def test_fp64_matches_alg2_oracle(case):
     info = plan.info()
     assert info["rho"] == pytest.approx(ref.rho, rel=1e-14)
     xt = gpu(x)
-    assert rel(plan.apply_W(xt).cpu().numpy(), ref.apply_W(x)) < 1e-10
+    assert_close(plan.apply_W(xt).cpu().numpy(), ref.apply_W(x), 1e-10)
     deg = plan.degree().cpu().numpy()
     np.testing.assert_allclose(deg, ref.degree, rtol=1e-10, atol=1e-12 * np.abs(ref.degree).max())
     # Lemma 3.1: a coarse plan can push a small degree below zero (eps >= eta);
@@ -74,8 +75,44 @@ def test_fp64_matches_alg2_oracle(case):
         with pytest.raises(NflError):
             plan.apply_A(xt)
         return
-    assert rel(plan.apply_A(xt).cpu().numpy(), ref.apply_A(x)) < 1e-10
-    assert rel(plan.apply_Ls(xt).cpu().numpy(), ref.apply_Ls(x)) < 1e-10
+    assert_close(plan.apply_A(xt).cpu().numpy(), ref.apply_A(x), 1e-10)
+    assert_close(plan.apply_Ls(xt).cpu().numpy(), ref.apply_Ls(x), 1e-10)
+
+
+def _dense_clusters(n, n_dense, seed):
+    """Four normal clusters (std 0.05 in [-1, 1]^3) plus n_dense nodes in one very tight
+    cluster (std 0.002), which puts more than one 8192-node chunk into a tile."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, (4, 3))
+    v = c[rng.integers(0, 4, n)] + 0.05 * rng.standard_normal((n, 3))
+    v[:n_dense] = c[0] + 0.002 * rng.standard_normal((n_dense, 3))
+    return v
+
+
+# the plain FP64 form at the large windows in 3-D: the cell-run spread (m = 6 on 4^3-cell
+# tiles, m = 7, 8 on 2^3-cell tiles) and the FP64 interpolation, N = 128 (the grid of the
+# 10^7-node workload) included; (m, N, n, sigma)
+FP64_LARGE_M = [(6, 128, 12000, 0.3), (6, 32, 12000, 0.6), (7, 32, 10000, 0.6), (8, 32, 10000, 0.6)]
+
+
+@pytest.mark.parametrize("case", FP64_LARGE_M, ids=lambda c: "m%d-N%d-n%d" % c[:3])
+def test_fp64_large_windows_match_alg2_oracle(case):
+    m, N, n, sigma = case
+    v = _dense_clusters(n, 9000, seed=70 + m + N)
+    x = workloads.rhs(n, seed=71 + m)
+    ref = fastsum.NormalizedFastsum(v, sigma, N, m, m)
+    plan = Plan(gpu(v), sigma, N, m, m, -1.0, "fp64")
+    info = plan.info()
+    assert info["work_items"] > info["tiles"]          # a tile of several chunks
+    xt = gpu(x)
+    err = assert_close(plan.apply_W(xt).cpu().numpy(), ref.apply_W(x), 1e-10, x=x)
+    print("FP64 m=%d N=%d W x against Alg. 2:" % (m, N), err)
+    deg = plan.degree().cpu().numpy()
+    np.testing.assert_allclose(deg, ref.degree, rtol=1e-10, atol=1e-12 * np.abs(ref.degree).max())
+    assert info["degree_ok"] == 1
+    yl = plan.apply_Ls(xt).cpu().numpy()
+    # L_s x = x - A x: the A x parts
+    assert_close(x - yl, x - ref.apply_Ls(x), 1e-10)
 
 
 def test_spiral5k_fp64_against_alg2_and_direct():
@@ -85,11 +122,11 @@ def test_spiral5k_fp64_against_alg2_and_direct():
     plan = Plan(gpu(v), 0.5, 32, 4, 4, -1.0, "fp64")
     y = plan.apply_W(gpu(x)).cpu().numpy()
     ref = fastsum.NormalizedFastsum(v, 0.5, 32, 4, 4)
-    assert rel(y, ref.apply_W(x)) < 1e-10
+    assert_close(y, ref.apply_W(x), 1e-10)
     # against the exact sum: within the method's own error (window m = 4 ~ 1e-7)
-    assert rel(y, direct.apply_W(v, 0.5, x)) < 5e-7
+    assert_close(y, direct.apply_W(v, 0.5, x), 5e-7)
     yl = plan.apply_Ls(gpu(x)).cpu().numpy()
-    assert rel(yl, ref.apply_Ls(x)) < 1e-10
+    assert_close(yl, ref.apply_Ls(x), 1e-10)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("fp32c", 1e-6)])
@@ -98,13 +135,15 @@ def test_mixed_precision_forms(prec, tol):
     x = workloads.rhs(3000, seed=12)
     ref = fastsum.NormalizedFastsum(v, 0.3, 32, 4, 4)
     plan = Plan(gpu(v), 0.3, 32, 4, 4, -1.0, prec)
-    assert rel(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x)) < tol
-    assert rel(plan.apply_A(gpu(x)).cpu().numpy(), ref.apply_A(x)) < tol
+    assert_close(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x), tol)
+    assert_close(plan.apply_A(gpu(x)).cpu().numpy(), ref.apply_A(x), tol)
     assert plan.info()["device_error"] == 0
 
 
 # every 3-D tile shape of the spread kernels (warp-slice: m = 2, 3, 4, 6; cell-run:
 # m = 7, 8; shared-tile: m = 5) and of the tensor-core interpolation, both mixed forms
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
 @pytest.mark.parametrize("m,N", [(2, 16), (3, 16), (4, 32), (6, 32), (7, 32), (5, 32), (8, 32)])
 def test_mixed_forms_each_window_size(m, N, prec, tol):
@@ -114,10 +153,10 @@ def test_mixed_forms_each_window_size(m, N, prec, tol):
     ref = fastsum.NormalizedFastsum(v, 0.4, N, m, m)
     plan = Plan(gpu(v), 0.4, N, m, m, -1.0, prec)
     y = plan.apply_W(gpu(x)).cpu().numpy()
-    assert rel(y, ref.apply_W(x)) < tol
+    assert_close(y, ref.apply_W(x), tol)
     np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)
     yl = plan.apply_Ls(gpu(x)).cpu().numpy()
-    assert rel(x - yl, x - ref.apply_Ls(x)) < tol
+    assert_close(x - yl, x - ref.apply_Ls(x), tol)
     assert plan.info()["device_error"] == 0
 
 
@@ -139,14 +178,18 @@ def test_mixed_forms_wrap_and_low_dimensions(case, prec, tol):
     x = workloads.rhs(n, seed=41 + n)
     ref = fastsum.NormalizedFastsum(v, sigma, N, m, p, None if eps_B < 0 else eps_B)
     plan = Plan(gpu(v), sigma, N, m, p, eps_B, prec)
-    assert rel(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x)) < tol
+    assert_close(plan.apply_W(gpu(x)).cpu().numpy(), ref.apply_W(x), tol)
     assert plan.info()["device_error"] == 0
 
 
 # the other kernels of Sec. 2 through Alg. 2 (scaling rule, K(0), output scale)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32c", 2e-6)])
 @pytest.mark.parametrize("kind,d", [("laplacian_rbf", 3), ("multiquadric", 3), ("inverse_multiquadric", 3),
                                     ("multiquadric", 2), ("inverse_multiquadric", 1)])
+
+
 def test_kernel_variants_match_alg2_oracle(kind, d, prec, tol):
     n = 1500
     v = _cloud("clusters", n, d, seed=50 + d)
@@ -158,9 +201,9 @@ def test_kernel_variants_match_alg2_oracle(kind, d, prec, tol):
     assert info["k0"] == pytest.approx(ref.K0, rel=1e-15)
     assert info["out_scale"] == pytest.approx(ref.out_scale, rel=1e-12)
     xt = gpu(x)
-    assert rel(plan.apply_W(xt).cpu().numpy(), ref.apply_W(x)) < tol
+    assert_close(plan.apply_W(xt).cpu().numpy(), ref.apply_W(x), tol)
     np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)
-    assert rel(plan.apply_A(xt).cpu().numpy(), ref.apply_A(x)) < tol
+    assert_close(plan.apply_A(xt).cpu().numpy(), ref.apply_A(x), tol)
     assert info["device_error"] == 0
 
 
@@ -197,7 +240,7 @@ def test_two_nodes_closed_form():
     plan = Plan(gpu(v), 0.8, 64, 8, 4, -1.0, "fp64")
     y = plan.apply_W(gpu(x)).cpu().numpy()
     ref = fastsum.NormalizedFastsum(v, 0.8, 64, 8, 4)
-    assert rel(y, ref.apply_W(x)) < 1e-10
+    assert_close(y, ref.apply_W(x), 1e-10)
     # sigma~ = 0.7 after scaling: a wide kernel on the torus, method error ~3e-4
     np.testing.assert_allclose(y, [-3.0 * w, 2.0 * w], rtol=2e-3)
     np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=1e-10)
@@ -209,7 +252,7 @@ def test_coincident_nodes():
     plan = Plan(gpu(v), 0.5, 16, 4, 4, -1.0, "fp64")
     y = plan.apply_W(gpu(x)).cpu().numpy()
     ref = fastsum.NormalizedFastsum(v, 0.5, 16, 4, 4)
-    assert rel(y, ref.apply_W(x)) < 1e-10
+    assert_close(y, ref.apply_W(x), 1e-10)
     np.testing.assert_allclose(y, x.sum() - x, rtol=1e-4)          # W = 1 1^T - I exactly
 
 
@@ -269,7 +312,7 @@ def test_cg_solve_matches_dense_solve():
     plan = Plan(gpu(v), 0.5, 64, 8, 8, -1.0, "fp64")
     u, iters, relres, st = plan.cg_solve(gpu(f), beta=beta, shift=gpu(shift), tol=1e-12, maxit=2000)
     assert relres <= 1e-12
-    assert rel(u.cpu().numpy(), u_ref) < 1e-9
+    assert_close(u.cpu().numpy(), u_ref, 1e-9)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("fp32c", 1e-6), ("fp32", 1e-6)])
@@ -296,11 +339,11 @@ def test_bf16w_matches_bf16_tap_oracle(m, N, d):
     y = p.apply_W(gpu(x)).cpu().numpy()
     ref = fastsum.NormalizedFastsum(v, 0.3, N, m, m, taps="bf16").apply_W(x)
     ref64 = fastsum.NormalizedFastsum(v, 0.3, N, m, m).apply_W(x)
-    assert rel(y, ref) < 2e-5
+    assert_close(y, ref, 2e-5)
     assert rel(y, ref64) > 1e-4
     ya = p.apply_A(gpu(x)).cpu().numpy()
     refa = fastsum.NormalizedFastsum(v, 0.3, N, m, m, taps="bf16").apply_A(x)
-    assert rel(ya, refa) < 2e-5
+    assert_close(ya, refa, 2e-5)
 
 
 @pytest.mark.parametrize("prec,m,tol", [("fp32c", 6, 2e-6), ("fp32", 4, 1e-5), ("fp64", 4, 1e-10)])
@@ -317,7 +360,7 @@ def test_autotune_keeps_the_products(prec, m, tol):
     assert t["slide_tiles"] in (1, 4, 8, 16)
     assert t["best_ms"] > 0.0
     ref = fastsum.NormalizedFastsum(v, 0.3, 32, m, m).apply_W(x)
-    assert rel(p.apply_W(gpu(x)).cpu().numpy(), ref) < tol
+    assert_close(p.apply_W(gpu(x)).cpu().numpy(), ref, tol)
 
 
 @pytest.mark.parametrize("prec,m,tol", [("fp32c", 6, 1e-6), ("fp32", 4, 5e-6), ("bf16w", 3, 5e-6)])

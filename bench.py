@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the W x precision sweep (FP32, FP32C, BF16W)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch parameters")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the spiral5k, image1M and graphs256 fields")
     return ap.parse_args()
 
 
@@ -222,6 +223,109 @@ def run_reference(args, world, rank):
         "cpu_baseline": {"value": value, "unit": "matvecs/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def _events_ms(fn, reps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def other_workloads(dev):
+    """The paper-shaped workloads beside the headline one (not part of the timed step):
+    spiral5k (FP64 W x and the 10 smallest eigenpairs), image1M (L_s in FP32C and FP64),
+    graphs256 (batched plan creation and one captured CUDA graph of 8 columns per graph)."""
+    import numpy as np
+    import torch
+    from paper_1808_04580_gb300 import Plan, apply_batched, create_batched, workloads
+    stream = torch.cuda.current_stream()
+    gpu = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)   # noqa: E731
+    # column blocks in column-major storage (the layout the library takes without a copy)
+    cols = lambda a: torch.from_numpy(np.asfortranarray(a, dtype=np.float64)).to(dev)   # noqa: E731
+    out = {}
+
+    # spiral5k: n = 5000 two-arm spiral, sigma 0.5, N 32, m 4, p 4, FP64
+    v = workloads.two_arm_spiral(5000, seed=0)
+    x = gpu(workloads.rhs(5000, seed=1))
+    p = Plan(gpu(v), 0.5, 32, 4, 4, -1.0, "fp64")
+    ms = _events_ms(lambda: p.apply_W(x), 20, stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ev, V, iters, st = p.lanczos_k_smallest(10, tol=1e-10, maxit=300, seed=1)
+    lz = time.perf_counter() - t
+    R = p.apply_A(V) - V * torch.from_numpy(1.0 - ev).to(dev)[None, :]
+    out["spiral5k"] = {"workload": "n=5000 two-arm spiral d=3, sigma=0.5, N=32, m=4, p=4, FP64",
+                       "W_matvecs_per_s": 1000.0 / ms, "ms_per_W_matvec": ms,
+                       "lanczos_10_smallest_s": lz, "lanczos_steps": iters, "status": st,
+                       "max_residual": float(torch.linalg.norm(R, dim=0).max())}
+    p.close()
+
+    # image1M: 1000 x 1000 Voronoi image (12 regions), sigma 0.1, N 64, m 4
+    v, _ = workloads.voronoi_image(seed=0)
+    n = v.shape[0]
+    X = cols(workloads.rhs(n, nrhs=4, seed=2))
+    vg = gpu(v)
+    res = {"workload": "n=1,000,000 pixels of a 1000x1000 image, 12 Voronoi regions, RGB features d=3, "
+                       "sigma=0.1, N=64, m=4"}
+    ys = {}
+    for prec in ("fp32c", "fp64"):
+        pp = Plan(vg, 0.1, 64, 4, 4, -1.0, prec)
+        if prec == "fp32c":
+            pp.autotune()
+        Y = torch.empty((4, n), dtype=torch.float64, device=dev)
+        ms = _events_ms(lambda: pp.apply_Ls(X, out=Y), 5 if prec == "fp32c" else 2, stream)
+        res[prec] = {"Ls_matvecs_per_s": 4 * 1000.0 / ms, "ms_per_step_of_4": ms}
+        ys[prec] = Y.clone()
+        pp.close()
+    a, b = X.t() - ys["fp32c"], X.t() - ys["fp64"]
+    res["fp32c_rel_err_vs_fp64_Ax"] = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    res["speedup_fp32c_vs_fp64"] = res["fp32c"]["Ls_matvecs_per_s"] / res["fp64"]["Ls_matvecs_per_s"]
+    out["image1M"] = res
+    del X, vg, ys
+
+    # graphs256: 256 Gaussian-mixture graphs, n log-uniform in [1e3, 2e5], 8 columns each, FP32C
+    clouds = workloads.many_graphs(256, seed=0)
+    sizes = [c.shape[0] for c in clouds]
+    vgs = [gpu(c) for c in clouds]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    plans = create_batched(vgs, 0.5, 64, 4, 4, -1.0, "fp32c")
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t
+    t = time.perf_counter()
+    single = [Plan(vv, 0.5, 64, 4, 4, -1.0, "fp32c") for vv in vgs]
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t
+    for q in single:
+        q.close()
+    for q in plans:
+        q.autotune()
+    xs = [cols(workloads.rhs(nn, nrhs=8, seed=g + 7)) for g, nn in enumerate(sizes)]
+    outs = [torch.empty((8, nn), dtype=torch.float64, device=dev) for nn in sizes]
+    apply_batched(plans, xs, "Ls", outs=outs)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        apply_batched(plans, xs, "Ls", outs=outs)
+    ms = _events_ms(graph.replay, 5, stream)
+    ncols = 8 * len(plans)
+    out["graphs256"] = {"workload": "256 Gaussian-mixture graphs d=3, n log-uniform in [1e3, 2e5] (sum %d), "
+                                    "8 right-hand sides each, FP32C, sigma=0.5, N=64, m=4" % sum(sizes),
+                        "ms_per_replay": ms, "Ls_matvecs_per_s": ncols * 1000.0 / ms,
+                        "point_rhs_per_s": 8 * sum(sizes) * 1000.0 / ms,
+                        "launches_per_replay": int(sum(q.kernels(8) for q in plans)),
+                        "plan_create_batched_s": t_batched, "plan_create_one_by_one_s": t_single}
+    for q in plans:
+        q.close()
+    return out
 
 
 def main():
@@ -428,6 +532,10 @@ def main():
             sweep[form] = entry
             pf.close()
 
+    others = None
+    if rank == 0 and not args.no_other:
+        others = other_workloads(dev)
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": args.steps,
@@ -453,6 +561,7 @@ def main():
             "spread_gather": spread_gather,
             "fma_rates_tflops": {k: (v / 1e12 if v else None) for k, v in rates.items()},
             "cpu_baseline": cpu_baseline,
+            "other_workloads": others,
             "e2e": e2e,
             "gpu_launches": plan.kernels(nrhs) * args.steps,
             "clocks": clocks,

@@ -133,7 +133,10 @@ typedef struct {
  *   n         >= 1.   d in {1, 2, 3}.
  *   kernel    NFL_KERNEL_* (above).
  *   sigma     > 0: the kernel's shape parameter (sigma, or c for the multiquadrics).
- *   N         bandwidth: a power of two in [4, 512] (Fig. tab:fastsum_param).
+ *   N         bandwidth: a power of two in [4, 512].  Sec. 3 and Fig.
+ *             tab:fastsum_param allow any even N; this library reads it as a
+ *             power of two (its FFT passes are radix-4/2), which covers every
+ *             N the paper uses (16, 32, 64 and 512 in Sec. 6).
  *   m         window cut-off, 1 <= m <= 12.
  *   p         regularization smoothness; p <= 0 selects the default p = m.
  *   eps_B     regularization width in [0, 1/2); eps_B < 0 selects p / N.
@@ -148,6 +151,25 @@ nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double
                            int N, int m, int p, double eps_B, int precision,
                            void *stream, nfl_plan **out);
 
+/*
+ * G plans at once (Alg. 2 steps 1-4 for each of G independent node sets, e.g.
+ * many graphs of uneven size): the same work as G calls of nfl_plan_create,
+ * but each stage of plan creation is issued for every plan (spread over the
+ * library's streams, forked from `stream`) before the host synchronizes once,
+ * so the batch costs a handful of host synchronizations in total rather than
+ * a handful per plan.
+ *   v[g]      device, n[g] x d row-major FP64 node coordinates of graph g.
+ *   n[g]      >= 1.   sigma[g] > 0: the kernel parameter of graph g.
+ *   d, kernel, N, m, p, eps_B, precision   as in nfl_plan_create, common to all.
+ *   stream    every plan's stream on return.
+ *   out       host array of G entries receiving the plans.
+ * On any failure no plan is returned (all entries NULL) and the first failing
+ * plan's status is returned.  Synchronizes the host.
+ */
+nfl_status nfl_plan_create_batched(int G, const double *const *v, const int64_t *n, int d, int kernel,
+                                   const double *sigma, int N, int m, int p, double eps_B, int precision,
+                                   void *stream, nfl_plan **out);
+
 /* Release the plan and its device memory (synchronizes its stream). NULL is ignored. */
 void nfl_plan_destroy(nfl_plan *plan);
 
@@ -157,7 +179,8 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info);
 
 /*
  * Pick the launch parameters of the plan's products by timing them on the
- * plan's own nodes (a W product with x = 1, CUDA events on the plan's
+ * plan's own nodes (not a paper construct: the products stay those of Alg. 1
+ * and Alg. 2 step 5; the paper's parameters N, m, p, eps_B are the caller's) (a W product with x = 1, CUDA events on the plan's
  * stream), one parameter at a time, keeping the fastest:
  *   fft_lines_cap  grid points per CTA of the FFT passes (lines of length
  *                  2N per CTA = cap / 2N), from {256, 512, 1024, 2048};
@@ -224,7 +247,8 @@ nfl_status nfl_apply_host(nfl_plan *plan, int op, const double *x, int64_t ldx,
 
 /*
  * Products for many independent graphs in one call (a batch of plans):
- * y_g = op(x_g) for g < G with op 0 = W, 1 = A, 2 = L_s, each x_g / y_g a
+ * y_g = op(x_g) for g < G with op 0 = W, 1 = A, 2 = L_s (Alg. 1, Alg. 2 step 5;
+ * the batching is not a paper construct: the paper treats one graph at a time), each x_g / y_g a
  * device block of nrhs columns with leading dimension ld[g] >= n_g.  The
  * work forks from the stream of plans[0] onto library streams (16 per
  * device, made on first use; plans largest first to the least loaded
@@ -407,7 +431,7 @@ nfl_status nfl_cg_solve_noalloc(nfl_plan *plan, double beta, const double *shift
                                 int *iters, double *relres);
 
 /*
- * Stage timing (tracing).  When enabled, CUDA events on the plan's stream
+ * Stage timing (tracing; not a paper construct).  When enabled, CUDA events on the plan's stream
  * bracket the four stages of every product column -- or of every block of
  * columns that goes through the stages together: prep (grid clear, staging
  * of x~ and the epilogue's z, for FP32C the fixed-point scale), spread, FFT
@@ -430,10 +454,12 @@ nfl_status nfl_plan_stage_times(nfl_plan *plan, double *ms, int64_t *columns);
  */
 nfl_status nfl_plan_inject_fault(nfl_plan *plan, int kind);
 
-/* Number of kernel launches one product column makes (for launch accounting). */
+/* Number of kernel launches one product column makes (launch accounting; not a
+ * paper construct). */
 nfl_status nfl_plan_kernels_per_column(const nfl_plan *plan, int *kernels);
 
-/* Number of kernel launches one product of nrhs >= 1 columns makes: blocks of
+/* Number of kernel launches one product of nrhs >= 1 columns makes (not a paper
+ * construct): blocks of
  * nfl_info.block_cols columns take one launch per stage on the 3-D
  * tensor-core path. */
 nfl_status nfl_plan_kernels(const nfl_plan *plan, int nrhs, int *kernels);

@@ -179,8 +179,8 @@ nfl_status ensure_columns(Plan &P, int nc);
 // warp-spread work items from tile_items with runs of at most slide_tiles tiles
 nfl_status rebuild_spread_items(Plan &P);
 
-// plan-time pieces
-nfl_status compute_coefficients(Plan &P);
+// the warp spread's work list built from tile_items (host)
+std::vector<WorkItem> spread_item_list(const Plan &P);
 
 }  // namespace nfl
 

@@ -269,9 +269,15 @@ nfl_status ensure_columns(Plan &P, int nc) {
     return NFL_OK;
 }
 
-nfl_status rebuild_spread_items(Plan &P) {
+// The warp spread's work list: runs of at most slide_tiles tiles, largest first.
+std::vector<WorkItem> spread_item_list(const Plan &P) {
     std::vector<WorkItem> s = slide_items(P.tile_items, P.ntile[P.d - 1], P.slide_tiles);
     std::stable_sort(s.begin(), s.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
+    return s;
+}
+
+nfl_status rebuild_spread_items(Plan &P) {
+    const std::vector<WorkItem> s = spread_item_list(P);
     if ((int64_t)s.size() > P.nsitems || !P.sitems) {
         cudaFree(P.sitems);
         P.sitems = nullptr;
@@ -528,7 +534,13 @@ static double bessel_i0(double z) {
     return sum;
 }
 
-nfl_status compute_coefficients(Plan &P) {
+// Step 3 (b_l by the trapezoidal rule) and the fused multiplier, launched on the
+// plan's stream without a host synchronization: the kernel samples, the three
+// separable cosine sums and the multiplier.  tab (page-locked host memory that
+// stays valid until the stream has passed these launches) receives the cosine
+// table (N values) and the deconvolution factors (N/2 + 1); S, T1, ctab, dec
+// are device temporaries the caller frees after the stream has passed them.
+static nfl_status coefficients_launch(Plan &P, double *tab, double *&S, double *&T1, double *&ctab, double *&dec) {
     const int N = P.N, d = P.d, Kh = N / 2 + 1;
     KRParams kp{};
     kp.N = N;
@@ -544,14 +556,10 @@ nfl_status compute_coefficients(Plan &P) {
     }
     int64_t full = 1;
     for (int a = 0; a < d; ++a) full *= N;
-    double *S = nullptr, *T1 = nullptr, *ctab = nullptr, *dec = nullptr;
-    auto cleanup = [&]() { cudaFree(S); cudaFree(T1); cudaFree(ctab); cudaFree(dec); };
     if (cudaMalloc(&S, full * sizeof(double)) != cudaSuccess || cudaMalloc(&T1, full * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&ctab, N * sizeof(double)) != cudaSuccess || cudaMalloc(&dec, Kh * sizeof(double)) != cudaSuccess) {
-        cleanup();
+        cudaMalloc(&ctab, N * sizeof(double)) != cudaSuccess || cudaMalloc(&dec, Kh * sizeof(double)) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
-    }
-    std::vector<double> h_ct(N), h_dec(Kh);
+    double *h_ct = tab, *h_dec = tab + N;
     for (int q = 0; q < N; ++q) h_ct[q] = std::cos(2.0 * M_PI * q / N);
     // dec(k) = (phi(0) / (n phi_hat(k)))^2 = (phi(0) / I_0(m sqrt(b^2 - (2 pi k / n)^2)))^2
     const double b = P.kb_b, m = P.m, n = P.ngrid;
@@ -562,11 +570,9 @@ nfl_status compute_coefficients(Plan &P) {
         h_dec[k] = r * r;
     }
     cudaStream_t s = P.stream;
-    if (cudaMemcpyAsync(ctab, h_ct.data(), N * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(dec, h_dec.data(), Kh * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cleanup();
+    if (cudaMemcpyAsync(ctab, h_ct, N * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dec, h_dec, Kh * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return NFL_ERR_CUDA;
-    }
     const int blocks = P.num_sms * 8;
     kr_samples<<<blocks, 256, 0, s>>>(S, kp);
     // cosine transform along each axis, last axis first
@@ -590,10 +596,7 @@ nfl_status compute_coefficients(Plan &P) {
     else { mp.nA = Kh; mp.nB = N + 1; }
     if (fft_is_double(P.prec)) build_multiplier<double><<<blocks, 256, 0, s>>>(src, dec, mp, (double *)P.mult);
     else build_multiplier<float><<<blocks, 256, 0, s>>>(src, dec, mp, (float *)P.mult);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cleanup();
-    return e == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
 }
 
 static void free_plan(Plan *P) {
@@ -679,16 +682,61 @@ static void window_poly(Plan &P) {
     }
 }
 
-static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel, double sigma, int N, int m, int p,
-                                   double eps_B, int prec, cudaStream_t stream, Plan *P) {
+// ------------------------------------------------------------ plan creation
+// Alg. 2 steps 1-4 run as phases, each of which only issues work on the plan's
+// stream and ends with device-to-host reads into page-locked memory; the host
+// synchronizes once between phases.  nfl_plan_create runs the phases for one
+// plan; nfl_plan_create_batched runs each phase for every plan of a batch
+// (spread over the library's streams) before the one synchronization, so a
+// batch costs as many host synchronizations as one plan.
+constexpr int kRBlocks = 1024;   // reduction partials per pass
+
+struct Builder {
+    Plan *P = nullptr;
+    const double *v = nullptr;
+    int64_t n = 0;
+    int d = 0, kernel = 0, N = 0, m = 0, p = 0, prec = 0;
+    double sigma = 0, eps_B = 0;
+    cudaStream_t stream = 0;
+    nfl_status st = NFL_OK;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    Geometry G{};
+    int cpt = 1;
+    double *part = nullptr;              // device reduction partials (kRBlocks x 6)
+    double *hp = nullptr;                // page-locked: the partials and counts read back
+    int32_t *key_of = nullptr, *rank = nullptr, *kcount = nullptr, *count = nullptr, *chunks = nullptr;
+    int64_t *kstart = nullptr, *start = nullptr, *item_off = nullptr;
+    unsigned long long *nonempty = nullptr;
+    WorkItem *hitems = nullptr;          // page-locked: chunks read back, then the lists uploaded
+    double *htab = nullptr;              // page-locked: twiddles, cosine table, deconvolution factors
+    double *S = nullptr, *T1 = nullptr, *ctab = nullptr, *dec = nullptr;   // coefficient temporaries
+};
+
+static void release_temporaries(Builder &B) {
+    cudaFree(B.part); cudaFree(B.key_of); cudaFree(B.rank); cudaFree(B.kcount); cudaFree(B.count);
+    cudaFree(B.chunks); cudaFree(B.kstart); cudaFree(B.start); cudaFree(B.item_off); cudaFree(B.nonempty);
+    cudaFree(B.S); cudaFree(B.T1); cudaFree(B.ctab); cudaFree(B.dec);
+    cudaFreeHost(B.hp); cudaFreeHost(B.hitems); cudaFreeHost(B.htab);
+    B.part = B.S = B.T1 = B.ctab = B.dec = B.hp = B.htab = nullptr;
+    B.key_of = B.rank = B.kcount = B.count = B.chunks = nullptr;
+    B.kstart = B.start = B.item_off = nullptr;
+    B.nonempty = nullptr;
+    B.hitems = nullptr;
+}
+
+// Fields, window polynomials, per-plan scalars; step 1: bounding-box partials.
+static nfl_status phase_setup(Builder &B) {
+    Plan *P = B.P;
+    int prec = B.prec;
     // BF16W is the FP32 form with BF16-rounded window taps
     P->bf16_taps = prec == NFL_PREC_BF16W;
     if (P->bf16_taps) prec = NFL_PREC_FP32;
-    P->n = n; P->d = d; P->N = N; P->m = m; P->p = p; P->prec = prec;
-    P->sigma = sigma; P->eps_B = eps_B; P->stream = stream;
-    P->ngrid = 2 * N;
+    P->n = B.n; P->d = B.d; P->N = B.N; P->m = B.m; P->p = B.p; P->prec = prec;
+    P->sigma = B.sigma; P->eps_B = B.eps_B; P->stream = B.stream;
+    P->kernel = B.kernel;
+    P->ngrid = 2 * B.N;
     P->kb_b = M_PI * (2.0 - 1.0 / 2.0);
-    P->kb_inv_sinh_bm = 1.0 / -std::expm1(-2.0 * P->kb_b * m);   // 1 / (1 - e^{-2 b m})
+    P->kb_inv_sinh_bm = 1.0 / -std::expm1(-2.0 * P->kb_b * B.m);   // 1 / (1 - e^{-2 b m})
     window_poly(*P);
     int dev = 0;
     NFL_STATUS_TRY(cudaGetDevice(&dev));
@@ -697,47 +745,54 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
     NFL_STATUS_TRY(cudaMalloc(&P->scratch, 64 * sizeof(double)));
     NFL_STATUS_TRY(cudaMalloc(&P->error_flag, sizeof(int)));
     NFL_STATUS_TRY(cudaMalloc(&P->work_counter, 2 * sizeof(unsigned)));
-    NFL_STATUS_TRY(cudaMemsetAsync(P->error_flag, 0, sizeof(int), stream));
+    NFL_STATUS_TRY(cudaMemsetAsync(P->error_flag, 0, sizeof(int), B.stream));
+    NFL_STATUS_TRY(cudaMalloc(&B.part, kRBlocks * 6 * sizeof(double)));
+    NFL_STATUS_TRY(cudaHostAlloc(&B.hp, kRBlocks * 6 * sizeof(double), cudaHostAllocDefault));
+    bbox_partials<<<kRBlocks, 256, 0, B.stream>>>(B.v, B.n, B.d, B.part);
+    NFL_STATUS_TRY(cudaMemcpyAsync(B.hp, B.part, kRBlocks * 6 * sizeof(double), cudaMemcpyDeviceToHost, B.stream));
+    return NFL_OK;
+}
 
-    const int rblocks = 1024;
-    double *part = nullptr;
-    NFL_STATUS_TRY(cudaMalloc(&part, rblocks * 6 * sizeof(double)));
-    std::vector<double> hp(rblocks * 6);
-    // step 1: bounding box, centre, radius, rho
-    bbox_partials<<<rblocks, 256, 0, stream>>>(v, n, d, part);
-    cudaError_t ce = cudaMemcpyAsync(hp.data(), part, rblocks * 6 * sizeof(double), cudaMemcpyDeviceToHost, stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
-    if (ce != cudaSuccess) { cudaFree(part); return NFL_ERR_CUDA; }
-    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    for (int a = 0; a < d; ++a) {
-        lo[a] = INFINITY;
-        hi[a] = -INFINITY;
+// Step 1: bounding box and centre; radius partials.
+static nfl_status phase_radius(Builder &B) {
+    Plan *P = B.P;
+    const double *hp = B.hp;
+    for (int a = 0; a < B.d; ++a) {
+        B.lo[a] = INFINITY;
+        B.hi[a] = -INFINITY;
         bool bad = false;   // a block saw a non-finite coordinate (fmin/fmax would drop NaN)
-        for (int b = 0; b < rblocks; ++b) {
+        for (int b = 0; b < kRBlocks; ++b) {
             bad = bad || std::isnan(hp[b * 6 + a]) || std::isnan(hp[b * 6 + 3 + a]);
-            lo[a] = std::fmin(lo[a], hp[b * 6 + a]);
-            hi[a] = std::fmax(hi[a], hp[b * 6 + 3 + a]);
+            B.lo[a] = std::fmin(B.lo[a], hp[b * 6 + a]);
+            B.hi[a] = std::fmax(B.hi[a], hp[b * 6 + 3 + a]);
         }
-        if (bad || !std::isfinite(lo[a]) || !std::isfinite(hi[a])) { cudaFree(part); return NFL_ERR_INVALID_ARG; }
-        P->center[a] = 0.5 * (lo[a] + hi[a]);
+        if (bad || !std::isfinite(B.lo[a]) || !std::isfinite(B.hi[a])) return NFL_ERR_INVALID_ARG;
+        P->center[a] = 0.5 * (B.lo[a] + B.hi[a]);
     }
-    radius_partials<<<rblocks, 256, 0, stream>>>(v, n, d, P->center[0], P->center[1], P->center[2], part);
-    ce = cudaMemcpyAsync(hp.data(), part, rblocks * sizeof(double), cudaMemcpyDeviceToHost, stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
-    if (ce != cudaSuccess) { cudaFree(part); return NFL_ERR_CUDA; }
+    radius_partials<<<kRBlocks, 256, 0, B.stream>>>(B.v, B.n, B.d, P->center[0], P->center[1], P->center[2], B.part);
+    NFL_STATUS_TRY(cudaMemcpyAsync(B.hp, B.part, kRBlocks * sizeof(double), cudaMemcpyDeviceToHost, B.stream));
+    return NFL_OK;
+}
+
+// Steps 1-2: rho and sigma~; the active box, tiles, and the counting sort of the nodes.
+static nfl_status phase_sort(Builder &B) {
+    Plan *P = B.P;
+    const int d = B.d, m = B.m;
+    const int64_t n = B.n;
+    const cudaStream_t stream = B.stream;
     double r2 = 0.0;
-    for (int b = 0; b < rblocks; ++b) r2 = std::fmax(r2, hp[b]);
+    for (int b = 0; b < kRBlocks; ++b) r2 = std::fmax(r2, B.hp[b]);
     const double radius = std::sqrt(r2);
-    P->rho = radius > 0.0 ? (0.25 - 0.5 * eps_B) / radius : 1.0;   // all nodes coincide: any rho fits
-    P->sigma_t = P->rho * sigma;                                    // step 2
+    P->rho = radius > 0.0 ? (0.25 - 0.5 * B.eps_B) / radius : 1.0;   // all nodes coincide: any rho fits
+    P->sigma_t = P->rho * B.sigma;                                   // step 2
     // the scaled kernel is rho^(+-1) times the caller's for the multiquadrics
-    P->kernel = kernel;
+    const int kernel = B.kernel;
     P->out_scale = kernel == NFL_KERNEL_MULTIQUADRIC ? 1.0 / P->rho
                    : ((kernel == NFL_KERNEL_INV_MULTIQUADRIC || kernel == NFL_KERNEL_GAUSSIAN_DSIGMA) ? P->rho : 1.0);
-    P->k0 = kernel_value(kernel, 0.0, sigma);
+    P->k0 = kernel_value(kernel, 0.0, B.sigma);
 
     // active box: cells floor(n v~) - t0 with t0 leaving m taps (and one cell) of room
-    Geometry G{};
+    Geometry &G = B.G;
     G.d = d;
     G.rho = P->rho;
     G.ngrid = P->ngrid;
@@ -749,20 +804,19 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
     G.tile_edge = P->tile_edge;
     P->box_elems = 1;
     for (int a = 0; a < d; ++a) {
-        const double umin = P->ngrid * (P->rho * (lo[a] - P->center[a]));
-        const double umax = P->ngrid * (P->rho * (hi[a] - P->center[a]));
+        const double umin = P->ngrid * (P->rho * (B.lo[a] - P->center[a]));
+        const double umax = P->ngrid * (P->rho * (B.hi[a] - P->center[a]));
         const int64_t bmin = (int64_t)std::floor(umin), bmax = (int64_t)std::floor(umax);
         P->t0[a] = bmin - (m - 1) - 1;
         G.t0[a] = P->t0[a];
         const int64_t span = bmax - P->t0[a] + m + 2;   // box positions touched, unwrapped
-        if (span > 1023) { cudaFree(part); return NFL_ERR_INVALID_ARG; }
+        if (span > 1023) return NFL_ERR_INVALID_ARG;
         P->wrap[a] = span > P->ngrid ? 1 : 0;
         P->L[a] = (int)(span > P->ngrid ? P->ngrid : span);
         P->ntile[a] = (int)((span + P->tile_edge - 1) / P->tile_edge);
         G.ntile[a] = P->ntile[a];
         P->box_elems *= P->L[a];
     }
-    cudaFree(part);
     P->tiles_total = 1;
     for (int a = 0; a < d; ++a) P->tiles_total *= P->ntile[a];
 
@@ -771,80 +825,93 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
     int cpt = 1;
     for (int a = 0; a < d; ++a) cpt *= P->tile_edge;
     if (nt * cpt > (int64_t)1 << 26) cpt = 1;   // very large grids: sort by tile only
+    B.cpt = cpt;
     const int64_t nkeys = nt * cpt;
-    int32_t *key_of = nullptr, *rank = nullptr, *kcount = nullptr, *count = nullptr, *chunks = nullptr;
-    int64_t *kstart = nullptr, *start = nullptr, *item_off = nullptr;
-    unsigned long long *nonempty = nullptr;
-    auto cleanup = [&]() {
-        cudaFree(key_of); cudaFree(rank); cudaFree(kcount); cudaFree(count); cudaFree(chunks);
-        cudaFree(kstart); cudaFree(start); cudaFree(item_off); cudaFree(nonempty);
-    };
-    if (cudaMalloc(&key_of, n * 4) != cudaSuccess || cudaMalloc(&rank, n * 4) != cudaSuccess ||
-        cudaMalloc(&kcount, nkeys * 4) != cudaSuccess || cudaMalloc(&kstart, (nkeys + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&count, nt * 4) != cudaSuccess || cudaMalloc(&chunks, nt * 4) != cudaSuccess ||
-        cudaMalloc(&start, (nt + 1) * 8) != cudaSuccess || cudaMalloc(&item_off, (nt + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&nonempty, 8) != cudaSuccess) {
-        cleanup();
+    if (cudaMalloc(&B.key_of, n * 4) != cudaSuccess || cudaMalloc(&B.rank, n * 4) != cudaSuccess ||
+        cudaMalloc(&B.kcount, nkeys * 4) != cudaSuccess || cudaMalloc(&B.kstart, (nkeys + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&B.count, nt * 4) != cudaSuccess || cudaMalloc(&B.chunks, nt * 4) != cudaSuccess ||
+        cudaMalloc(&B.start, (nt + 1) * 8) != cudaSuccess || cudaMalloc(&B.item_off, (nt + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&B.nonempty, 8) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
-    }
-    const bool dbl = points_are_double(prec);
+    const bool dbl = points_are_double(P->prec);
     if (cudaMalloc(&P->pts, n * (dbl ? sizeof(PointD) : sizeof(PointF))) != cudaSuccess ||
         cudaMalloc(&P->perm, n * 4) != cudaSuccess || cudaMalloc(&P->dinv_sorted, n * 8) != cudaSuccess ||
         cudaMalloc(&P->degree, n * 8) != cudaSuccess || cudaMalloc(&P->xsort, n * 8) != cudaSuccess ||
-        cudaMalloc(&P->xsorted, n * 8) != cudaSuccess) {
-        cleanup();
+        cudaMalloc(&P->xsorted, n * 8) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
-    }
     const int blocks = P->num_sms * 8;
-    ce = cudaMemsetAsync(kcount, 0, nkeys * 4, stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(nonempty, 0, 8, stream);
-    if (ce != cudaSuccess) { cleanup(); return NFL_ERR_CUDA; }
-    count_keys<<<blocks, 256, 0, stream>>>(v, n, G, cpt, key_of, rank, kcount);
-    exclusive_scan<<<1, 1024, 0, stream>>>(kcount, nkeys, kstart);
-    tiles_from_keys<<<blocks, 256, 0, stream>>>(kstart, nt, cpt, count, start);
-    if (dbl) scatter_nodes<PointD, double><<<blocks, 256, 0, stream>>>(v, n, G, key_of, rank, kstart, (PointD *)P->pts, P->perm);
-    else scatter_nodes<PointF, float><<<blocks, 256, 0, stream>>>(v, n, G, key_of, rank, kstart, (PointF *)P->pts, P->perm);
-    chunks_per_tile<<<blocks, 256, 0, stream>>>(count, nt, chunks, nonempty);
-    exclusive_scan<<<1, 1024, 0, stream>>>(chunks, nt, item_off);
-    unsigned long long h_nonempty = 0;
-    ce = cudaMemcpyAsync(&P->nitems, item_off + nt, 8, cudaMemcpyDeviceToHost, stream);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_nonempty, nonempty, 8, cudaMemcpyDeviceToHost, stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
-    if (ce != cudaSuccess) { cleanup(); return NFL_ERR_CUDA; }
-    P->tiles_nonempty = (int64_t)h_nonempty;
+    NFL_STATUS_TRY(cudaMemsetAsync(B.kcount, 0, nkeys * 4, stream));
+    NFL_STATUS_TRY(cudaMemsetAsync(B.nonempty, 0, 8, stream));
+    count_keys<<<blocks, 256, 0, stream>>>(B.v, n, G, cpt, B.key_of, B.rank, B.kcount);
+    exclusive_scan<<<1, 1024, 0, stream>>>(B.kcount, nkeys, B.kstart);
+    tiles_from_keys<<<blocks, 256, 0, stream>>>(B.kstart, nt, cpt, B.count, B.start);
+    if (dbl) scatter_nodes<PointD, double><<<blocks, 256, 0, stream>>>(B.v, n, G, B.key_of, B.rank, B.kstart,
+                                                                       (PointD *)P->pts, P->perm);
+    else scatter_nodes<PointF, float><<<blocks, 256, 0, stream>>>(B.v, n, G, B.key_of, B.rank, B.kstart,
+                                                                  (PointF *)P->pts, P->perm);
+    chunks_per_tile<<<blocks, 256, 0, stream>>>(B.count, nt, B.chunks, B.nonempty);
+    exclusive_scan<<<1, 1024, 0, stream>>>(B.chunks, nt, B.item_off);
+    NFL_STATUS_TRY(cudaMemcpyAsync(B.hp, B.item_off + nt, 8, cudaMemcpyDeviceToHost, stream));
+    NFL_STATUS_TRY(cudaMemcpyAsync(B.hp + 1, B.nonempty, 8, cudaMemcpyDeviceToHost, stream));
+    return cudaGetLastError() == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+}
+
+// The work items (tile chunks) and tile starts; the chunks are read back.
+static nfl_status phase_items(Builder &B) {
+    Plan *P = B.P;
+    const cudaStream_t stream = B.stream;
+    std::memcpy(&P->nitems, B.hp, 8);
+    unsigned long long ne = 0;
+    std::memcpy(&ne, B.hp + 1, 8);
+    P->tiles_nonempty = (int64_t)ne;
+    const int64_t nt = P->tiles_total;
     if (cudaMalloc(&P->items, std::max<int64_t>(P->nitems, 1) * sizeof(WorkItem)) != cudaSuccess ||
-        cudaMalloc(&P->tile_start, (nt + 1) * sizeof(int32_t)) != cudaSuccess) {
-        cleanup();
+        cudaMalloc(&P->tile_start, (nt + 1) * sizeof(int32_t)) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
-    }
-    fill_items<<<blocks, 256, 0, stream>>>(count, start, item_off, nt, P->items);
-    tile_starts<<<blocks, 256, 0, stream>>>(kstart, nt, cpt, P->tile_start);
-    ce = cudaGetLastError();
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
-    cleanup();
-    if (ce != cudaSuccess) return NFL_ERR_CUDA;
-    {
+    const int blocks = P->num_sms * 8;
+    fill_items<<<blocks, 256, 0, stream>>>(B.count, B.start, B.item_off, nt, P->items);
+    tile_starts<<<blocks, 256, 0, stream>>>(B.kstart, nt, B.cpt, P->tile_start);
+    // room for the sorted chunks and the spread items (at most one per chunk) to upload
+    NFL_STATUS_TRY(cudaHostAlloc(&B.hitems, std::max<int64_t>(2 * P->nitems, 1) * sizeof(WorkItem),
+                                 cudaHostAllocDefault));
+    if (P->nitems > 0)
+        NFL_STATUS_TRY(cudaMemcpyAsync(B.hitems, P->items, P->nitems * sizeof(WorkItem), cudaMemcpyDeviceToHost,
+                                       stream));
+    return cudaGetLastError() == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+}
+
+// Work lists, FFT buffers, twiddles; step 3 (coefficients) and step 4 (degrees, one
+// fast product with x = 1); the degree partials are read back.
+static nfl_status phase_finish(Builder &B) {
+    Plan *P = B.P;
+    const cudaStream_t stream = B.stream;
+    const int64_t n = B.n;
+    const int N = B.N, d = B.d;
+    const int prec = P->prec;
+    if (P->nitems > 0) {
         // largest chunks first: the kernels that take items from a shared counter
         // then end with small ones (longest-processing-time order)
-        std::vector<WorkItem> h(P->nitems);
-        const auto by_size = [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; };
-        if (P->nitems > 0) {
-            ce = cudaMemcpy(h.data(), P->items, P->nitems * sizeof(WorkItem), cudaMemcpyDeviceToHost);
-            if (ce != cudaSuccess) return NFL_ERR_CUDA;
-            P->tile_items = h;
-            const nfl_status sst = rebuild_spread_items(*P);
-            if (sst != NFL_OK) return sst;
-            std::stable_sort(h.begin(), h.end(), by_size);
-            ce = cudaMemcpy(P->items, h.data(), P->nitems * sizeof(WorkItem), cudaMemcpyHostToDevice);
-            if (ce != cudaSuccess) return NFL_ERR_CUDA;
-        }
+        P->tile_items.assign(B.hitems, B.hitems + P->nitems);
+        const std::vector<WorkItem> s = spread_item_list(*P);
+        if (cudaMalloc(&P->sitems, std::max<size_t>(s.size(), 1) * sizeof(WorkItem)) != cudaSuccess)
+            return NFL_ERR_OUT_OF_MEMORY;
+        P->nsitems = (int64_t)s.size();
+        std::vector<WorkItem> h = P->tile_items;
+        std::stable_sort(h.begin(), h.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
+        std::copy(h.begin(), h.end(), B.hitems);
+        std::copy(s.begin(), s.end(), B.hitems + P->nitems);
+        NFL_STATUS_TRY(cudaMemcpyAsync(P->items, B.hitems, P->nitems * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                                       stream));
+        if (!s.empty())
+            NFL_STATUS_TRY(cudaMemcpyAsync(P->sitems, B.hitems + P->nitems, s.size() * sizeof(WorkItem),
+                                           cudaMemcpyHostToDevice, stream));
     }
 
     // FFT buffers, twiddles, multiplier
     const bool fd = fft_is_double(prec);
     const size_t real_sz = fd ? 8 : 4, cplx_sz = 2 * real_sz;
     const int64_t Kh = N / 2 + 1, K0 = N + 1;
-    const int64_t L0 = P->L[0], L1 = P->L[1], L2 = P->L[2];
+    const int64_t L0 = P->L[0], L1 = P->L[1];
     int64_t bufA = 1, bufB = 1, mult = K0;
     if (d == 2) { bufA = Kh * L0; bufB = Kh * L0; mult = Kh * K0; }
     if (d == 3) {
@@ -869,41 +936,100 @@ static nfl_status plan_create_impl(const double *v, int64_t n, int d, int kernel
         cudaMalloc(&P->g, P->box_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
         cudaMalloc(&P->twiddle, (P->ngrid / 2) * cplx_sz) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
-    {
-        const int half = P->ngrid / 2;
-        std::vector<double> tw(2 * half);
+    // page-locked table: twiddles (ngrid / 2 complex), cosine table (N), deconvolution (N / 2 + 1)
+    const int half = P->ngrid / 2;
+    NFL_STATUS_TRY(cudaHostAlloc(&B.htab, (2 * half + N + Kh) * sizeof(double), cudaHostAllocDefault));
+    if (fd) {
         for (int q = 0; q < half; ++q) {
-            tw[2 * q] = std::cos(2.0 * M_PI * q / P->ngrid);
-            tw[2 * q + 1] = -std::sin(2.0 * M_PI * q / P->ngrid);
+            B.htab[2 * q] = std::cos(2.0 * M_PI * q / P->ngrid);
+            B.htab[2 * q + 1] = -std::sin(2.0 * M_PI * q / P->ngrid);
         }
-        if (fd) {
-            NFL_STATUS_TRY(cudaMemcpy(P->twiddle, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
-        } else {
-            std::vector<float> twf(tw.begin(), tw.end());
-            NFL_STATUS_TRY(cudaMemcpy(P->twiddle, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice));
+        NFL_STATUS_TRY(cudaMemcpyAsync(P->twiddle, B.htab, 2 * half * 8, cudaMemcpyHostToDevice, stream));
+    } else {
+        float *tf = reinterpret_cast<float *>(B.htab);
+        for (int q = 0; q < half; ++q) {
+            tf[2 * q] = static_cast<float>(std::cos(2.0 * M_PI * q / P->ngrid));
+            tf[2 * q + 1] = static_cast<float>(-std::sin(2.0 * M_PI * q / P->ngrid));
         }
+        NFL_STATUS_TRY(cudaMemcpyAsync(P->twiddle, B.htab, 2 * half * 4, cudaMemcpyHostToDevice, stream));
     }
-    nfl_status st = compute_coefficients(*P);   // step 3
+    nfl_status st = coefficients_launch(*P, B.htab + 2 * half, B.S, B.T1, B.ctab, B.dec);   // step 3
     if (st != NFL_OK) return st;
 
     // step 4: degrees through the fast path with x = 1
     st = run_column(*P, OP_DEGREE, nullptr, nullptr);
     if (st != NFL_OK) return st;
-    double *mm = nullptr;
-    NFL_STATUS_TRY(cudaMalloc(&mm, rblocks * 2 * sizeof(double)));
-    minmax_partials<<<rblocks, 256, 0, stream>>>(P->degree, n, mm);
-    ce = cudaMemcpyAsync(hp.data(), mm, rblocks * 2 * sizeof(double), cudaMemcpyDeviceToHost, stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
-    cudaFree(mm);
-    if (ce != cudaSuccess) return NFL_ERR_CUDA;
+    minmax_partials<<<kRBlocks, 256, 0, stream>>>(P->degree, n, B.part);
+    NFL_STATUS_TRY(cudaMemcpyAsync(B.hp, B.part, kRBlocks * 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    return cudaGetLastError() == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
+}
+
+// Degree summary (Lemma 3.1: A and L_s need min d_E > 0).
+static nfl_status phase_summary(Builder &B) {
+    Plan *P = B.P;
     P->min_deg = INFINITY;
     P->max_deg = -INFINITY;
-    for (int b = 0; b < rblocks; ++b) {
-        P->min_deg = std::fmin(P->min_deg, hp[2 * b]);
-        P->max_deg = std::fmax(P->max_deg, hp[2 * b + 1]);
+    for (int b = 0; b < kRBlocks; ++b) {
+        P->min_deg = std::fmin(P->min_deg, B.hp[2 * b]);
+        P->max_deg = std::fmax(P->max_deg, B.hp[2 * b + 1]);
     }
     P->degree_ok = P->min_deg > 0.0 && std::isfinite(P->max_deg);
     return NFL_OK;
+}
+
+// Runs every phase for all builders, with one synchronization of the streams in
+// use between phases; a builder that fails skips the later phases.  Temporaries
+// are released at the end (after the streams have passed them).
+static void run_phases(std::vector<Builder> &Bs) {
+    typedef nfl_status (*Phase)(Builder &);
+    const Phase phases[] = {phase_setup, phase_radius, phase_sort, phase_items, phase_finish, phase_summary};
+    std::vector<cudaStream_t> streams;
+    for (const Builder &B : Bs)
+        if (std::find(streams.begin(), streams.end(), B.stream) == streams.end()) streams.push_back(B.stream);
+    for (Phase ph : phases) {
+        for (Builder &B : Bs)
+            if (B.st == NFL_OK) B.st = ph(B);
+        for (cudaStream_t s : streams) {
+            if (cudaStreamSynchronize(s) == cudaSuccess) continue;
+            for (Builder &B : Bs)
+                if (B.stream == s && B.st == NFL_OK) B.st = NFL_ERR_CUDA;
+        }
+    }
+    for (Builder &B : Bs) release_temporaries(B);
+}
+
+// Argument checks of the create calls; p <= 0 and eps_B < 0 take their defaults.
+static nfl_status check_plan_args(int64_t n, int d, int kernel, double sigma, int N, int m, int &p, double &eps_B,
+                                  int precision) {
+    if (n < 1 || n > 0x7fffffff || d < 1 || d > 3 || kernel < NFL_KERNEL_GAUSSIAN || kernel > NFL_KERNEL_GAUSSIAN_DSIGMA)
+        return NFL_ERR_INVALID_ARG;
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return NFL_ERR_INVALID_ARG;
+    if (N < 4 || N > 512 || (N & (N - 1)) != 0) return NFL_ERR_INVALID_ARG;
+    if (m < 1 || m > kMaxM) return NFL_ERR_INVALID_ARG;
+    if (p <= 0) p = m;
+    if (p > 16) return NFL_ERR_INVALID_ARG;
+    if (eps_B < 0.0) eps_B = double(p) / N;
+    if (!(eps_B < 0.5)) return NFL_ERR_INVALID_ARG;
+    if (precision != NFL_PREC_FP64 && precision != NFL_PREC_FP32 && precision != NFL_PREC_FP32C &&
+        precision != NFL_PREC_BF16W)
+        return NFL_ERR_INVALID_ARG;
+    return NFL_OK;
+}
+
+static void fill_builder(Builder &B, Plan *P, const double *v, int64_t n, int d, int kernel, double sigma, int N,
+                         int m, int p, double eps_B, int precision, cudaStream_t stream) {
+    B.P = P;
+    B.v = v;
+    B.n = n;
+    B.d = d;
+    B.kernel = kernel;
+    B.sigma = sigma;
+    B.N = N;
+    B.m = m;
+    B.p = p;
+    B.eps_B = eps_B;
+    B.prec = precision;
+    B.stream = stream;
 }
 
 }  // namespace nfl
@@ -931,27 +1057,76 @@ nfl_status nfl_plan_create(const double *v, int64_t n, int d, int kernel, double
                            double eps_B, int precision, void *stream, nfl_plan **out) {
     if (!out) return NFL_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!v || n < 1 || n > 0x7fffffff || d < 1 || d > 3 || kernel < NFL_KERNEL_GAUSSIAN ||
-        kernel > NFL_KERNEL_GAUSSIAN_DSIGMA) return NFL_ERR_INVALID_ARG;
-    if (!(sigma > 0.0) || !std::isfinite(sigma)) return NFL_ERR_INVALID_ARG;
-    if (N < 4 || N > 512 || (N & (N - 1)) != 0) return NFL_ERR_INVALID_ARG;
-    if (m < 1 || m > nfl::kMaxM) return NFL_ERR_INVALID_ARG;
-    if (p <= 0) p = m;
-    if (p > 16) return NFL_ERR_INVALID_ARG;
-    if (eps_B < 0.0) eps_B = double(p) / N;
-    if (!(eps_B < 0.5)) return NFL_ERR_INVALID_ARG;
-    if (precision != NFL_PREC_FP64 && precision != NFL_PREC_FP32 && precision != NFL_PREC_FP32C &&
-        precision != NFL_PREC_BF16W)
-        return NFL_ERR_INVALID_ARG;
+    if (!v) return NFL_ERR_INVALID_ARG;
+    const nfl_status ck = nfl::check_plan_args(n, d, kernel, sigma, N, m, p, eps_B, precision);
+    if (ck != NFL_OK) return ck;
     Plan *P = new (std::nothrow) Plan();
     if (!P) return NFL_ERR_OUT_OF_MEMORY;
-    nfl_status st = nfl::plan_create_impl(v, n, d, kernel, sigma, N, m, p, eps_B, precision, (cudaStream_t)stream, P);
-    if (st != NFL_OK) {
+    std::vector<nfl::Builder> Bs(1);
+    nfl::fill_builder(Bs[0], P, v, n, d, kernel, sigma, N, m, p, eps_B, precision, (cudaStream_t)stream);
+    nfl::run_phases(Bs);
+    if (Bs[0].st != NFL_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
         nfl::free_plan(P);
-        return st;
+        return Bs[0].st;
     }
     *out = reinterpret_cast<nfl_plan *>(P);
+    return NFL_OK;
+}
+
+nfl_status nfl_plan_create_batched(int G, const double *const *v, const int64_t *n, int d, int kernel,
+                                   const double *sigma, int N, int m, int p, double eps_B, int precision,
+                                   void *stream, nfl_plan **out) {
+    if (!out || !v || !n || !sigma || G < 1) return NFL_ERR_INVALID_ARG;
+    for (int g = 0; g < G; ++g) out[g] = nullptr;
+    int pg = p;
+    double eg = eps_B;
+    for (int g = 0; g < G; ++g) {
+        if (!v[g]) return NFL_ERR_INVALID_ARG;
+        pg = p;
+        eg = eps_B;
+        const nfl_status ck = nfl::check_plan_args(n[g], d, kernel, sigma[g], N, m, pg, eg, precision);
+        if (ck != NFL_OK) return ck;
+    }
+    nfl::BatchStreams *pool = nfl::batch_streams();
+    if (!pool) return NFL_ERR_CUDA;
+    const cudaStream_t origin = (cudaStream_t)stream;
+    const int K = G < nfl::kBatchStreams ? G : nfl::kBatchStreams;
+    // plans to library streams, largest first to the least loaded, forked from the caller's stream
+    if (cudaEventRecord(pool->fork, origin) != cudaSuccess) return NFL_ERR_CUDA;
+    for (int k = 0; k < K; ++k)
+        if (cudaStreamWaitEvent(pool->s[k], pool->fork, 0) != cudaSuccess) return NFL_ERR_CUDA;
+    std::vector<int> order(G);
+    std::vector<int64_t> load(K, 0);
+    for (int g = 0; g < G; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    std::vector<nfl::Builder> Bs(G);
+    for (int g : order) {
+        const int k = int(std::min_element(load.begin(), load.end()) - load.begin());
+        load[k] += n[g];
+        Plan *P = new (std::nothrow) Plan();
+        if (!P) {
+            for (nfl::Builder &B : Bs) delete B.P;
+            return NFL_ERR_OUT_OF_MEMORY;
+        }
+        nfl::fill_builder(Bs[g], P, v[g], n[g], d, kernel, sigma[g], N, m, pg, eg, precision, pool->s[k]);
+    }
+    nfl::run_phases(Bs);   // every phase ends with the library streams synchronized
+    nfl_status st = NFL_OK;
+    for (const nfl::Builder &B : Bs)
+        if (B.st != NFL_OK) {
+            st = B.st;
+            break;
+        }
+    if (st != NFL_OK) {
+        for (int k = 0; k < K; ++k) cudaStreamSynchronize(pool->s[k]);
+        for (nfl::Builder &B : Bs) nfl::free_plan(B.P);
+        return st;
+    }
+    for (int g = 0; g < G; ++g) {
+        Bs[g].P->stream = origin;
+        out[g] = reinterpret_cast<nfl_plan *>(Bs[g].P);
+    }
     return NFL_OK;
 }
 

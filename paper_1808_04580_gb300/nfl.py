@@ -55,6 +55,8 @@ _L = ctypes.c_int64
 
 SIGNATURES = {
     "nfl_plan_create": (_I, [_P, _L, _I, _I, _D, _I, _I, _I, _D, _I, _P, ctypes.POINTER(_P)]),
+    "nfl_plan_create_batched": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_L), _I, _I, ctypes.POINTER(_D), _I, _I,
+                                     _I, _D, _I, _P, ctypes.POINTER(_P)]),
     "nfl_plan_destroy": (None, [_P]),
     "nfl_plan_info": (_I, [_P, ctypes.POINTER(Info)]),
     "nfl_set_stream": (_I, [_P, _P]),
@@ -157,6 +159,12 @@ class Plan:
                                         float(eps_B), PRECISIONS[precision], _stream(), ctypes.byref(h))
         _check(st, "nfl_plan_create")
         self._h = h
+
+    @classmethod
+    def _wrap(cls, handle, n, d, device):
+        obj = cls.__new__(cls)
+        obj.n, obj.d, obj.device, obj._h = int(n), int(d), device, handle
+        return obj
 
     def close(self):
         if self._h is not None and _LIB is not None:
@@ -382,6 +390,33 @@ class Plan:
 
 
 _OPS = {"W": 0, "A": 1, "Ls": 2}
+
+
+def create_batched(vs, sigma, N, m, p=0, eps_B=-1.0, precision="fp64", kernel="gaussian"):
+    """Plans for a list of node sets in one library call (nfl_plan_create_batched).
+
+    vs: list of (n_g, d) CUDA float64 tensors (same d); sigma: a number or one per
+    set.  Returns the list of Plans, whose stream is the current stream.
+    """
+    G = len(vs)
+    if G == 0:
+        return []
+    vs = [_cuda_f64(v, "v").contiguous() for v in vs]
+    d = int(vs[0].shape[1])
+    if any(v.dim() != 2 or v.shape[1] != d for v in vs):
+        raise ValueError("every node set must be (n_g, d) with the same d")
+    sig = [float(sigma)] * G if np.isscalar(sigma) else [float(s) for s in sigma]
+    if len(sig) != G:
+        raise ValueError("one sigma per node set")
+    arr_v = (_P * G)(*[v.data_ptr() for v in vs])
+    arr_n = (_L * G)(*[int(v.shape[0]) for v in vs])
+    arr_s = (_D * G)(*sig)
+    out = (_P * G)()
+    with torch.cuda.device(vs[0].device):
+        st = _lib().nfl_plan_create_batched(G, arr_v, arr_n, d, KERNELS[kernel], arr_s, int(N), int(m), int(p),
+                                            float(eps_B), PRECISIONS[precision], _stream(), out)
+    _check(st, "nfl_plan_create_batched")
+    return [Plan._wrap(ctypes.c_void_p(out[g]), arr_n[g], d, vs[g].device) for g in range(G)]
 RATE_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
 
 

@@ -150,3 +150,33 @@ def test_first_block_product_under_capture_is_refused():
     graph.replay()
     torch.cuda.synchronize()
     assert float(torch.linalg.norm((x - out.t()) - (x - ref)) / torch.linalg.norm(x - ref)) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32c", 1e-6)])
+def test_create_batched_equals_single_plans(prec, tol):
+    """nfl_plan_create_batched builds the same plans as one nfl_plan_create per node
+    set (same scaling, box, work items and degrees), and the products agree."""
+    from paper_1808_04580_gb300 import NflError, create_batched
+    sizes = [1000, 3700, 15000, 800, 42000, 2500, 1, 2]
+    sig = [0.5, 0.4, 0.5, 0.6, 0.5, 0.45, 0.5, 0.5]
+    clouds = [workloads.gaussian_mixture(n, seed=60 + g) for g, n in enumerate(sizes)]
+    plans = create_batched([gpu(v) for v in clouds], sig, 32, 4, 4, -1.0, prec)
+    for g, (v, s, p) in enumerate(zip(clouds, sig, plans)):
+        q = Plan(gpu(v), s, 32, 4, 4, -1.0, prec)
+        ip, iq = p.info(), q.info()
+        for key in ("n", "rho", "sigma_tilde", "center", "box", "tiles", "work_items", "block_cols", "degree_ok"):
+            assert ip[key] == iq[key], (g, key)
+        np.testing.assert_allclose(p.degree().cpu().numpy(), q.degree().cpu().numpy(), rtol=tol, atol=0)
+        if ip["degree_ok"]:
+            x = gpu(workloads.rhs(sizes[g], seed=80 + g))
+            a, b = p.apply_Ls(x), q.apply_Ls(x)
+            assert float(torch.linalg.norm((x - a) - (x - b)) / torch.linalg.norm(x - b)) < tol, g
+    # one member against the oracle's Alg. 2
+    x = workloads.rhs(sizes[1], seed=81)
+    ref = fastsum.NormalizedFastsum(clouds[1], sig[1], 32, 4, 4).apply_W(x)
+    y = plans[1].apply_W(gpu(x)).cpu().numpy()
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < (1e-10 if prec == "fp64" else 1e-6)
+    # an invalid member: no plan is returned
+    with pytest.raises(NflError) as e:
+        create_batched([gpu(v) for v in clouds[:3]], [0.5, -1.0, 0.5], 32, 4, 4, -1.0, prec)
+    assert e.value.name == "NFL_ERR_INVALID_ARG"

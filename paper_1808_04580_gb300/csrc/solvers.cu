@@ -728,102 +728,216 @@ nfl_status nfl_form_grad_nodes(nfl_plan *plan, const double *v, const double *a,
 // ------------------------------------------------ Alg. 3: Nystrom-Gaussian-NFFT
 namespace nfl {
 
-// Cyclic Jacobi iteration for a symmetric c x c matrix (host, FP64, row-major):
-// A = V diag(lam) V^T, V column j the eigenvector of lam[j].  Plane rotations
-// zero one off-diagonal pair at a time (the classical method; a few sweeps
-// converge quadratically for these small matrices).
-static bool jacobi_eig(std::vector<double> A, int c, std::vector<double> &lam, std::vector<double> &V) {
-    V.assign((size_t)c * c, 0.0);
-    for (int i = 0; i < c; ++i) V[(size_t)i * c + i] = 1.0;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int i = 0; i < c; ++i)
-            for (int j = 0; j < c; ++j) {
-                const double a2 = A[(size_t)i * c + j] * A[(size_t)i * c + j];
-                tot += a2;
-                if (i != j) off += a2;
-            }
-        if (off <= 1e-30 * tot || off == 0.0) {
-            lam.resize(c);
-            for (int i = 0; i < c; ++i) lam[i] = A[(size_t)i * c + i];
-            return true;
-        }
-        for (int p = 0; p < c; ++p)
-            for (int q = p + 1; q < c; ++q) {
-                const double apq = A[(size_t)p * c + q];
-                if (apq == 0.0) continue;
-                const double theta = (A[(size_t)q * c + q] - A[(size_t)p * c + p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
-                for (int k = 0; k < c; ++k) {        // columns p, q
-                    const double akp = A[(size_t)k * c + p], akq = A[(size_t)k * c + q];
-                    A[(size_t)k * c + p] = cs * akp - sn * akq;
-                    A[(size_t)k * c + q] = sn * akp + cs * akq;
-                }
-                for (int k = 0; k < c; ++k) {        // rows p, q
-                    const double apk = A[(size_t)p * c + k], aqk = A[(size_t)q * c + k];
-                    A[(size_t)p * c + k] = cs * apk - sn * aqk;
-                    A[(size_t)q * c + k] = sn * apk + cs * aqk;
-                }
-                for (int k = 0; k < c; ++k) {
-                    const double vkp = V[(size_t)k * c + p], vkq = V[(size_t)k * c + q];
-                    V[(size_t)k * c + p] = cs * vkp - sn * vkq;
-                    V[(size_t)k * c + q] = sn * vkp + cs * vkq;
-                }
-            }
+// Pair t of round r of the round-robin ordering on cp players (cp even): every
+// pair of players meets once in the cp - 1 rounds, and the pairs of a round are
+// disjoint.
+__device__ __forceinline__ void rr_pair(int r, int t, int cp, int *p, int *q) {
+    if (t == 0) {
+        *p = r % (cp - 1);
+        *q = cp - 1;
+    } else {
+        *p = (r + t) % (cp - 1);
+        *q = (r - t + cp - 1) % (cp - 1);
     }
-    return false;
 }
 
-// Orthonormalize the c columns of X (n x c, column-major, in place) by
-// Gram-Schmidt with one reorthogonalization (DGKS).  R (host, c x c, row-major,
-// upper triangular) receives X_in = X_out R; a column that falls below 1e-13
-// of its norm is dependent and becomes zero (R_jj = 0).
-static nfl_status gs_qr(Plan &P, double *X, int c, double *part, double *sc, std::vector<double> &R) {
+// Eigen-decomposition of a symmetric c x c matrix A (column-major, overwritten),
+// one CTA: cyclic Jacobi sweeps in the parallel ordering (each round rotates the
+// c/2 disjoint pairs of the round-robin schedule at once, A <- J^T A J with J the
+// product of the round's plane rotations, each chosen to zero its A_pq), until the
+// off-diagonal part is below 1e-30 of A in the squared Frobenius norm (60 sweeps
+// at most).  Then the eigenvalues are ranked in descending order and the first
+// `keep` are written to vals with their eigenvectors as the columns of vecs
+// (c x keep, column-major).  V is c x c workspace.  info[0] = 1 when the sweeps
+// did not converge, info[1] = 1 when a kept eigenvalue is not positive (with
+// require_positive), info[2] = 1 when A held a NaN or Inf.
+__global__ void __launch_bounds__(1024) jacobi_eig_kernel(double *A, int c, double *V, int keep, int require_positive,
+                                                          double *vals, double *vecs, int *info) {
+    extern __shared__ double sh[];
+    const int cp = c + (c & 1), np = cp / 2;
+    double *cs = sh, *sn = sh + np;
+    __shared__ double red_off[1024], red_tot[1024];
+    __shared__ int stop;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < c * c; e += nt) V[e] = (e % c == e / c) ? 1.0 : 0.0;
+    __syncthreads();
+    int sweep = 0;
+    for (; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < c * c; e += nt) {
+            const double a2 = A[e] * A[e];
+            tot += a2;
+            if (e % c != e / c) off += a2;
+        }
+        red_off[tid] = off;
+        red_tot[tid] = tot;
+        __syncthreads();
+        for (int h = nt / 2; h > 0; h >>= 1) {
+            if (tid < h) {
+                red_off[tid] += red_off[tid + h];
+                red_tot[tid] += red_tot[tid + h];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const double o = red_off[0], t = red_tot[0];
+            stop = !isfinite(t) ? 2 : ((o <= 1e-30 * t || o == 0.0) ? 1 : 0);
+        }
+        __syncthreads();
+        if (stop) break;
+        for (int r = 0; r < cp - 1; ++r) {
+            for (int t = tid; t < np; t += nt) {
+                int p, q;
+                rr_pair(r, t, cp, &p, &q);
+                double cv = 1.0, sv = 0.0;
+                if (p < c && q < c) {
+                    const double apq = A[p + (int64_t)q * c];
+                    if (apq != 0.0) {
+                        const double theta = (A[q + (int64_t)q * c] - A[p + (int64_t)p * c]) / (2.0 * apq);
+                        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        cv = 1.0 / sqrt(tt * tt + 1.0);
+                        sv = tt * cv;
+                    }
+                }
+                cs[t] = cv;
+                sn[t] = sv;
+            }
+            __syncthreads();
+            // rows p, q of A (A <- J^T A)
+            for (int e = tid; e < np * c; e += nt) {
+                const int t = e / c, k = e - t * c;
+                int p, q;
+                rr_pair(r, t, cp, &p, &q);
+                if (p >= c || q >= c) continue;
+                const double apk = A[p + (int64_t)k * c], aqk = A[q + (int64_t)k * c];
+                A[p + (int64_t)k * c] = cs[t] * apk - sn[t] * aqk;
+                A[q + (int64_t)k * c] = sn[t] * apk + cs[t] * aqk;
+            }
+            __syncthreads();
+            // columns p, q of A and V (A <- A J, V <- V J)
+            for (int e = tid; e < np * c; e += nt) {
+                const int t = e / c, k = e - t * c;
+                int p, q;
+                rr_pair(r, t, cp, &p, &q);
+                if (p >= c || q >= c) continue;
+                const double akp = A[k + (int64_t)p * c], akq = A[k + (int64_t)q * c];
+                A[k + (int64_t)p * c] = cs[t] * akp - sn[t] * akq;
+                A[k + (int64_t)q * c] = sn[t] * akp + cs[t] * akq;
+                const double vkp = V[k + (int64_t)p * c], vkq = V[k + (int64_t)q * c];
+                V[k + (int64_t)p * c] = cs[t] * vkp - sn[t] * vkq;
+                V[k + (int64_t)q * c] = sn[t] * vkp + cs[t] * vkq;
+            }
+            __syncthreads();
+        }
+    }
+    // rank of eigenvalue i in descending order (ties by index), keep the first `keep`
+    for (int i = tid; i < c; i += nt) {
+        const double li = A[i + (int64_t)i * c];
+        int rank = 0;
+        for (int j = 0; j < c; ++j) {
+            const double lj = A[j + (int64_t)j * c];
+            rank += (lj > li || (lj == li && j < i)) ? 1 : 0;
+        }
+        if (rank < keep) {
+            vals[rank] = li;
+            for (int k = 0; k < c; ++k) vecs[k + (int64_t)rank * c] = V[k + (int64_t)i * c];
+            if (require_positive && !(li > 0.0)) atomicExch(&info[1], 1);
+        }
+    }
+    if (tid == 0) {
+        if (stop == 2) info[2] = 1;
+        else if (!stop) info[0] = 1;
+    }
+}
+
+// B = (B + B^T) / 2 for a c x c matrix (column-major).
+__global__ void symmetrize(double *B, int c) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
+        const int i = e % c, j = e / c;
+        if (i < j) {
+            const double a = 0.5 * (B[i + (int64_t)j * c] + B[j + (int64_t)i * c]);
+            B[i + (int64_t)j * c] = a;
+            B[j + (int64_t)i * c] = a;
+        }
+    }
+}
+
+// R[0..j) of column j += coef[0..j)  (Gram-Schmidt coefficients)
+__global__ void add_coef(double *Rj, const double *coef, int j) {
+    for (int i = threadIdx.x; i < j; i += blockDim.x) Rj[i] += coef[i];
+}
+
+// Column j's norm: R_jj = ||x_j|| unless it fell below 1e-13 of its norm before
+// orthogonalization (n0), in which case the column is dependent (R_jj = 0, and
+// the column is zeroed); scale[0] receives the factor applied to x_j.
+__global__ void gs_norm(double *Rjj, const double *n0, const double *nn, double *scale, int *info) {
+    const double nrm = sqrt(*nn);
+    if (!isfinite(*n0) || !isfinite(*nn)) info[2] = 1;
+    const bool dependent = !(nrm > 1e-13 * sqrt(*n0));
+    *Rjj = dependent ? 0.0 : nrm;
+    *scale = dependent ? 0.0 : 1.0 / nrm;
+}
+
+__global__ void scale_by(double *x, int64_t n, const double *s) {
+    const double f = *s;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= f;
+}
+
+// T = R diag(1 / sig) R^T, R M x M column-major.
+__global__ void form_T(const double *R, const double *sig, int M, double *T) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * M; e += gridDim.x * blockDim.x) {
+        const int i = e % M, j = e / M;
+        double acc = 0.0;
+        for (int t = 0; t < M; ++t) acc += R[i + (int64_t)t * M] * R[j + (int64_t)t * M] / sig[t];
+        T[e] = acc;
+    }
+}
+
+// Orthonormalize the c columns of X (n x c, column-major, in place) by Gram-Schmidt
+// with one reorthogonalization (DGKS), all on the device: R (device, c x c,
+// column-major, upper triangular) receives X_in = X_out R; a column that falls
+// below 1e-13 of its norm is dependent and becomes zero (R_jj = 0).  sc holds
+// c + 4 doubles of workspace.
+static cudaError_t gs_qr(Plan &P, double *X, int c, double *part, double *sc, double *R, int *info) {
     const int64_t n = P.n;
     const cudaStream_t s = P.stream;
     const int vb = vec_blocks(P);
-    R.assign((size_t)c * c, 0.0);
-    std::vector<double> coef(c);
+    double *n0 = sc + c, *nn = sc + c + 1, *scale = sc + c + 2;
+    NFL_CUDA_TRY(cudaMemsetAsync(R, 0, (size_t)c * c * sizeof(double), s));
     for (int j = 0; j < c; ++j) {
         double *xj = X + (int64_t)j * n;
-        double n0 = 0.0;
-        if (dot(P, xj, xj, part, sc, &n0) != cudaSuccess) return NFL_ERR_CUDA;
-        if (!std::isfinite(n0)) return NFL_ERR_NAN;
+        dot_partials<<<kRedBlocks, 256, 0, s>>>(xj, xj, n, part);
+        sum_partials<<<1, 256, 0, s>>>(part, kRedBlocks, 1, n0);
         for (int pass = 0; pass < 2 && j > 0; ++pass) {
             dim3 g(kRedBlocks, j);
             multidot_partials<<<g, 256, 0, s>>>(X, n, xj, part);
             sum_partials<<<std::min(j, 1024), 256, 0, s>>>(part, kRedBlocks, j, sc);
             sub_Qc<<<vb, 256, j * sizeof(double), s>>>(X, n, j, sc, xj);
-            if (cudaMemcpyAsync(coef.data(), sc, j * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return NFL_ERR_CUDA;
-            for (int i = 0; i < j; ++i) R[(size_t)i * c + j] += coef[i];
+            add_coef<<<1, 256, 0, s>>>(R + (int64_t)j * c, sc, j);
         }
-        double nn = 0.0;
-        if (dot(P, xj, xj, part, sc, &nn) != cudaSuccess) return NFL_ERR_CUDA;
-        const double nrm = std::sqrt(nn);
-        const bool dependent = !(nrm > 1e-13 * std::sqrt(n0));
-        R[(size_t)j * c + j] = dependent ? 0.0 : nrm;
-        scale_copy<<<vb, 256, 0, s>>>(xj, xj, n, dependent ? 0.0 : 1.0 / nrm);
+        dot_partials<<<kRedBlocks, 256, 0, s>>>(xj, xj, n, part);
+        sum_partials<<<1, 256, 0, s>>>(part, kRedBlocks, 1, nn);
+        gs_norm<<<1, 1, 0, s>>>(R + (int64_t)j * c + j, n0, nn, scale, info);
+        scale_by<<<vb, 256, 0, s>>>(xj, n, scale);
     }
-    return NFL_OK;
+    return cudaGetLastError();
 }
 
-// Y[:, j] = X R[:, j] for j < ncol_out, X n x c on the device, R host c x ncol_out row-major.
-static nfl_status times_small(Plan &P, const double *X, int c, const std::vector<double> &R, int ncol_out,
-                              double *Y, double *sc) {
-    const int64_t n = P.n;
-    const cudaStream_t s = P.stream;
-    std::vector<double> col(c);
-    for (int j = 0; j < ncol_out; ++j) {
-        for (int i = 0; i < c; ++i) col[i] = R[(size_t)i * ncol_out + j];
-        if (cudaMemcpyAsync(sc, col.data(), c * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return NFL_ERR_CUDA;
-        gemv_Qs<<<vec_blocks(P), 256, c * sizeof(double), s>>>(X, n, c, sc, Y + (int64_t)j * n);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return NFL_ERR_CUDA;
-    }
-    return NFL_OK;
+// Y[:, j] = X S[:, j] for j < ncol, X n x c and S c x ncol (column-major), both on the device.
+static cudaError_t times_small(Plan &P, const double *X, int c, const double *S, int ncol, double *Y) {
+    for (int j = 0; j < ncol; ++j)
+        gemv_Qs<<<vec_blocks(P), 256, c * sizeof(double), P.stream>>>(X, P.n, c, S + (int64_t)j * c,
+                                                                       Y + (int64_t)j * P.n);
+    return cudaGetLastError();
+}
+
+static cudaError_t jacobi(Plan &P, double *A, int c, double *V, int keep, bool positive, double *vals, double *vecs,
+                          int *info) {
+    const int np = (c + 1) / 2;
+    jacobi_eig_kernel<<<1, 1024, 2 * np * sizeof(double), P.stream>>>(A, c, V, keep, positive ? 1 : 0, vals, vecs,
+                                                                      info);
+    return cudaGetLastError();
 }
 
 }  // namespace nfl
@@ -839,12 +953,22 @@ nfl_status nfl_nystrom_k_largest(nfl_plan *plan, int k, int L, int M, const doub
     if (!P.degree_ok) return NFL_ERR_NONPOSITIVE_DEGREE;               // step 2 (degrees of the plan)
     const int64_t n = P.n;
     const cudaStream_t s = P.stream;
-    Dev Yb, Bb, Cb, part, sc;
+    // device: Y, B1 (n x L), C (n x M); the small matrices B2, V (L x L), U_M (L x M),
+    // sig (L), R (L x L), T, Uh (M x M), lam (M), U_k (M x k); status flags
+    Dev Yb, Bb, Cb, part, sc, small, flags;
+    const size_t nsmall = (size_t)4 * L * L + 2 * L + 2 * (size_t)M * M + M + (size_t)M * k + 8;
     if (cudaMalloc(&Yb.buf, (size_t)n * L * 8) != cudaSuccess || cudaMalloc(&Bb.buf, (size_t)n * L * 8) != cudaSuccess ||
         cudaMalloc(&Cb.buf, (size_t)n * M * 8) != cudaSuccess ||
-        cudaMalloc(&part.buf, (size_t)kRedBlocks * L * 8) != cudaSuccess || cudaMalloc(&sc.buf, (size_t)(L + 8) * 8) != cudaSuccess)
+        cudaMalloc(&part.buf, (size_t)kRedBlocks * L * 8) != cudaSuccess ||
+        cudaMalloc(&sc.buf, (size_t)(L + 8) * 8) != cudaSuccess || cudaMalloc(&small.buf, nsmall * 8) != cudaSuccess ||
+        cudaMalloc(&flags.buf, 8 * sizeof(int)) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
     double *Y = Yb.buf, *B1 = Bb.buf, *C = Cb.buf;
+    double *B2 = small.buf, *V = B2 + (size_t)L * L, *UM = V + (size_t)L * L, *sig = UM + (size_t)L * L;
+    double *R = sig + L, *T = R + (size_t)L * L, *Uh = T + (size_t)M * M, *lam = Uh + (size_t)M * M;
+    double *Uk = lam + M;
+    int *info = reinterpret_cast<int *>(flags.buf);
+    NFL_STATUS_TRY(cudaMemsetAsync(info, 0, 8 * sizeof(int), s));
     // step 3: Y = A G column by column, Q = orth(Y) (in place)
     if (G) {
         if (cudaMemcpyAsync(B1, G, (size_t)n * L * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return NFL_ERR_CUDA;
@@ -855,70 +979,35 @@ nfl_status nfl_nystrom_k_largest(nfl_plan *plan, int k, int L, int M, const doub
         nfl_status st = run_column(P, OP_A, B1 + (int64_t)j * n, Y + (int64_t)j * n);
         if (st != NFL_OK) return st;
     }
-    std::vector<double> R;
-    nfl_status st = gs_qr(P, Y, L, part.buf, sc.buf, R);
-    if (st != NFL_OK) return st;
+    NFL_STATUS_TRY(gs_qr(P, Y, L, part.buf, sc.buf, R, info));
     // step 4: B1 = A Q, B2 = Q^T B1 (symmetrized)
     for (int j = 0; j < L; ++j) {
-        st = run_column(P, OP_A, Y + (int64_t)j * n, B1 + (int64_t)j * n);
+        nfl_status st = run_column(P, OP_A, Y + (int64_t)j * n, B1 + (int64_t)j * n);
         if (st != NFL_OK) return st;
     }
-    std::vector<double> B2((size_t)L * L);
     for (int j = 0; j < L; ++j) {
         dim3 g(kRedBlocks, L);
         multidot_partials<<<g, 256, 0, s>>>(Y, n, B1 + (int64_t)j * n, part.buf);
-        sum_partials<<<std::min(L, 1024), 256, 0, s>>>(part.buf, kRedBlocks, L, sc.buf);
-        std::vector<double> col(L);
-        if (cudaMemcpyAsync(col.data(), sc.buf, L * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return NFL_ERR_CUDA;
-        for (int i = 0; i < L; ++i) B2[(size_t)i * L + j] = col[i];
+        sum_partials<<<std::min(L, 1024), 256, 0, s>>>(part.buf, kRedBlocks, L, B2 + (int64_t)j * L);
     }
-    for (int i = 0; i < L; ++i)
-        for (int j = i + 1; j < L; ++j) {
-            const double a = 0.5 * (B2[(size_t)i * L + j] + B2[(size_t)j * L + i]);
-            B2[(size_t)i * L + j] = B2[(size_t)j * L + i] = a;
-        }
-    // step 5: the M largest positive eigenvalues of B2 and their eigenvectors U_M (L x M)
-    std::vector<double> sig, U;
-    if (!jacobi_eig(B2, L, sig, U)) return NFL_ERR_NOT_CONVERGED;
-    std::vector<int> order(L);
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return sig[a] > sig[b]; });
-    std::vector<double> UM((size_t)L * M), sigM(M);
-    for (int t = 0; t < M; ++t) {
-        sigM[t] = sig[order[t]];
-        if (!(sigM[t] > 0.0)) return NFL_ERR_BREAKDOWN;
-        for (int i = 0; i < L; ++i) UM[(size_t)i * M + t] = U[(size_t)i * L + order[t]];
-    }
+    symmetrize<<<std::max(1, (L * L + 255) / 256), 256, 0, s>>>(B2, L);
+    // step 5: the M largest eigenvalues of B2 (all positive) and their eigenvectors U_M (L x M)
+    NFL_STATUS_TRY(jacobi(P, B2, L, V, M, true, sig, UM, info));
     // step 6: Qh Rh = B1 U_M
-    st = times_small(P, B1, L, UM, M, C, sc.buf);
-    if (st != NFL_OK) return st;
-    std::vector<double> Rh;
-    st = gs_qr(P, C, M, part.buf, sc.buf, Rh);
-    if (st != NFL_OK) return st;
+    NFL_STATUS_TRY(times_small(P, B1, L, UM, M, C));
+    NFL_STATUS_TRY(gs_qr(P, C, M, part.buf, sc.buf, R, info));
     // step 7: eig of T = Rh Sigma_M^{-1} Rh^T; V_M = Qh Uh
-    std::vector<double> T((size_t)M * M, 0.0);
-    for (int i = 0; i < M; ++i)
-        for (int j = 0; j < M; ++j) {
-            double acc = 0.0;
-            for (int t = 0; t < M; ++t) acc += Rh[(size_t)i * M + t] * Rh[(size_t)j * M + t] / sigM[t];
-            T[(size_t)i * M + j] = acc;
-        }
-    std::vector<double> lam, Uh;
-    if (!jacobi_eig(T, M, lam, Uh)) return NFL_ERR_NOT_CONVERGED;
-    std::vector<int> ord(M);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+    form_T<<<std::max(1, (M * M + 255) / 256), 256, 0, s>>>(R, sig, M, T);
+    NFL_STATUS_TRY(jacobi(P, T, M, Uh, k, false, lam, Uk, info));
     // step 8: the k largest
-    for (int t = 0; t < k; ++t) evals[t] = lam[ord[t]];
-    if (evecs) {
-        std::vector<double> Uk((size_t)M * k);
-        for (int i = 0; i < M; ++i)
-            for (int t = 0; t < k; ++t) Uk[(size_t)i * k + t] = Uh[(size_t)i * M + ord[t]];
-        st = times_small(P, C, M, Uk, k, evecs, sc.buf);
-        if (st != NFL_OK) return st;
-    }
+    int h_info[8] = {0};
+    NFL_STATUS_TRY(cudaMemcpyAsync(h_info, info, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    NFL_STATUS_TRY(cudaMemcpyAsync(evals, lam, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NFL_STATUS_TRY(cudaStreamSynchronize(s));
+    if (h_info[2]) return NFL_ERR_NAN;
+    if (h_info[0]) return NFL_ERR_NOT_CONVERGED;
+    if (h_info[1]) return NFL_ERR_BREAKDOWN;
+    if (evecs) NFL_STATUS_TRY(times_small(P, C, M, Uk, k, evecs));
     return cudaStreamSynchronize(s) == cudaSuccess ? NFL_OK : NFL_ERR_CUDA;
 }
 

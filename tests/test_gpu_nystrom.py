@@ -59,3 +59,19 @@ def test_invalid_sizes_rejected(cloud):
     for k, L, M in [(0, 10, 5), (6, 10, 5), (5, 4, 5), (5, 600, 10)]:
         with pytest.raises(NflError):
             plan.nystrom_k_largest(k, L, M)
+
+
+@pytest.mark.parametrize("k,L,M", [(3, 37, 9), (5, 64, 21)])
+def test_odd_and_larger_sizes_match_oracle_alg3(cloud, k, L, M):
+    """The device eigensolves of Alg. 3 (steps 5 and 7) at odd orders and L = 64,
+    against the oracle's Alg. 3 with the same random block."""
+    v, _ = cloud
+    G = np.random.default_rng(L).standard_normal((v.shape[0], L))
+    fs = fastsum.NormalizedFastsum(v, 1.0, 32, 4, 4)
+    apply_fast = lambda X: np.stack([fs.apply_A(X[:, j]) for j in range(X.shape[1])], axis=1)
+    lam_ref, _ = spectral.nystrom_gaussian(apply_fast, G, k, M)
+    plan = Plan(gpu(v), 1.0, 32, 4, 4, -1.0, "fp64")
+    lam, V = plan.nystrom_k_largest(k, L, M, G=gpu(G))
+    np.testing.assert_allclose(lam, lam_ref, rtol=1e-9, atol=1e-9)
+    V = V.cpu().numpy()
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-10)

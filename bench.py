@@ -245,7 +245,7 @@ def other_workloads(dev):
     graphs256 (batched plan creation and one captured CUDA graph of 8 columns per graph)."""
     import numpy as np
     import torch
-    from paper_1808_04580_gb300 import Plan, apply_batched, create_batched, workloads
+    from paper_1808_04580_gb300 import Batch, Plan, apply_batched, create_batched, workloads
     stream = torch.cuda.current_stream()
     gpu = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)   # noqa: E731
     # column blocks in column-major storage (the layout the library takes without a copy)
@@ -316,12 +316,42 @@ def other_workloads(dev):
     with torch.cuda.graph(graph, capture_error_mode="thread_local"):
         apply_batched(plans, xs, "Ls", outs=outs)
     ms = _events_ms(graph.replay, 5, stream)
+    # the same products with one launch per stage and part (nfl_batch_run), the members
+    # split into parts that run on parallel library streams
     ncols = 8 * len(plans)
+    sweep = {}
+    for parts in (1, 2, 4, 8):
+        b = Batch(plans, xs, "Ls", parts=parts)
+        b.run()
+        torch.cuda.synchronize()
+        graph_b = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph_b, capture_error_mode="thread_local"):
+            b.run()
+        ms_b = _events_ms(graph_b.replay, 5, stream)
+        b.set_profiling(True)
+        b.run()
+        st = b.stage_times()
+        worst = 0.0
+        for o, x, y in zip(b.outputs, xs, outs):
+            a1, a2 = x - o, x - y.t()
+            worst = max(worst, float(torch.linalg.norm(a1 - a2) / torch.linalg.norm(a2)))
+        b.close()
+        del graph_b
+        sweep[parts] = {"ms_per_replay": ms_b, "Ls_matvecs_per_s": ncols * 1000.0 / ms_b,
+                        "kernel_launches_per_replay": 8 * parts,
+                        "stage_ms_summed_over_parts": {k: st[k] for k in ("prep", "spread", "fft", "gather")},
+                        "rel_diff_vs_per_plan_products": worst}
+    best = min(sweep, key=lambda k: sweep[k]["ms_per_replay"])
+    out["graphs256_one_launch_per_stage"] = dict(sweep[best], parts=best,
+                                                 point_rhs_per_s=8 * sum(sizes) * 1000.0 / sweep[best]["ms_per_replay"],
+                                                 parts_sweep={k: v["ms_per_replay"] for k, v in sweep.items()},
+                                                 stage_ms_one_part=sweep[1]["stage_ms_summed_over_parts"])
     out["graphs256"] = {"workload": "256 Gaussian-mixture graphs d=3, n log-uniform in [1e3, 2e5] (sum %d), "
                                     "8 right-hand sides each, FP32C, sigma=0.5, N=64, m=4" % sum(sizes),
                         "ms_per_replay": ms, "Ls_matvecs_per_s": ncols * 1000.0 / ms,
                         "point_rhs_per_s": 8 * sum(sizes) * 1000.0 / ms,
                         "launches_per_replay": int(sum(q.kernels(8) for q in plans)),
+                        "api": "nfl_apply_batched: per-plan block products over 16 library streams",
                         "plan_create_batched_s": t_batched, "plan_create_one_by_one_s": t_single}
     for q in plans:
         q.close()

@@ -41,6 +41,7 @@ extern "C" {
 #endif
 
 typedef struct nfl_plan nfl_plan;
+typedef struct nfl_batch nfl_batch;
 
 typedef enum {
     NFL_OK = 0,
@@ -263,6 +264,52 @@ nfl_status nfl_apply_host(nfl_plan *plan, int op, const double *x, int64_t ldx,
  */
 nfl_status nfl_apply_batched(nfl_plan *const *plans, int G, int op, const double *const *x,
                              double *const *y, const int64_t *ld, int nrhs);
+
+/*
+ * A batch of G plans whose products run with one kernel launch per stage and
+ * part (Alg. 1 with the scalings of Alg. 2 step 5 for many independent graphs;
+ * the batching is not a paper construct): y_g = op(x_g), op 0 = W, 1 = A,
+ * 2 = L_s, for every member g, where x_g and y_g are the caller's device blocks
+ * of nrhs columns bound at creation.  The members are split into `parts`
+ * groups of about equal estimated work; a run issues, for each part on its
+ * own library stream (forked from the run's stream and joined back), three
+ * memsets and eight kernels: the staging of x~ and the epilogue's z, the
+ * spread (all the part's (work item, column) pairs from one counter, largest
+ * first), the five FFT passes and the interpolation, each over every member
+ * of the part.  Several parts let the stages of different parts overlap (the
+ * spread and interpolation are FMA-bound, the FFT passes bound by shared
+ * memory).  Members must be 3-D plans of one mixed precision (FP32, FP32C or
+ * BF16W), with the same m in {2, 3, 4, 6} and the same N (NFL_ERR_INVALID_ARG
+ * otherwise), distinct, with positive degrees unless op is W
+ * (NFL_ERR_NONPOSITIVE_DEGREE); they keep their own spread items, and the FFT
+ * passes use the first member's CTA size.  The batch owns its staging, grid
+ * and FFT buffers (per member and column: 12 n bytes, 12 to 16 bytes per box
+ * position and the FFT buffers, all allocated at creation), and refers to
+ * the plans and the caller's blocks, which must outlive it.
+ *   plans, x, y, ldx, ldy   host arrays of G entries; ldx[g], ldy[g] >= n_g.
+ *   nrhs                    columns per member, 1 <= nrhs <= 65535.
+ *   parts                   1 <= parts <= 8 (at most G are used).
+ * nfl_batch_run allocates nothing and does not synchronize the host, so a run
+ * can be captured into a CUDA graph (a DAG of `parts` chains).  Results equal
+ * the members' own products up to the FP32 summation order.  A bounded-wait
+ * timeout in the interpolation sets the device_error flag of the member it
+ * was working on.  nfl_batch_destroy synchronizes the device and frees the
+ * batch's buffers; nfl_batch_parts returns the number of parts.
+ */
+nfl_status nfl_batch_create(nfl_plan *const *plans, int G, int op, const double *const *x, const int64_t *ldx,
+                            double *const *y, const int64_t *ldy, int nrhs, int parts, nfl_batch **out);
+nfl_status nfl_batch_parts(const nfl_batch *batch, int *parts);
+nfl_status nfl_batch_run(nfl_batch *batch, void *stream);
+void nfl_batch_destroy(nfl_batch *batch);
+
+/* Stage timing of a batch's runs (tracing; not a paper construct), as for plans:
+ * when enabled, events bracket the staging (with the memsets), the spread, the
+ * FFT passes and the interpolation of every run; nfl_batch_stage_times
+ * synchronizes the stream of the last run, writes the accumulated ms per stage
+ * into ms[0..3] and the number of timed runs into *runs, and clears them;
+ * with several parts the times are summed over the parts. */
+nfl_status nfl_batch_set_profiling(nfl_batch *batch, int enable);
+nfl_status nfl_batch_stage_times(nfl_batch *batch, double *ms, int64_t *runs);
 
 /*
  * k smallest eigenpairs of L_s, i.e. the k largest of A (Sec. 2), by the

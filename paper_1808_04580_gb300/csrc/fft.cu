@@ -36,23 +36,6 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
-struct PassArgs {
-    const void *in;
-    void *out;
-    int nA, nB;
-    int64_t sA, sB;
-    int Lin;
-    unsigned lin_magic;   // ceil(2^32 / Lin): e / Lin = umulhi(e, lin_magic) for e < 2^22
-    int64_t oC, oA;
-    int Lout;
-    int n, logn, N;
-    int BB;
-    const void *tw;       // e^{-2 pi i q / n}, q < n/2
-    const void *M;        // fused multiplier, index ((b * nA) + a) * (N + 1) + (k + N/2)
-    int real_in, real_out;
-    const double *abs_sum;  // int64 fixed-point input: sum |x~| of the spread call, per column
-    int64_t in_cstride, out_cstride;   // elements between the columns of a block (grid.z)
-};
 
 // Grid value as a real of the FFT type.  int64 fixed point to FP32 through its
 // 32-bit halves (hi 2^32 + lo, both converted exactly or to nearest), which
@@ -141,17 +124,16 @@ __device__ C *stockham(C *x, C *y, int nl, int n, int logn, const C *tw, bool in
 // z = a + i b gives A_k = (Z_k + conj Z_{n-k}) / 2 and B_k = (Z_k - conj Z_{n-k}) / 2i;
 // inverse, Z = A + i B over the Hermitian extension of both half spectra gives
 // a = Re z, b = Im z.
+// One CTA's work of a pass: lines b0 = bxi BB .. of line group ai, column col.
 template <typename T, typename TIN, int MODE>
-__global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
+__device__ __forceinline__ void fft_pass_body(const PassArgs &a, int bxi, int ai, int col) {
     using C = typename Cplx<T>::type;
     constexpr bool PAIR = (MODE == P_FWD_R2C || MODE == P_INV_C2R);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NL = PAIR ? (a.BB + 1) / 2 : a.BB;     // complex lines in shared memory
     C *bx = reinterpret_cast<C *>(smem_raw);
     C *by = bx + NL * a.n;
-    const int col = blockIdx.z;
-    const int ai = blockIdx.y;
-    const int b0 = blockIdx.x * a.BB;
+    const int b0 = bxi * a.BB;
     const int nb = min(a.BB, a.nB - b0);
     const int n = a.n, N = a.N;
     const C *tw = reinterpret_cast<const C *>(a.tw);
@@ -255,6 +237,30 @@ __global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
 }
 
 template <typename T, typename TIN, int MODE>
+__global__ void __launch_bounds__(256) fft_pass(PassArgs a) {
+    fft_pass_body<T, TIN, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// A pass over the plans of a batch in one launch: CTA b belongs to the plan g with
+// start[g] <= b < start[g + 1] and is its (line block, line group, column) in that
+// plan's grid of the per-plan launch.
+template <typename T, typename TIN, int MODE>
+__global__ void __launch_bounds__(256) fft_pass_batch(const PassArgs *args, const int *start, int G) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const PassArgs a = args[lo];
+    const int local = b - start[lo];
+    const int gx = (a.nB + a.BB - 1) / a.BB;
+    const int bxi = local % gx, rest = local / gx;
+    fft_pass_body<T, TIN, MODE>(a, bxi, rest % a.nA, rest / a.nA);
+}
+
+template <typename T, typename TIN, int MODE>
 static cudaError_t run_pass(Plan &P, PassArgs a, int nc) {
     using C = typename Cplx<T>::type;
     // few lines per CTA and one radix-4 butterfly per thread and stage: small CTAs,
@@ -350,6 +356,81 @@ static cudaError_t launch_fft_t(Plan &P, int nc) {
     i1.nA = (int)L1; i1.nB = (int)L0; i1.sA = L0 * K2; i1.sB = K2; i1.Lin = (int)K2;
     i1.oC = L1 * L0; i1.oA = L0; i1.Lout = (int)L2;
     return run_pass<T, T, P_INV_C2R>(P, with_strides(i1), nc);
+}
+
+// Launch shape of a pass of line length n at cap grid points per CTA: complex lines
+// per CTA NL, lines BB (real line pairs for R2C / C2R), threads and shared memory.
+static void pass_shape(int cap, int n, bool pair, size_t csize, int &BB, int &threads, int &smem) {
+    int NL = cap / n;
+    NL = NL > 16 ? 16 : (NL < 1 ? 1 : NL);
+    BB = pair ? 2 * NL : NL;
+    smem = 2 * NL * n * (int)csize;
+    threads = NL * n / 4;
+    threads = threads < 64 ? 64 : (threads > 256 ? 256 : threads);
+}
+
+int fft_passes_3d(const Plan &P, const void *grid, void *bufA, void *bufB, void *g, int64_t sa, int64_t sb, int cap,
+                  PassArgs *out, int nc, int *ctas) {
+    const int N = P.N, n = P.ngrid;
+    int logn = 0;
+    while ((1 << logn) < n) ++logn;
+    PassArgs base{};
+    base.n = n;
+    base.logn = logn;
+    base.N = N;
+    base.tw = P.twiddle;
+    base.M = P.mult;
+    const int64_t L0 = P.L[0], L1 = P.L[1], L2 = P.L[2], sg = P.box_elems;
+    const int64_t K2 = N / 2 + 1, K1 = N + 1;
+    PassArgs *f = out;
+    f[0] = base;
+    f[0].in = grid; f[0].out = bufA; f[0].in_cstride = sg; f[0].out_cstride = sa;
+    f[0].nA = (int)L0; f[0].nB = (int)L1; f[0].sA = L1 * L2; f[0].sB = L2; f[0].Lin = (int)L2;
+    f[0].oC = L0 * L1; f[0].oA = L1; f[0].Lout = (int)K2;
+    f[1] = base;
+    f[1].in = bufA; f[1].out = bufB; f[1].in_cstride = sa; f[1].out_cstride = sb;
+    f[1].nA = (int)K2; f[1].nB = (int)L0; f[1].sA = L0 * L1; f[1].sB = L1; f[1].Lin = (int)L1;
+    f[1].oC = K2 * L0; f[1].oA = L0; f[1].Lout = (int)K1;
+    f[2] = base;
+    f[2].in = bufB; f[2].out = bufA; f[2].in_cstride = sb; f[2].out_cstride = sa;
+    f[2].nA = (int)K2; f[2].nB = (int)K1; f[2].sA = L0; f[2].sB = K2 * L0; f[2].Lin = (int)L0;
+    f[2].oC = K2 * K1; f[2].oA = K1; f[2].Lout = (int)L0;
+    f[3] = base;
+    f[3].in = bufA; f[3].out = bufB; f[3].in_cstride = sa; f[3].out_cstride = sb;
+    f[3].nA = (int)L0; f[3].nB = (int)K2; f[3].sA = K2 * K1; f[3].sB = K1; f[3].Lin = (int)K1;
+    f[3].oC = L0 * K2; f[3].oA = K2; f[3].Lout = (int)L1;
+    f[4] = base;
+    f[4].in = bufB; f[4].out = g; f[4].in_cstride = sb; f[4].out_cstride = sg;
+    f[4].nA = (int)L1; f[4].nB = (int)L0; f[4].sA = L0 * K2; f[4].sB = K2; f[4].Lin = (int)K2;
+    f[4].oC = L1 * L0; f[4].oA = L0; f[4].Lout = (int)L2;
+    for (int i = 0; i < 5; ++i) {
+        int threads = 0, smem = 0;
+        pass_shape(cap, n, i == 0 || i == 4, sizeof(float2), f[i].BB, threads, smem);
+        f[i].lin_magic = (unsigned)((0x100000000ull + (unsigned)f[i].Lin - 1) / (unsigned)f[i].Lin);
+        ctas[i] = ((f[i].nB + f[i].BB - 1) / f[i].BB) * f[i].nA * nc;
+    }
+    return 5;
+}
+
+template <typename TIN, int MODE>
+static cudaError_t batch_pass(Batch &B, int i, cudaStream_t s) {
+    int BB = 0, threads = 0, smem = 0;
+    pass_shape(B.fft_cap, 2 * B.N, MODE == P_FWD_R2C || MODE == P_INV_C2R, sizeof(float2), BB, threads, smem);
+    NFL_CUDA_TRY(cudaFuncSetAttribute(fft_pass_batch<float, TIN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem));
+    if (B.pass_ctas[i] < 1) return cudaSuccess;
+    fft_pass_batch<float, TIN, MODE><<<B.pass_ctas[i], threads, smem, s>>>(B.pass_args[i], B.pass_start[i], B.G);
+    return cudaGetLastError();
+}
+
+// The five passes over every member of a batch, one launch each.
+cudaError_t launch_fft_batch(Batch &B, cudaStream_t s) {
+    if (B.prec == NFL_PREC_FP32C) NFL_CUDA_TRY((batch_pass<long long, P_FWD_R2C>(B, 0, s)));
+    else NFL_CUDA_TRY((batch_pass<float, P_FWD_R2C>(B, 0, s)));
+    NFL_CUDA_TRY((batch_pass<float, P_FWD_C2C>(B, 1, s)));
+    NFL_CUDA_TRY((batch_pass<float, P_FUSED>(B, 2, s)));
+    NFL_CUDA_TRY((batch_pass<float, P_INV_C2C>(B, 3, s)));
+    return batch_pass<float, P_INV_C2R>(B, 4, s);
 }
 
 cudaError_t launch_fft(Plan &P, int nc) {

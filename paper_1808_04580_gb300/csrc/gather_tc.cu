@@ -55,6 +55,8 @@ struct GatherTCArgs {
     unsigned *counter;    // next work item, shared by all CTAs
     int skip_mma;                 // fault test: the MMAs are never issued, so every wait runs out
     unsigned long long wait_ns;   // limit of each bounded wait
+    const BatchPlanDev *bplans;   // batch: the members (item it is bitems[it] of member bitems[it].plan)
+    const BatchItem *bitems;
     float poly[2 * kMaxM][kPolyCoef];   // window by taps, as in the plan
 };
 
@@ -85,8 +87,25 @@ struct TCGeom {
     static constexpr int B_BYTES = NH * N * 64;           // all halves
 };
 
-// BF16: the window taps are rounded to BF16 (the BF16W form)
-template <int M, int TE, bool BF16>
+// Per-item plan fields of a batch, in shared memory (written by thread 0 per item).
+struct GatherItemPlan {
+    const PointF *pts;
+    const int32_t *perm;
+    const double *dinv, *zc;
+    const float *gc;
+    double *yc;
+    double out_scale;
+    int *error_flag;
+    WorkItem w;
+    int ntile[3], L[3], wrap[3];
+};
+
+#define GT_L(i) (BATCH ? ip.L[i] : a.L[i])
+#define GT_WRAP(i) (BATCH ? ip.wrap[i] : a.wrap[i])
+
+// BF16: the window taps are rounded to BF16 (the BF16W form).  BATCH: the items of
+// all members of a batch, each item's plan fields read from its member's descriptor.
+template <int M, int TE, bool BF16, bool BATCH = false>
 __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     using G = TCGeom<M, TE>;
     constexpr int PA = G::PA, N = G::N, NH = G::NH, NCOL = G::NCOL, TAPS = 2 * M;
@@ -101,6 +120,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(16) float2 polys[M][kPolyCoef];   // (tap 2q, tap 2q+1) coefficients
     __shared__ unsigned next_item;
+    __shared__ GatherItemPlan ip;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     for (int e = tid; e < M * kPolyCoef; e += 128) {
@@ -129,18 +149,41 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
 
     while (!failed) {
         // the CTA's next work item (largest first: the plan sorts them by size)
-        if (tid == 0) next_item = atomicAdd(a.counter, 1u);
+        if (tid == 0) {
+            next_item = atomicAdd(a.counter, 1u);
+            if (BATCH && next_item < (unsigned)(a.nitems * a.ncol)) {
+                // the member of this item and its fields
+                const unsigned it0 = next_item / (unsigned)a.ncol;
+                const int c0 = (int)(next_item - it0 * (unsigned)a.ncol);
+                const BatchItem e = a.bitems[it0];
+                const BatchPlanDev &D = a.bplans[e.plan];
+                ip.w = D.items[e.item];
+                ip.pts = D.pts;
+                ip.perm = D.perm;
+                ip.dinv = D.dinv;
+                ip.zc = D.zd + c0 * D.n;
+                ip.gc = D.g + c0 * D.box;
+                ip.yc = D.y + c0 * D.ldy;
+                ip.out_scale = D.out_scale;
+                ip.error_flag = D.error_flag;
+                for (int i = 0; i < 3; ++i) {
+                    ip.ntile[i] = D.ntile[i];
+                    ip.L[i] = D.L[i];
+                    ip.wrap[i] = D.wrap[i];
+                }
+            }
+        }
         __syncthreads();
         const unsigned itc = next_item;
         if (itc >= (unsigned)(a.nitems * a.ncol)) break;
         const unsigned it = a.ncol == 1 ? itc : itc / (unsigned)a.ncol;
         const int col = (int)(itc - it * (unsigned)a.ncol);
-        const float *gc = a.g + col * a.g_stride;
-        const double *zc = a.zd + col * a.z_stride;
-        double *yc = a.y + col * a.ldy;
-        const WorkItem w = a.items[it];
+        const float *gc = BATCH ? ip.gc : a.g + col * a.g_stride;
+        const double *zc = BATCH ? ip.zc : a.zd + col * a.z_stride;
+        double *yc = BATCH ? ip.yc : a.y + col * a.ldy;
+        const WorkItem w = BATCH ? ip.w : a.items[it];
         int tc[3];
-        tile_coords<3>(w.tile, a.ntile, tc);
+        tile_coords<3>(w.tile, BATCH ? ip.ntile : a.ntile, tc);
         // B operand: row n = b PA + c holds G[a][(b, c)] for k = a = 0..15, split into TF32
         // hi/lo parts; zero beyond PA^2 rows, beyond PA along a and outside the box
         for (int n = tid; n < NH * N; n += 128) {
@@ -148,16 +191,16 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
             const int bq = used ? n / PA : 0, cq = used ? n - bq * PA : 0;
             int p1 = tc[1] * TE - (M - 1) + bq;
             int p2 = tc[2] * TE - (M - 1) + cq;
-            if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-            if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-            const bool ok12 = used && p1 >= 0 && p1 < a.L[1] && p2 >= 0 && p2 < a.L[2];
-            const float *src = gc + ((int64_t)(ok12 ? p2 : 0) * a.L[1] + (ok12 ? p1 : 0)) * a.L[0];
+            if (GT_WRAP(1)) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+            if (GT_WRAP(2)) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+            const bool ok12 = used && p1 >= 0 && p1 < GT_L(1) && p2 >= 0 && p2 < GT_L(2);
+            const float *src = gc + ((int64_t)(ok12 ? p2 : 0) * GT_L(1) + (ok12 ? p1 : 0)) * GT_L(0);
             float v[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 int p0 = tc[0] * TE - (M - 1) + k;
-                if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-                v[k] = (ok12 && k < PA && p0 >= 0 && p0 < a.L[0]) ? src[p0] : 0.f;
+                if (GT_WRAP(0)) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                v[k] = (ok12 && k < PA && p0 >= 0 && p0 < GT_L(0)) ? src[p0] : 0.f;
             }
 #pragma unroll
             for (int kb = 0; kb < 4; ++kb) {
@@ -183,11 +226,11 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 int s0 = 0, s1 = 0, s2 = 0;
                 if (live) {
                     kq = base + tid;
-                    const PointF p = a.pts[kq];
+                    const PointF p = (BATCH ? ip.pts : a.pts)[kq];
                     // epilogue operands, loaded now and used after the contraction
-                    iq = a.perm[kq];
+                    iq = (BATCH ? ip.perm : a.perm)[kq];
                     if (a.op != OP_DEGREE) zq = zc[kq];
-                    if (a.op == OP_A || a.op == OP_LS) dq = a.dinv[kq];
+                    if (a.op == OP_A || a.op == OP_LS) dq = (BATCH ? ip.dinv : a.dinv)[kq];
                     s0 = cell_axis(p.cell, 0) - tc[0] * TE;
                     s1 = cell_axis(p.cell, 1) - tc[1] * TE;
                     s2 = cell_axis(p.cell, 2) - tc[2] * TE;
@@ -308,7 +351,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                     // every thread takes the same decision (barriers below stay matched)
                     if (__syncthreads_or(!done)) {
                         failed = true;
-                        if (tid == 0) atomicExch(a.error_flag, 1);
+                        if (tid == 0) atomicExch(BATCH ? ip.error_flag : a.error_flag, 1);
                     }
                 }
                 phase ^= 1u;
@@ -351,7 +394,8 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                         a.degree_out[iq] = dd;
                         a.dinv_out[kq] = dd > 0.0 ? 1.0 / sqrt(dd) : 0.0;
                     } else {
-                        const double s = a.op == OP_W ? a.out_scale : (a.op == OP_A ? a.out_scale : -a.out_scale) * dq;
+                        const double osc = BATCH ? ip.out_scale : a.out_scale;
+                        const double s = a.op == OP_W ? osc : (a.op == OP_A ? osc : -osc) * dq;
                         yc[iq] = fma(s, fd, zq);
                     }
                 }
@@ -385,6 +429,44 @@ static cudaError_t launch_tc(Plan &P, const GatherTCArgs &a) {
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, 128, smem, P.stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int M, int TE>
+static cudaError_t launch_tc_batch(Batch &B, const GatherTCArgs &a, cudaStream_t s) {
+    using G = TCGeom<M, TE>;
+    auto kern = B.bf16 ? gather3_tc<M, TE, true, true> : gather3_tc<M, TE, false, true>;
+    const int smem = 52 * 1024;
+    static_assert(2 * G::A_BYTES + 2 * G::B_BYTES + 1024 <= 52 * 1024, "operands fit");
+    NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int64_t grid = 4LL * B.num_sms;
+    if (grid > B.ngitems * a.ncol) grid = B.ngitems * a.ncol;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The interpolation of every member of a batch in one launch: (item, column) pairs of
+// all members from one counter, items largest first.
+cudaError_t launch_gather_tc_batch(Batch &B, cudaStream_t s) {
+    GatherTCArgs a{};
+    a.ncol = B.ncol;
+    a.nitems = B.ngitems;
+    a.bitems = B.gitems;
+    a.bplans = B.desc;
+    a.ngrid = 2 * B.N;
+    a.op = B.op;
+    a.counter = B.counter + 1;
+    a.skip_mma = 0;
+    a.wait_ns = 2000000000ull;
+    for (int j = 0; j < 2 * kMaxM; ++j)
+        for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = B.poly[j][k];
+    switch (B.m) {
+        case 2: return launch_tc_batch<2, 8>(B, a, s);
+        case 3: return launch_tc_batch<3, 8>(B, a, s);
+        case 4: return launch_tc_batch<4, 8>(B, a, s);
+        case 6: return launch_tc_batch<6, 4>(B, a, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 bool gather_tc_available(const Plan &P) {

@@ -168,6 +168,88 @@ struct BatchStreams {
 };
 BatchStreams *batch_streams();
 
+// A batch of plans whose products run with one launch per stage (batch.cu): every
+// member is a 3-D FP32 / FP32C / BF16W plan of the same m and N on the warp-spread /
+// tensor-core path; the batch owns contiguous staging, grid and FFT buffers for all
+// members' columns and binds the caller's input and output blocks.
+struct BatchPlanDev {
+    const PointF *pts;
+    const int32_t *perm;
+    const double *dinv;
+    const int32_t *tile_start;
+    const WorkItem *items;        // gather chunks of the plan
+    const WorkItem *sitems;       // warp-spread items of the plan
+    const double *x;              // caller's input block, column c at x + c ldx
+    double *y;                    // caller's output block, column c at y + c ldy
+    int64_t ldx, ldy;
+    float *xs;                    // staged x~, column c at xs + c n
+    double *zd;                   // staged epilogue z, column c at zd + c n
+    void *grid;                   // spreading grid, column c at grid + c box
+    float *g;                     // interpolation grid, column c at g + c box
+    double *abs_sum;              // FP32C scale sums, one per column
+    int64_t n, box;
+    int ntile[3], L[3], wrap[3];
+    double k0, out_scale;
+    int *error_flag;              // the member's device error flag
+};
+struct BatchItem {
+    int32_t plan, item;
+};
+// One FFT pass over contiguous lines (fft.cu).
+struct PassArgs {
+    const void *in;
+    void *out;
+    int nA, nB;
+    int64_t sA, sB;
+    int Lin;
+    unsigned lin_magic;   // ceil(2^32 / Lin): e / Lin = umulhi(e, lin_magic) for e < 2^22
+    int64_t oC, oA;
+    int Lout;
+    int n, logn, N;
+    int BB;
+    const void *tw;       // e^{-2 pi i q / n}, q < n/2
+    const void *M;        // fused multiplier, index ((b * nA) + a) * (N + 1) + (k + N/2)
+    int real_in, real_out;
+    const double *abs_sum;  // int64 fixed-point input: sum |x~| of the spread call, per column
+    int64_t in_cstride, out_cstride;   // elements between the columns of a block (grid.z)
+};
+
+struct Batch {
+    std::vector<Plan *> plans;
+    int G = 0, op = 0, ncol = 1, m = 0, N = 0, prec = 0;
+    bool bf16 = false;
+    int num_sms = 0;
+    BatchPlanDev *desc = nullptr;        // device, G entries
+    BatchItem *sitems = nullptr, *gitems = nullptr;   // device: all spread / gather items, largest first
+    int64_t nsitems = 0, ngitems = 0;
+    int *stage_start = nullptr;          // device: first staging CTA of each plan, [G] = total
+    int stage_ctas = 0;
+    unsigned *counter = nullptr;         // device: [0] spread, [1] gather
+    void *grid_all = nullptr;            // contiguous buffers of all members' columns
+    size_t grid_bytes = 0;
+    double *abs_all = nullptr;
+    void *xs_all = nullptr, *zd_all = nullptr, *g_all = nullptr, *bufA_all = nullptr, *bufB_all = nullptr;
+    PassArgs *pass_args[5] = {};         // device, G entries per FFT pass
+    int *pass_start[5] = {};             // device: first CTA of each plan per pass, [G] = total
+    int pass_ctas[5] = {};
+    int fft_cap = 512;
+    int *error_flag = nullptr;
+    float poly[2 * kMaxM][kPolyCoef] = {};
+    // stage timing: 5 events per timed run (before staging, spread, FFT, interpolation, after)
+    bool profile = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    cudaStream_t last_stream = nullptr;
+};
+cudaError_t launch_stage_batch(Batch &B, cudaStream_t s);
+cudaError_t launch_spread3_warp_batch(Batch &B, cudaStream_t s);
+cudaError_t launch_fft_batch(Batch &B, cudaStream_t s);
+cudaError_t launch_gather_tc_batch(Batch &B, cudaStream_t s);
+// the five 3-D FFT passes of a plan over given buffers (column strides of the grids
+// box, of bufA / bufB their sizes), with BB and the magic divisor set for cap
+int fft_passes_3d(const Plan &P, const void *grid, void *bufA, void *bufB, void *g, int64_t sa, int64_t sb,
+                  int cap, PassArgs *out, int nc, int *ctas);
+
 // number of kernels one column launches
 int kernels_per_column(const Plan &P);
 

@@ -58,17 +58,12 @@ struct Spread3Args {
 //   W: z = -k0 x,  A: z = -k0 d^2 x,  L_s: z = x + k0 d^2 x   (none for the degree).
 // Column blockIdx.y of a block: x + c ldx in, out + c n and z_out + c n out, abs_sum[c].
 template <typename T>
-__global__ void __launch_bounds__(256) stage_values(const double *x, int64_t ldx, const int32_t *perm,
-                                                    const double *dinv, int64_t n, int ones, T *out, double *z_out,
-                                                    int op, double k0, double *abs_sum) {
+__device__ __forceinline__ void stage_body(const double *x, const int32_t *perm, const double *dinv, int64_t n, int ones,
+                                           T *out, double *z_out, int op, double k0, double *abs_sum, int64_t blk,
+                                           int64_t nblk) {
     __shared__ double red[256];
-    const int col = blockIdx.y;
-    x += col * ldx;
-    out += col * n;
-    z_out += col * n;
-    if (abs_sum) abs_sum += col;
     double acc = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t k = blk * (int64_t)blockDim.x + threadIdx.x; k < n; k += nblk * blockDim.x) {
         const double xv = ones ? 1.0 : x[perm[k]];
         const double dk = dinv ? dinv[k] : 1.0;
         const double v = dinv ? xv * dk : xv;
@@ -86,6 +81,41 @@ __global__ void __launch_bounds__(256) stage_values(const double *x, int64_t ldx
         __syncthreads();
     }
     if (threadIdx.x == 0) atomicAdd(abs_sum, red[0]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) stage_values(const double *x, int64_t ldx, const int32_t *perm,
+                                                    const double *dinv, int64_t n, int ones, T *out, double *z_out,
+                                                    int op, double k0, double *abs_sum) {
+    const int col = blockIdx.y;
+    stage_body<T>(x + col * ldx, perm, dinv, n, ones, out + col * n, z_out + col * n, op, k0,
+                  abs_sum ? abs_sum + col : nullptr, blockIdx.x, gridDim.x);
+}
+
+// The staging of every member of a batch in one launch: CTA x-index b belongs to the
+// plan g with start[g] <= b < start[g + 1]; column blockIdx.y.
+__global__ void __launch_bounds__(256) stage_values_batch(const BatchPlanDev *D, const int *start, int G, int op,
+                                                          int fixed) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchPlanDev &P = D[lo];
+    const int col = blockIdx.y;
+    const bool scale = op == OP_A || op == OP_LS;
+    stage_body<float>(P.x + col * P.ldx, P.perm, scale ? P.dinv : nullptr, P.n, 0, P.xs + col * P.n,
+                      P.zd + col * P.n, op, P.k0, fixed ? P.abs_sum + col : nullptr, b - start[lo],
+                      start[lo + 1] - start[lo]);
+}
+
+cudaError_t launch_stage_batch(Batch &B, cudaStream_t s) {
+    if (B.stage_ctas < 1) return cudaSuccess;
+    stage_values_batch<<<dim3(B.stage_ctas, B.ncol), 256, 0, s>>>(B.desc, B.stage_start, B.G, B.op,
+                                                                   B.prec == NFL_PREC_FP32C ? 1 : 0);
+    return cudaGetLastError();
 }
 
 __device__ __forceinline__ void group_barrier(int id, int nthreads) {

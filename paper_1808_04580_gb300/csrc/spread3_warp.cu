@@ -58,8 +58,13 @@ struct SpreadWarpArgs {
     const int32_t *tile_start;      // first sorted node of each tile
     unsigned *counter;              // next work item, shared by all CTAs
     int bf16;                       // BF16W: taps rounded to BF16
+    const BatchPlanDev *bplans;     // batch: the members (item it is bitems[it] of member bitems[it].plan)
+    const BatchItem *bitems;
     float poly[2 * kMaxM][kPolyCoef];
 };
+
+// box extent of axis i of the current item's plan
+#define SW_L(i) (BATCH ? ip.L[i] : a.L[i])
 
 template <int M, int TE>
 struct WarpGeom {
@@ -91,8 +96,17 @@ struct WarpGeom {
     static_assert(WARP_BYTES % 16 == 0, "16-byte aligned per-warp areas");
 };
 
-// BLOCK: a block product of a.ncol columns (item, column pairs); otherwise one column
-template <int M, int TE, bool FIXED, bool BLOCK>
+// Per-item plan fields of a batch, in shared memory (written by thread 0 per item).
+struct SpreadItemPlan {
+    const PointF *pts;
+    const int32_t *tile_start;
+    int ntile[3], L[3], wrap[3];
+};
+
+// BLOCK: a block product of a.ncol columns (item, column pairs); otherwise one column.
+// BATCH (with BLOCK): the items of all members of a batch, each item's plan fields
+// read from its member's descriptor.
+template <int M, int TE, bool FIXED, bool BLOCK, bool BATCH = false>
 __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(SpreadWarpArgs a) {
     using G = WarpGeom<M, TE>;
     constexpr int PA = G::PA, PA3 = G::PA3, TAPS = G::TAPS, RP = G::RP, CPL = G::CPL, S = G::S, NG = G::NG,
@@ -118,7 +132,13 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
     }
     for (int e = lane; e < G::TILE; e += 32) tile[e] = 0.f;
     __shared__ float fscales[kBlockCols];           // FP32C scale 2^k of each column of a block
-    if (FIXED && BLOCK && threadIdx.x < a.ncol) fscales[threadIdx.x] = float(fixed_scale_of(a.abs_sum[threadIdx.x]));
+    if (FIXED && BLOCK && !BATCH && threadIdx.x < a.ncol)
+        fscales[threadIdx.x] = float(fixed_scale_of(a.abs_sum[threadIdx.x]));
+    __shared__ SpreadItemPlan ip;
+    __shared__ WorkItem bw;
+    __shared__ float bscale;
+    __shared__ const float *bxs;
+    __shared__ void *bgrid;
     float fscale1 = 1.f;                            // the one column's
     if (FIXED && !BLOCK) fscale1 = float(fixed_scale_of(*a.abs_sum));
     __syncthreads();
@@ -185,27 +205,49 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
 
     for (;;) {
         // the CTA's next work item (largest first: the plan sorts them by size)
-        if (threadIdx.x == 0) next_item = atomicAdd(a.counter, 1u);
+        if (threadIdx.x == 0) {
+            next_item = atomicAdd(a.counter, 1u);
+            if (BATCH && (int64_t)next_item < a.nitems * a.ncol) {
+                // the member of this item and its fields
+                const unsigned it0 = next_item / (unsigned)a.ncol;
+                const int c0 = (int)(next_item - it0 * (unsigned)a.ncol);
+                const BatchItem e = a.bitems[it0];
+                const BatchPlanDev &D = a.bplans[e.plan];
+                bw = D.sitems[e.item];
+                ip.pts = D.pts;
+                ip.tile_start = D.tile_start;
+                for (int i = 0; i < 3; ++i) {
+                    ip.ntile[i] = D.ntile[i];
+                    ip.L[i] = D.L[i];
+                    ip.wrap[i] = D.wrap[i];
+                }
+                bxs = D.xs + c0 * D.n;
+                bscale = FIXED ? float(fixed_scale_of(D.abs_sum[c0])) : 1.f;
+                bgrid = FIXED ? (void *)(reinterpret_cast<unsigned long long *>(D.grid) + c0 * D.box)
+                              : (void *)(reinterpret_cast<float *>(D.grid) + c0 * D.box);
+            }
+        }
         __syncthreads();
         const int64_t itc = next_item;
         if (itc >= a.nitems * (BLOCK ? a.ncol : 1)) break;
         const int64_t it = BLOCK ? (int64_t)((unsigned)itc / (unsigned)a.ncol) : itc;
         const int col = BLOCK ? (int)(itc - it * a.ncol) : 0;
-        const float *xs = BLOCK ? a.xs + col * a.xs_stride : a.xs;
-        const float fscale = !FIXED ? 1.f : (BLOCK ? fscales[col] : fscale1);
-        void *const gridc = !BLOCK ? a.grid
+        const float *xs = BATCH ? bxs : (BLOCK ? a.xs + col * a.xs_stride : a.xs);
+        const float fscale = !FIXED ? 1.f : (BATCH ? bscale : (BLOCK ? fscales[col] : fscale1));
+        void *const gridc = BATCH ? bgrid
+                          : !BLOCK ? a.grid
                                    : FIXED ? (void *)(reinterpret_cast<unsigned long long *>(a.grid) + col * a.grid_stride)
                                            : (void *)(reinterpret_cast<float *>(a.grid) + col * a.grid_stride);
-        const WorkItem w = a.items[it];
+        const WorkItem w = BATCH ? bw : a.items[it];
         const int wend = w.start + w.count;
         const int ntl = w.pad;                    // tiles in the item (a run along axis 2), or 1
         // lane l holds the first node of tile w.tile + l of a run (l <= ntl <= 31)
-        const int lane_start = (ntl > 1 && lane <= ntl) ? a.tile_start[w.tile + lane] : 0;
+        const int lane_start = (ntl > 1 && lane <= ntl) ? (BATCH ? ip.tile_start : a.tile_start)[w.tile + lane] : 0;
         woff = 0;
         for (int jt = 0; jt < ntl; ++jt) {
             const int tile_id = w.tile + jt;
             int tc[3];
-            tile_coords<3>(tile_id, a.ntile, tc);
+            tile_coords<3>(tile_id, BATCH ? ip.ntile : a.ntile, tc);
             int cur = -1;
             // this tile's nodes: the chunk, or the whole tile within a run
             const int run_s = __shfl_sync(0xffffffffu, lane_start, jt);
@@ -219,7 +261,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
             PointF pn = {{0.f, 0.f, 0.f}, 0};
             float xn = 0.f;
             if (base + lane < gend) {
-                pn = a.pts[base + lane];
+                pn = (BATCH ? ip.pts : a.pts)[base + lane];
                 xn = xs[base + lane];
             }
             for (; base < gend; base += S) {
@@ -240,7 +282,7 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     const float xv = xn;
                     const int kn = base + S + lane;
                     if (kn < gend) {
-                        pn = a.pts[kn];
+                        pn = (BATCH ? ip.pts : a.pts)[kn];
                         xn = xs[kn];
                     }
                     const unsigned long long T0 = pack2(fmaf(2.f, f[0], -1.f), fmaf(2.f, f[0], -1.f));
@@ -353,11 +395,11 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     }
                     if (v == 0.f) continue;
                     int p0 = b0 + q0, p1 = b1 + q1, p2 = b2 + q;
-                    if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-                    if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-                    if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-                    if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
-                    const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+                    if (BATCH ? ip.wrap[0] : a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (BATCH ? ip.wrap[1] : a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (BATCH ? ip.wrap[2] : a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (p0 < 0 || p0 >= SW_L(0) || p1 < 0 || p1 >= SW_L(1) || p2 < 0 || p2 >= SW_L(2)) continue;
+                    const int64_t gidx = ((int64_t)p0 * SW_L(1) + p1) * SW_L(2) + p2;
                     if (FIXED)
                         atomicAdd(reinterpret_cast<unsigned long long *>(gridc) + gidx,
                                   (unsigned long long)to_fixed(v * fscale));
@@ -395,11 +437,11 @@ __global__ void __launch_bounds__(WarpGeom<M, TE>::NG * 32, 3) spread3_warp(Spre
                     if (q2 >= PA) { q2 -= PA; ++q1; }
                     if (q1 >= PA) { q1 -= PA; ++q0; }
                     if (v == 0.f) continue;
-                    if (a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
-                    if (a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-                    if (a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-                    if (p0 < 0 || p0 >= a.L[0] || p1 < 0 || p1 >= a.L[1] || p2 < 0 || p2 >= a.L[2]) continue;
-                    const int64_t gidx = ((int64_t)p0 * a.L[1] + p1) * a.L[2] + p2;
+                    if (BATCH ? ip.wrap[0] : a.wrap[0]) p0 = ((p0 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (BATCH ? ip.wrap[1] : a.wrap[1]) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (BATCH ? ip.wrap[2] : a.wrap[2]) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
+                    if (p0 < 0 || p0 >= SW_L(0) || p1 < 0 || p1 >= SW_L(1) || p2 < 0 || p2 >= SW_L(2)) continue;
+                    const int64_t gidx = ((int64_t)p0 * SW_L(1) + p1) * SW_L(2) + p2;
                     if (FIXED)
                         atomicAdd(reinterpret_cast<unsigned long long *>(gridc) + gidx,
                                   (unsigned long long)to_fixed(v * fscale));
@@ -426,6 +468,45 @@ static cudaError_t launch_warp(Plan &P, const SpreadWarpArgs &a) {
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, G::NG * 32, G::SMEM, P.stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int M, int TE, bool FIXED>
+static cudaError_t launch_warp_batch(Batch &B, const SpreadWarpArgs &a, cudaStream_t s) {
+    using G = WarpGeom<M, TE>;
+    auto kern = spread3_warp<M, TE, FIXED, true, true>;
+    NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
+    NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int per_sm = 0;
+    NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NG * 32, G::SMEM));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * B.num_sms;
+    if (grid > B.nsitems * a.ncol) grid = B.nsitems * a.ncol;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, G::NG * 32, G::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The spread of every member of a batch in one launch: (item, column) pairs of all
+// members from one counter, items largest first.
+cudaError_t launch_spread3_warp_batch(Batch &B, cudaStream_t s) {
+    SpreadWarpArgs a{};
+    a.ncol = B.ncol;
+    a.nitems = B.nsitems;
+    a.bitems = B.sitems;
+    a.bplans = B.desc;
+    a.ngrid = 2 * B.N;
+    a.counter = B.counter;
+    a.bf16 = B.bf16 ? 1 : 0;
+    for (int j = 0; j < 2 * kMaxM; ++j)
+        for (int k = 0; k < kPolyCoef; ++k) a.poly[j][k] = B.poly[j][k];
+    const bool fixed = B.prec == NFL_PREC_FP32C;
+    switch (B.m) {
+        case 2: return fixed ? launch_warp_batch<2, 8, true>(B, a, s) : launch_warp_batch<2, 8, false>(B, a, s);
+        case 3: return fixed ? launch_warp_batch<3, 8, true>(B, a, s) : launch_warp_batch<3, 8, false>(B, a, s);
+        case 4: return fixed ? launch_warp_batch<4, 8, true>(B, a, s) : launch_warp_batch<4, 8, false>(B, a, s);
+        case 6: return fixed ? launch_warp_batch<6, 4, true>(B, a, s) : launch_warp_batch<6, 4, false>(B, a, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 bool spread_warp_available(const Plan &P) {

@@ -83,6 +83,13 @@ SIGNATURES = {
     "nfl_plan_kernels_per_column": (_I, [_P, ctypes.POINTER(_I)]),
     "nfl_plan_inject_fault": (_I, [_P, _I]),
     "nfl_fma_rate": (_I, [_I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "nfl_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_L), ctypes.POINTER(_P),
+                              ctypes.POINTER(_L), _I, _I, ctypes.POINTER(_P)]),
+    "nfl_batch_parts": (_I, [_P, ctypes.POINTER(_I)]),
+    "nfl_batch_run": (_I, [_P, _P]),
+    "nfl_batch_destroy": (None, [_P]),
+    "nfl_batch_set_profiling": (_I, [_P, _I]),
+    "nfl_batch_stage_times": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
     "nfl_status_string": (ctypes.c_char_p, [_I]),
 }
 
@@ -456,3 +463,72 @@ def apply_batched(plans, xs, op="Ls", outs=None):
     _check(_lib().nfl_apply_batched(arr_p, G, _OPS[op], arr_x, arr_y, arr_l, int(nrhs or 1)), "nfl_apply_batched")
     return [y if v else y.t() for y, v in zip(ys, vecs)]
 
+
+class Batch:
+    """Products of many plans with one launch per stage and part (nfl_batch_create / nfl_batch_run).
+
+    plans: Plans of one mixed precision, m and N (3-D), split into ``parts`` groups
+    that run concurrently; xs: their (n_g,) or (n_g, r)
+    CUDA float64 blocks (same r), bound at creation together with the outputs
+    (``outs``: contiguous (r, n_g) or (n_g,) tensors, else allocated).  ``run()``
+    issues the products on the current stream (capturable in a CUDA graph);
+    ``outputs`` are shaped like xs.  Column-major x blocks (``X.t()`` of a
+    contiguous (r, n) tensor) are used in place, so they can be refilled between runs.
+    """
+
+    def __init__(self, plans, xs, op="Ls", outs=None, parts=1):
+        G = len(plans)
+        if len(xs) != G or G == 0:
+            raise ValueError("one block per plan")
+        cols, ys, vecs, nrhs = [], [], [], None
+        for g, (plan, x) in enumerate(zip(plans, xs)):
+            xc, r, vec = _as_columns(x, plan.n)
+            if nrhs is None:
+                nrhs = r
+            elif r != nrhs:
+                raise ValueError("every block needs the same number of columns")
+            cols.append(xc)
+            ys.append(torch.empty_like(xc) if outs is None else outs[g])
+            vecs.append(vec)
+        self._plans, self._x, self._y, self._vec = list(plans), cols, ys, vecs
+        self._h = None
+        arr_p = (_P * G)(*[p._h for p in plans])
+        arr_x = (_P * G)(*[c.data_ptr() for c in cols])
+        arr_y = (_P * G)(*[y.data_ptr() for y in ys])
+        arr_l = (_L * G)(*[p.n for p in plans])
+        h = ctypes.c_void_p()
+        _check(_lib().nfl_batch_create(arr_p, G, _OPS[op], arr_x, arr_l, arr_y, arr_l, int(nrhs), int(parts),
+                                       ctypes.byref(h)), "nfl_batch_create")
+        self._h = h
+        k = ctypes.c_int(0)
+        _check(_lib().nfl_batch_parts(self._h, ctypes.byref(k)), "nfl_batch_parts")
+        self.parts = k.value
+
+    def run(self):
+        _check(_lib().nfl_batch_run(self._h, _stream()), "nfl_batch_run")
+        return self.outputs
+
+    @property
+    def outputs(self):
+        return [y if v else y.t() for y, v in zip(self._y, self._vec)]
+
+    def set_profiling(self, enable=True):
+        _check(_lib().nfl_batch_set_profiling(self._h, 1 if enable else 0), "nfl_batch_set_profiling")
+
+    def stage_times(self):
+        """Accumulated ms per stage since the last call: dict(prep, spread, fft, gather, runs)."""
+        ms = (ctypes.c_double * 4)()
+        runs = ctypes.c_int64(0)
+        _check(_lib().nfl_batch_stage_times(self._h, ms, ctypes.byref(runs)), "nfl_batch_stage_times")
+        return dict(prep=ms[0], spread=ms[1], fft=ms[2], gather=ms[3], runs=runs.value)
+
+    def close(self):
+        if self._h is not None and _LIB is not None:
+            _LIB.nfl_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -119,6 +119,9 @@ typedef struct {
     int fft_lines_cap;    /* FFT passes: grid points per CTA (lines x length)  */
     int slide_tiles;      /* 3-D warp spread: most tiles in one sliding run    */
     int block_cols;       /* columns per launch of a block product (1: none)   */
+    int64_t dense_items;  /* 3-D m = 6 FP32 / FP32C: chunks of the tiles with at
+                             least 32 nodes per occupied cell, which one-column
+                             products spread by Chebyshev moments (0: none)   */
 } nfl_info;
 
 /*

@@ -11,7 +11,10 @@ namespace nfl {
 int kernels_per_column(const Plan &P) {
     const int passes = P.d == 1 ? 1 : (P.d == 2 ? 3 : 5);
     const bool staged = P.d == 3 && column_tile_edge(P.m) == P.tile_edge;
-    return (staged || P.prec == NFL_PREC_FP32C ? 1 : 0) + 1 + passes + 1;
+    // the one-column spread with dense cells launches the warp-slice kernel for the sparse
+    // tiles and the moment kernel for the dense ones (each only when it has items)
+    const int spreads = moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.ndense > 0 ? 1 : 0) : 1;
+    return (staged || P.prec == NFL_PREC_FP32C ? 1 : 0) + spreads + passes + 1;
 }
 
 // stage events: 5 per timed product (before prep, spread, fft, gather, after); a
@@ -372,7 +375,9 @@ nfl_status nfl_plan_kernels(const nfl_plan *plan, int nrhs, int *kernels) {
     const nfl::Plan &P = *reinterpret_cast<const nfl::Plan *>(plan);
     if (nrhs > 1 && P.block_cols > 1 && nfl::block_path_available(P)) {
         const int blocks = (nrhs + P.block_cols - 1) / P.block_cols;
-        *kernels = blocks * nfl::kernels_per_column(P);   // one launch per stage and block
+        // one launch per stage and block (a block spreads every tile with the warp-slice kernel)
+        const int spreads = nfl::moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.ndense > 0 ? 1 : 0) : 1;
+        *kernels = blocks * (nfl::kernels_per_column(P) - spreads + 1);
     } else {
         *kernels = nrhs * nfl::kernels_per_column(P);
     }

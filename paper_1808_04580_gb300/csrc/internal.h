@@ -36,6 +36,8 @@ constexpr int kMaxM = 12;
 constexpr int kHostSlots = 3;   // device staging slots per direction for host-buffer products
 constexpr int kBlockCols = 8;   // columns a block product takes through each stage in one launch
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
+constexpr int kCheb = 8;        // Chebyshev basis of the dense-cell spread (degree 7)
+constexpr int kDenseCell = 32;  // nodes per occupied cell from which a tile is spread by moments
 
 // Per-column buffers of block products (see Plan::blk).
 struct BlockBuffers {
@@ -74,6 +76,11 @@ struct Plan {
     WorkItem *sitems = nullptr;
     int32_t *tile_start = nullptr;      // first sorted node of each tile; [tiles_total] = n
     std::vector<WorkItem> tile_items;   // host copy of the per-tile chunks, in tile order
+    std::vector<int32_t> tile_cells;    // occupied cells of each tile (host)
+    // one-column products with the dense-cell spread (moments_available): runs over the
+    // sparse tiles for the warp spread, and the chunks of the dense tiles
+    int64_t nsparse = 0, ndense = 0;
+    WorkItem *sparse_items = nullptr, *dense_items = nullptr;
     int slide_tiles = 8;                // most tiles in one sliding run of the warp spread
     int fft_cap = 512;                  // FFT passes: grid points per CTA
 
@@ -94,6 +101,9 @@ struct Plan {
     // phi(f + m - 1 - j) / phi(0) = sum_k kb_poly[j][k] t^k, t = 2 f - 1, to
     // within FP32 rounding of the peak (Chebyshev interpolation in FP64).
     float kb_poly[2 * kMaxM][kPolyCoef] = {};
+    // the same taps in the Chebyshev basis T_k(t), k < kCheb (interpolation at kCheb
+    // Chebyshev points): phi(f + m - 1 - j) / phi(0) = sum_k kb_cheb[j][k] T_k(2 f - 1)
+    float kb_cheb[2 * kMaxM][kCheb] = {};
 
     // FFT data
     int K[3] = {1, 1, 1};       // kept frequencies per axis (R2C axis N/2+1, others N+1)
@@ -109,11 +119,16 @@ struct Plan {
     void *bufA = nullptr;       // complex FFT intermediates
     void *bufB = nullptr;
     void *g = nullptr;          // interpolation grid (real, FFT type)
+    // interpolation grid layout: rows of g_row reals along x0 with x0 at g_off + x0 (the
+    // rest zero), so that on the tensor-core path every tile's halo starts 16-byte aligned
+    int g_off = 0, g_row = 0;
+    int g_vec = 0;              // 1: rows aligned so, the interpolation loads them as float4
+    int64_t g_elems = 0;        // per column
     void *mult = nullptr;       // fused multiplier M_eff (real, FFT type)
     void *twiddle = nullptr;    // e^{-2 pi i q / ngrid}, q < ngrid/2 (complex, FFT type)
     double *scratch = nullptr;  // small device scalars (reductions, fixed-point scale)
     int *error_flag = nullptr;  // set by a kernel whose bounded wait ran out
-    unsigned *work_counter = nullptr;   // [0] spread, [1] gather: next work item (reset per column)
+    unsigned *work_counter = nullptr;   // [0] spread, [1] gather, [2] dense-cell spread: next work item (reset per column)
     int fault_kind = 0;         // fault test (nfl_plan_inject_fault): 1 = interpolation MMAs never issued
     int num_sms = 0;
 
@@ -185,7 +200,9 @@ struct BatchPlanDev {
     float *xs;                    // staged x~, column c at xs + c n
     double *zd;                   // staged epilogue z, column c at zd + c n
     void *grid;                   // spreading grid, column c at grid + c box
-    float *g;                     // interpolation grid, column c at g + c box
+    float *g;                     // interpolation grid, column c at g + c g_elems
+    int64_t g_elems;
+    int g_row, g_off, gvec;       // its row length, x0 offset, 16-byte aligned rows
     double *abs_sum;              // FP32C scale sums, one per column
     int64_t n, box;
     int ntile[3], L[3], wrap[3];
@@ -263,6 +280,12 @@ nfl_status rebuild_spread_items(Plan &P);
 
 // the warp spread's work list built from tile_items (host)
 std::vector<WorkItem> spread_item_list(const Plan &P);
+// dense-cell spread (spread3_moments.cu): available for the plan, the split of the
+// work lists into sliding runs over sparse tiles and the chunks of dense tiles (host),
+// and the launch over the dense chunks (one column)
+bool moments_available(const Plan &P);
+void split_item_lists(const Plan &P, std::vector<WorkItem> &sparse, std::vector<WorkItem> &dense);
+cudaError_t launch_spread3_moments(Plan &P);
 
 }  // namespace nfl
 

@@ -202,6 +202,16 @@ __global__ void tile_starts(const int64_t *kstart, int64_t ntiles, int cells_per
         out[t] = (int32_t)kstart[t * cells_per_tile];
 }
 
+// Occupied cells of every tile, from the per-key (tile, cell) offsets.
+__global__ void occupied_cells(const int64_t *kstart, int64_t ntiles, int cells_per_tile, int32_t *out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int k = 0; k < cells_per_tile; ++k)
+            c += kstart[t * cells_per_tile + k + 1] > kstart[t * cells_per_tile + k] ? 1 : 0;
+        out[t] = c;
+    }
+}
+
 // Work items of the warp-slice spread from the per-tile chunks (in tile order): a tile
 // with several chunks keeps them as items of one tile; runs of single-chunk tiles that
 // follow each other along axis 2 in one row are joined while they hold at most kChunk
@@ -259,13 +269,15 @@ nfl_status ensure_columns(Plan &P, int nc) {
         cudaMalloc(&P.blk.xsorted, P.n * 8 * bc) != cudaSuccess ||
         cudaMalloc(&P.blk.bufA, P.bufA_elems * cplx_sz * bc) != cudaSuccess ||
         cudaMalloc(&P.blk.bufB, P.bufB_elems * cplx_sz * bc) != cudaSuccess ||
-        cudaMalloc(&P.blk.g, P.box_elems * real_sz * bc) != cudaSuccess ||
+        cudaMalloc(&P.blk.g, P.g_elems * real_sz * bc) != cudaSuccess ||
         cudaMalloc(&P.blk.grid, P.box_elems * grid_sz * bc) != cudaSuccess) {
         cudaFree(P.blk.xsort); cudaFree(P.blk.xsorted); cudaFree(P.blk.bufA);
         cudaFree(P.blk.bufB); cudaFree(P.blk.g); cudaFree(P.blk.grid);
         P.blk = BlockBuffers{};
         return NFL_ERR_OUT_OF_MEMORY;
     }
+    // the pads of the interpolation grids stay zero
+    if (cudaMemsetAsync(P.blk.g, 0, P.g_elems * real_sz * bc, P.stream) != cudaSuccess) return NFL_ERR_CUDA;
     return NFL_OK;
 }
 
@@ -276,7 +288,57 @@ std::vector<WorkItem> spread_item_list(const Plan &P) {
     return s;
 }
 
+bool moments_available(const Plan &P) {
+    return spread_warp_available(P) && P.m == 6 && !P.bf16_taps && !P.tile_cells.empty();
+}
+
+// Dense tiles (at least kDenseCell nodes per occupied cell) go to the dense-cell
+// spread chunk by chunk, largest first; the other tiles keep the sliding runs.
+void split_item_lists(const Plan &P, std::vector<WorkItem> &sparse, std::vector<WorkItem> &dense) {
+    std::vector<WorkItem> rest;
+    sparse.clear();
+    dense.clear();
+    std::vector<int64_t> tile_nodes(P.tiles_total, 0);
+    for (const WorkItem &w : P.tile_items) tile_nodes[w.tile] += w.count;
+    for (const WorkItem &w : P.tile_items) {
+        const int32_t cells = P.tile_cells[w.tile];
+        if (cells > 0 && tile_nodes[w.tile] >= (int64_t)kDenseCell * cells) dense.push_back(w);
+        else rest.push_back(w);
+    }
+    sparse = slide_items(rest, P.ntile[P.d - 1], P.slide_tiles);
+    const auto by_size = [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; };
+    std::stable_sort(sparse.begin(), sparse.end(), by_size);
+    std::stable_sort(dense.begin(), dense.end(), by_size);
+    for (WorkItem &w : dense) w.pad = 1;
+}
+
+// (Re)allocates dst for cnt items when it holds fewer (old lists are never read again)
+static nfl_status ensure_list(WorkItem *&dst, int64_t &have, int64_t cnt) {
+    if (dst && cnt <= have) return NFL_OK;
+    cudaFree(dst);
+    dst = nullptr;
+    have = 0;
+    if (cudaMalloc(&dst, std::max<int64_t>(cnt, 1) * sizeof(WorkItem)) != cudaSuccess) return NFL_ERR_OUT_OF_MEMORY;
+    return NFL_OK;
+}
+
 nfl_status rebuild_spread_items(Plan &P) {
+    if (moments_available(P)) {
+        std::vector<WorkItem> sp, de;
+        split_item_lists(P, sp, de);
+        int64_t hs = P.nsparse, hd = P.ndense;
+        if (ensure_list(P.sparse_items, hs, (int64_t)sp.size()) != NFL_OK ||
+            ensure_list(P.dense_items, hd, (int64_t)de.size()) != NFL_OK)
+            return NFL_ERR_OUT_OF_MEMORY;
+        if (cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
+        if ((!sp.empty() && cudaMemcpy(P.sparse_items, sp.data(), sp.size() * sizeof(WorkItem),
+                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
+            (!de.empty() && cudaMemcpy(P.dense_items, de.data(), de.size() * sizeof(WorkItem),
+                                       cudaMemcpyHostToDevice) != cudaSuccess))
+            return NFL_ERR_CUDA;
+        P.nsparse = (int64_t)sp.size();
+        P.ndense = (int64_t)de.size();
+    }
     const std::vector<WorkItem> s = spread_item_list(P);
     if ((int64_t)s.size() > P.nsitems || !P.sitems) {
         cudaFree(P.sitems);
@@ -617,6 +679,8 @@ static void free_plan(Plan *P) {
     cudaFree(P->blk.xsort); cudaFree(P->blk.xsorted); cudaFree(P->blk.bufA);
     cudaFree(P->blk.bufB); cudaFree(P->blk.g); cudaFree(P->blk.grid);
     cudaFree(P->sitems);
+    cudaFree(P->sparse_items);
+    cudaFree(P->dense_items);
     cudaFree(P->tile_start);
     cudaFree(P->pts);
     cudaFree(P->perm);
@@ -679,6 +743,16 @@ static void window_poly(Plan &P) {
             }
         }
         for (int q = 0; q < NC; ++q) P.kb_poly[j][q] = static_cast<float>(mono[q]);
+        // degree kCheb - 1 interpolant at kCheb Chebyshev points, kept in the Chebyshev basis
+        for (int k = 0; k < kCheb; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < kCheb; ++i) {
+                const double t = std::cos(M_PI * (i + 0.5) / kCheb);
+                acc += host_window(0.5 * (t + 1.0) + m - 1.0 - j, m, P.kb_b, P.kb_inv_sinh_bm) *
+                       std::cos(M_PI * k * (i + 0.5) / kCheb);
+            }
+            P.kb_cheb[j][k] = static_cast<float>((k == 0 ? 1.0 : 2.0) * acc / kCheb);
+        }
     }
 }
 
@@ -708,6 +782,7 @@ struct Builder {
     int64_t *kstart = nullptr, *start = nullptr, *item_off = nullptr;
     unsigned long long *nonempty = nullptr;
     WorkItem *hitems = nullptr;          // page-locked: chunks read back, then the lists uploaded
+    int32_t *occ = nullptr, *hocc = nullptr;   // occupied cells per tile (device, page-locked)
     double *htab = nullptr;              // page-locked: twiddles, cosine table, deconvolution factors
     double *S = nullptr, *T1 = nullptr, *ctab = nullptr, *dec = nullptr;   // coefficient temporaries
 };
@@ -717,6 +792,8 @@ static void release_temporaries(Builder &B) {
     cudaFree(B.chunks); cudaFree(B.kstart); cudaFree(B.start); cudaFree(B.item_off); cudaFree(B.nonempty);
     cudaFree(B.S); cudaFree(B.T1); cudaFree(B.ctab); cudaFree(B.dec);
     cudaFreeHost(B.hp); cudaFreeHost(B.hitems); cudaFreeHost(B.htab);
+    cudaFree(B.occ); cudaFreeHost(B.hocc);
+    B.occ = B.hocc = nullptr;
     B.part = B.S = B.T1 = B.ctab = B.dec = B.hp = B.htab = nullptr;
     B.key_of = B.rank = B.kcount = B.count = B.chunks = nullptr;
     B.kstart = B.start = B.item_off = nullptr;
@@ -744,7 +821,7 @@ static nfl_status phase_setup(Builder &B) {
     NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->l2_bytes, cudaDevAttrL2CacheSize, dev));
     NFL_STATUS_TRY(cudaMalloc(&P->scratch, 64 * sizeof(double)));
     NFL_STATUS_TRY(cudaMalloc(&P->error_flag, sizeof(int)));
-    NFL_STATUS_TRY(cudaMalloc(&P->work_counter, 2 * sizeof(unsigned)));
+    NFL_STATUS_TRY(cudaMalloc(&P->work_counter, 3 * sizeof(unsigned)));
     NFL_STATUS_TRY(cudaMemsetAsync(P->error_flag, 0, sizeof(int), B.stream));
     NFL_STATUS_TRY(cudaMalloc(&B.part, kRBlocks * 6 * sizeof(double)));
     NFL_STATUS_TRY(cudaHostAlloc(&B.hp, kRBlocks * 6 * sizeof(double), cudaHostAllocDefault));
@@ -871,8 +948,13 @@ static nfl_status phase_items(Builder &B) {
     const int blocks = P->num_sms * 8;
     fill_items<<<blocks, 256, 0, stream>>>(B.count, B.start, B.item_off, nt, P->items);
     tile_starts<<<blocks, 256, 0, stream>>>(B.kstart, nt, B.cpt, P->tile_start);
-    // room for the sorted chunks and the spread items (at most one per chunk) to upload
-    NFL_STATUS_TRY(cudaHostAlloc(&B.hitems, std::max<int64_t>(2 * P->nitems, 1) * sizeof(WorkItem),
+    // occupied cells per tile (for the dense-cell spread)
+    NFL_STATUS_TRY(cudaMalloc(&B.occ, std::max<int64_t>(nt, 1) * sizeof(int32_t)));
+    NFL_STATUS_TRY(cudaHostAlloc(&B.hocc, std::max<int64_t>(nt, 1) * sizeof(int32_t), cudaHostAllocDefault));
+    occupied_cells<<<blocks, 256, 0, stream>>>(B.kstart, nt, B.cpt, B.occ);
+    NFL_STATUS_TRY(cudaMemcpyAsync(B.hocc, B.occ, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    // room for the sorted chunks and the spread lists (at most one entry per chunk each) to upload
+    NFL_STATUS_TRY(cudaHostAlloc(&B.hitems, std::max<int64_t>(4 * P->nitems, 1) * sizeof(WorkItem),
                                  cudaHostAllocDefault));
     if (P->nitems > 0)
         NFL_STATUS_TRY(cudaMemcpyAsync(B.hitems, P->items, P->nitems * sizeof(WorkItem), cudaMemcpyDeviceToHost,
@@ -892,6 +974,7 @@ static nfl_status phase_finish(Builder &B) {
         // largest chunks first: the kernels that take items from a shared counter
         // then end with small ones (longest-processing-time order)
         P->tile_items.assign(B.hitems, B.hitems + P->nitems);
+        P->tile_cells.assign(B.hocc, B.hocc + P->tiles_total);
         const std::vector<WorkItem> s = spread_item_list(*P);
         if (cudaMalloc(&P->sitems, std::max<size_t>(s.size(), 1) * sizeof(WorkItem)) != cudaSuccess)
             return NFL_ERR_OUT_OF_MEMORY;
@@ -905,6 +988,24 @@ static nfl_status phase_finish(Builder &B) {
         if (!s.empty())
             NFL_STATUS_TRY(cudaMemcpyAsync(P->sitems, B.hitems + P->nitems, s.size() * sizeof(WorkItem),
                                            cudaMemcpyHostToDevice, stream));
+        if (moments_available(*P)) {
+            std::vector<WorkItem> sp, de;
+            split_item_lists(*P, sp, de);
+            if (cudaMalloc(&P->sparse_items, std::max<size_t>(sp.size(), 1) * sizeof(WorkItem)) != cudaSuccess ||
+                cudaMalloc(&P->dense_items, std::max<size_t>(de.size(), 1) * sizeof(WorkItem)) != cudaSuccess)
+                return NFL_ERR_OUT_OF_MEMORY;
+            P->nsparse = (int64_t)sp.size();
+            P->ndense = (int64_t)de.size();
+            WorkItem *hs = B.hitems + P->nitems + s.size(), *hd = hs + sp.size();
+            std::copy(sp.begin(), sp.end(), hs);
+            std::copy(de.begin(), de.end(), hd);
+            if (!sp.empty())
+                NFL_STATUS_TRY(cudaMemcpyAsync(P->sparse_items, hs, sp.size() * sizeof(WorkItem),
+                                               cudaMemcpyHostToDevice, stream));
+            if (!de.empty())
+                NFL_STATUS_TRY(cudaMemcpyAsync(P->dense_items, hd, de.size() * sizeof(WorkItem),
+                                               cudaMemcpyHostToDevice, stream));
+        }
     }
 
     // FFT buffers, twiddles, multiplier
@@ -931,11 +1032,19 @@ static nfl_status phase_finish(Builder &B) {
         const int w = int(budget / per_col);
         P->block_cols = w < 1 ? 1 : (w > kBlockCols ? kBlockCols : w);
     }
+    // interpolation grid: x0 rows padded so that every tile's halo start is a multiple of
+    // 4 reals on the tensor-core path (tile edge 4 or 8, no wrap along x0)
+    const bool gpad = d == 3 && gather_tc_available(*P) && P->tile_edge % 4 == 0 && !P->wrap[0];
+    P->g_vec = gpad ? 1 : 0;
+    P->g_off = gpad ? (P->m - 1) % 4 : 0;
+    P->g_row = gpad ? (P->g_off + (int)L0 + 3) / 4 * 4 : (int)L0;
+    P->g_elems = d == 3 ? (int64_t)P->g_row * P->L[1] * P->L[2] : P->box_elems;
     if (cudaMalloc(&P->grid, P->box_elems * grid_sz) != cudaSuccess ||
         cudaMalloc(&P->bufA, bufA * cplx_sz) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz) != cudaSuccess ||
-        cudaMalloc(&P->g, P->box_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
+        cudaMalloc(&P->g, P->g_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
         cudaMalloc(&P->twiddle, (P->ngrid / 2) * cplx_sz) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
+    NFL_STATUS_TRY(cudaMemsetAsync(P->g, 0, P->g_elems * real_sz, stream));   // the pads stay zero
     // page-locked table: twiddles (ngrid / 2 complex), cosine table (N), deconvolution (N / 2 + 1)
     const int half = P->ngrid / 2;
     NFL_STATUS_TRY(cudaHostAlloc(&B.htab, (2 * half + N + Kh) * sizeof(double), cudaHostAllocDefault));
@@ -1163,6 +1272,7 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->fft_lines_cap = P->fft_cap;
     info->slide_tiles = P->slide_tiles;
     info->block_cols = P->block_cols;
+    info->dense_items = moments_available(*P) ? P->ndense : 0;
     for (int a = 0; a < 3; ++a) {
         info->center[a] = P->center[a];
         info->box[a] = a < P->d ? P->L[a] : 1;

@@ -464,7 +464,7 @@ static cudaError_t launch_warp(Plan &P, const SpreadWarpArgs &a) {
     NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NG * 32, G::SMEM));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * P.num_sms;
-    if (grid > P.nsitems * a.ncol) grid = P.nsitems * a.ncol;
+    if (grid > a.nitems * a.ncol) grid = a.nitems * a.ncol;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, G::NG * 32, G::SMEM, P.stream>>>(a);
     return cudaGetLastError();
@@ -521,8 +521,10 @@ cudaError_t launch_spread3_warp(Plan &P, int nc) {
     a.grid_stride = P.box_elems;
     a.pts = reinterpret_cast<const PointF *>(P.pts);
     a.xs = static_cast<const float *>(P.xsort);
-    a.items = P.sitems;
-    a.nitems = P.nsitems;
+    // one column with the dense-cell spread: the warp-slice kernel takes the sparse tiles
+    const bool split = nc == 1 && moments_available(P);
+    a.items = split ? P.sparse_items : P.sitems;
+    a.nitems = split ? P.nsparse : P.nsitems;
     a.tile_start = P.tile_start;
     for (int i = 0; i < 3; ++i) {
         a.ntile[i] = P.ntile[i];
@@ -541,7 +543,9 @@ cudaError_t launch_spread3_warp(Plan &P, int nc) {
         case 2: return fixed ? launch_warp<2, 8, true>(P, a) : launch_warp<2, 8, false>(P, a);
         case 3: return fixed ? launch_warp<3, 8, true>(P, a) : launch_warp<3, 8, false>(P, a);
         case 4: return fixed ? launch_warp<4, 8, true>(P, a) : launch_warp<4, 8, false>(P, a);
-        case 6: return fixed ? launch_warp<6, 4, true>(P, a) : launch_warp<6, 4, false>(P, a);
+        case 6:
+            NFL_CUDA_TRY((fixed ? launch_warp<6, 4, true>(P, a) : launch_warp<6, 4, false>(P, a)));
+            return split ? launch_spread3_moments(P) : cudaSuccess;
     }
     return cudaErrorInvalidValue;
 }

@@ -44,6 +44,7 @@ class Info(ctypes.Structure):
         ("degree_ok", ctypes.c_int), ("device_error", ctypes.c_int), ("kernel", ctypes.c_int),
         ("k0", ctypes.c_double), ("out_scale", ctypes.c_double),
         ("fft_lines_cap", ctypes.c_int), ("slide_tiles", ctypes.c_int), ("block_cols", ctypes.c_int),
+        ("dense_items", ctypes.c_int64),
     ]
 
 

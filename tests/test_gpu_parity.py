@@ -145,6 +145,34 @@ def test_mixed_precision_forms(prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
+@pytest.mark.parametrize("dense", [False, True])
+def test_dense_cell_spread_matches_alg2_oracle(prec, tol, dense):
+    """m = 6 in 3-D: tiles with many nodes per occupied cell are spread by Chebyshev
+    moments (one-column products), the others by the warp-slice kernel; both kinds of
+    cloud against the oracle's Alg. 2, and the one-column product against a block
+    product (every tile by the warp-slice kernel)."""
+    n = 6000
+    rng = np.random.default_rng(33)
+    if dense:
+        c = rng.uniform(-1, 1, (3, 3))
+        v = c[rng.integers(0, 3, n)] + 0.02 * rng.standard_normal((n, 3))
+    else:
+        v = rng.uniform(-1, 1, (n, 3))
+    x = workloads.rhs(n, seed=34)
+    ref = fastsum.NormalizedFastsum(v, 0.5, 32, 6, 6)
+    plan = Plan(gpu(v), 0.5, 32, 6, 6, -1.0, prec)
+    info = plan.info()
+    assert (info["dense_items"] > 0) == dense
+    y = plan.apply_W(gpu(x)).cpu().numpy()
+    err = assert_close(y, ref.apply_W(x), tol, x=x)
+    print("m=6 %s dense=%s (%d dense items):" % (prec, dense, info["dense_items"]), err)
+    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)
+    X = np.stack([x, -x], axis=1)
+    Yb = plan.apply_W(gpu(X)).cpu().numpy()                 # block of 2 columns
+    assert_close(Yb[:, 0], y, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
 @pytest.mark.parametrize("m,N", [(2, 16), (3, 16), (4, 32), (6, 32), (7, 32), (5, 32), (8, 32)])
 def test_mixed_forms_each_window_size(m, N, prec, tol):
     n = 2600
@@ -372,7 +400,8 @@ def test_block_products_equal_column_products(prec, m, tol, op):
     p = Plan(gpu(v), 0.3, 32, m, m, -1.0, prec)
     inf = p.info()
     assert inf["block_cols"] == 8
-    assert p.kernels(11) == 2 * p.kernels_per_column()
+    assert p.kernels(11) == 2 * p.kernels(8)             # two blocks, one launch per stage each
+    assert p.kernels(8) <= p.kernels_per_column()
     X = np.random.default_rng(91).standard_normal((5000, 11))
     Xg = gpu(X)
     fn = getattr(p, "apply_" + op)

@@ -122,11 +122,10 @@ static nfl_status create_part(const std::vector<const Plan *> &PA, const std::ve
     const int64_t nc = nrhs;
     const size_t grid_sz = F.prec == NFL_PREC_FP32 ? 4 : 8;
     // contiguous buffers: element offsets of each member
-    std::vector<int64_t> on(G + 1, 0), ob(G + 1, 0), og(G + 1, 0), oa(G + 1, 0), obb(G + 1, 0);
+    std::vector<int64_t> on(G + 1, 0), ob(G + 1, 0), oa(G + 1, 0), obb(G + 1, 0);
     for (int g = 0; g < G; ++g) {
         on[g + 1] = on[g] + P[g]->n * nc;
         ob[g + 1] = ob[g] + P[g]->box_elems * nc;
-        og[g + 1] = og[g] + P[g]->g_elems * nc;
         oa[g + 1] = oa[g] + P[g]->bufA_elems * nc;
         obb[g + 1] = obb[g] + P[g]->bufB_elems * nc;
     }
@@ -139,13 +138,11 @@ static nfl_status create_part(const std::vector<const Plan *> &PA, const std::ve
         cudaMalloc(&B->abs_all, (size_t)G * nc * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&B->xs_all, (size_t)on[G] * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&B->zd_all, (size_t)on[G] * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&B->g_all, (size_t)og[G] * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&B->g_all, (size_t)ob[G] * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&B->bufA_all, (size_t)oa[G] * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&B->bufB_all, (size_t)obb[G] * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&B->counter, 2 * sizeof(unsigned)) != cudaSuccess)
         return fail(NFL_ERR_OUT_OF_MEMORY);
-    if (cudaMemset(B->g_all, 0, (size_t)og[G] * sizeof(float)) != cudaSuccess)   // the pads stay zero
-        return fail(NFL_ERR_CUDA);
     // member descriptors, item lists, staging and FFT CTA offsets
     std::vector<BatchPlanDev> desc(G);
     std::vector<BatchItem> sitems, gitems;
@@ -169,11 +166,7 @@ static nfl_status create_part(const std::vector<const Plan *> &PA, const std::ve
         D.xs = static_cast<float *>(B->xs_all) + on[g];
         D.zd = static_cast<double *>(B->zd_all) + on[g];
         D.grid = static_cast<unsigned char *>(B->grid_all) + ob[g] * grid_sz;
-        D.g = static_cast<float *>(B->g_all) + og[g];
-        D.g_elems = Q.g_elems;
-        D.g_row = Q.g_row;
-        D.g_off = Q.g_off;
-        D.gvec = Q.g_vec;
+        D.g = static_cast<float *>(B->g_all) + ob[g];
         D.abs_sum = B->abs_all + (size_t)g * nc;
         D.n = Q.n;
         D.box = Q.box_elems;

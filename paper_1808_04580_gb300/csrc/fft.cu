@@ -354,12 +354,8 @@ static cudaError_t launch_fft_t(Plan &P, int nc) {
     PassArgs i1 = base;
     i1.in = P.bufB; i1.out = P.g;
     i1.nA = (int)L1; i1.nB = (int)L0; i1.sA = L0 * K2; i1.sB = K2; i1.Lin = (int)K2;
-    // interpolation grid rows of g_row reals, x0 at g_off + x0
-    i1.oC = L1 * P.g_row; i1.oA = P.g_row; i1.Lout = (int)L2;
-    i1 = with_strides(i1);
-    i1.out = static_cast<T *>(P.g) + P.g_off;
-    i1.out_cstride = P.g_elems;
-    return run_pass<T, T, P_INV_C2R>(P, i1, nc);
+    i1.oC = L1 * L0; i1.oA = L0; i1.Lout = (int)L2;
+    return run_pass<T, T, P_INV_C2R>(P, with_strides(i1), nc);
 }
 
 // Launch shape of a pass of line length n at cap grid points per CTA: complex lines
@@ -404,9 +400,9 @@ int fft_passes_3d(const Plan &P, const void *grid, void *bufA, void *bufB, void 
     f[3].nA = (int)L0; f[3].nB = (int)K2; f[3].sA = K2 * K1; f[3].sB = K1; f[3].Lin = (int)K1;
     f[3].oC = L0 * K2; f[3].oA = K2; f[3].Lout = (int)L1;
     f[4] = base;
-    f[4].in = bufB; f[4].out = static_cast<float *>(g) + P.g_off; f[4].in_cstride = sb; f[4].out_cstride = P.g_elems;
+    f[4].in = bufB; f[4].out = g; f[4].in_cstride = sb; f[4].out_cstride = sg;
     f[4].nA = (int)L1; f[4].nB = (int)L0; f[4].sA = L0 * K2; f[4].sB = K2; f[4].Lin = (int)K2;
-    f[4].oC = L1 * P.g_row; f[4].oA = P.g_row; f[4].Lout = (int)L2;
+    f[4].oC = L1 * L0; f[4].oA = L0; f[4].Lout = (int)L2;
     for (int i = 0; i < 5; ++i) {
         int threads = 0, smem = 0;
         pass_shape(cap, n, i == 0 || i == 4, sizeof(float2), f[i].BB, threads, smem);

@@ -44,7 +44,6 @@ struct GatherTCArgs {
     int64_t nitems;   // items of one column; the grid takes nitems * ncol
     int ncol;         // columns of a block product (item it: item it / ncol, column it % ncol)
     int64_t g_stride, z_stride, ldy;   // column strides of g, zd and y
-    int g_row, g_off, gvec;            // interpolation grid rows (see the B operand)
     int ntile[3];
     int L[3];
     int wrap[3];
@@ -99,7 +98,6 @@ struct GatherItemPlan {
     int *error_flag;
     WorkItem w;
     int ntile[3], L[3], wrap[3];
-    int g_row, g_off, gvec;
 };
 
 #define GT_L(i) (BATCH ? ip.L[i] : a.L[i])
@@ -164,10 +162,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 ip.perm = D.perm;
                 ip.dinv = D.dinv;
                 ip.zc = D.zd + c0 * D.n;
-                ip.gc = D.g + c0 * D.g_elems;
-                ip.g_row = D.g_row;
-                ip.g_off = D.g_off;
-                ip.gvec = D.gvec;
+                ip.gc = D.g + c0 * D.box;
                 ip.yc = D.y + c0 * D.ldy;
                 ip.out_scale = D.out_scale;
                 ip.error_flag = D.error_flag;
@@ -190,35 +185,8 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
         int tc[3];
         tile_coords<3>(w.tile, BATCH ? ip.ntile : a.ntile, tc);
         // B operand: row n = b PA + c holds G[a][(b, c)] for k = a = 0..15, split into TF32
-        // hi/lo parts; zero beyond PA^2 rows and outside the box (and beyond PA along a,
-        // where the A operand is zero).  The grid's x0 rows have grow reals with x0 at
-        // goff + x0; with gvec every tile's halo starts on a 16-byte boundary, so each
-        // (row, 4 reals) is one float4 load and a warp's loads cover 8 rows contiguously.
-        const int grow = BATCH ? ip.g_row : a.g_row, goff = BATCH ? ip.g_off : a.g_off;
-        if (TE % 4 == 0 && (BATCH ? ip.gvec : a.gvec)) {
-            for (int e = tid; e < NH * N * 4; e += 128) {
-                const int n = e >> 2, ch = e & 3;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (n < NCOL) {
-                    const int bq = n / PA, cq = n - bq * PA;
-                    int p1 = tc[1] * TE - (M - 1) + bq;
-                    int p2 = tc[2] * TE - (M - 1) + cq;
-                    if (GT_WRAP(1)) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
-                    if (GT_WRAP(2)) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
-                    const int q0 = tc[0] * TE - (M - 1) + goff + 4 * ch;   // a multiple of 4
-                    if (p1 >= 0 && p1 < GT_L(1) && p2 >= 0 && p2 < GT_L(2) && q0 >= 0 && q0 + 4 <= grow)
-                        v = __ldg(reinterpret_cast<const float4 *>(gc + ((int64_t)p2 * GT_L(1) + p1) * grow + q0));
-                }
-                float4 h, l;
-                h.x = to_tf32(v.x); l.x = to_tf32(v.x - h.x);
-                h.y = to_tf32(v.y); l.y = to_tf32(v.y - h.y);
-                h.z = to_tf32(v.z); l.z = to_tf32(v.z - h.z);
-                h.w = to_tf32(v.w); l.w = to_tf32(v.w - h.w);
-                const uint32_t off = kmajor_off(n, 4 * ch);
-                *reinterpret_cast<float4 *>(sB_hi + off) = h;
-                *reinterpret_cast<float4 *>(sB_lo + off) = l;
-            }
-        } else for (int n = tid; n < NH * N; n += 128) {
+        // hi/lo parts; zero beyond PA^2 rows, beyond PA along a and outside the box
+        for (int n = tid; n < NH * N; n += 128) {
             const bool used = n < NCOL;
             const int bq = used ? n / PA : 0, cq = used ? n - bq * PA : 0;
             int p1 = tc[1] * TE - (M - 1) + bq;
@@ -226,7 +194,7 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
             if (GT_WRAP(1)) p1 = ((p1 % a.ngrid) + a.ngrid) % a.ngrid;
             if (GT_WRAP(2)) p2 = ((p2 % a.ngrid) + a.ngrid) % a.ngrid;
             const bool ok12 = used && p1 >= 0 && p1 < GT_L(1) && p2 >= 0 && p2 < GT_L(2);
-            const float *src = gc + ((int64_t)(ok12 ? p2 : 0) * GT_L(1) + (ok12 ? p1 : 0)) * grow + goff;
+            const float *src = gc + ((int64_t)(ok12 ? p2 : 0) * GT_L(1) + (ok12 ? p1 : 0)) * GT_L(0);
             float v[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -509,10 +477,7 @@ bool gather_tc_available(const Plan &P) {
 cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y, int64_t ldy, int nc) {
     GatherTCArgs a;
     a.ncol = nc;
-    a.g_stride = P.g_elems;
-    a.g_row = P.g_row;
-    a.g_off = P.g_off;
-    a.gvec = P.g_vec;
+    a.g_stride = P.box_elems;
     a.z_stride = P.n;
     a.ldy = ldy;
     a.pts = reinterpret_cast<const PointF *>(P.pts);

@@ -119,11 +119,6 @@ struct Plan {
     void *bufA = nullptr;       // complex FFT intermediates
     void *bufB = nullptr;
     void *g = nullptr;          // interpolation grid (real, FFT type)
-    // interpolation grid layout: rows of g_row reals along x0 with x0 at g_off + x0 (the
-    // rest zero), so that on the tensor-core path every tile's halo starts 16-byte aligned
-    int g_off = 0, g_row = 0;
-    int g_vec = 0;              // 1: rows aligned so, the interpolation loads them as float4
-    int64_t g_elems = 0;        // per column
     void *mult = nullptr;       // fused multiplier M_eff (real, FFT type)
     void *twiddle = nullptr;    // e^{-2 pi i q / ngrid}, q < ngrid/2 (complex, FFT type)
     double *scratch = nullptr;  // small device scalars (reductions, fixed-point scale)
@@ -200,9 +195,7 @@ struct BatchPlanDev {
     float *xs;                    // staged x~, column c at xs + c n
     double *zd;                   // staged epilogue z, column c at zd + c n
     void *grid;                   // spreading grid, column c at grid + c box
-    float *g;                     // interpolation grid, column c at g + c g_elems
-    int64_t g_elems;
-    int g_row, g_off, gvec;       // its row length, x0 offset, 16-byte aligned rows
+    float *g;                     // interpolation grid, column c at g + c box
     double *abs_sum;              // FP32C scale sums, one per column
     int64_t n, box;
     int ntile[3], L[3], wrap[3];

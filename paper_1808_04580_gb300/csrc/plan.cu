@@ -269,15 +269,13 @@ nfl_status ensure_columns(Plan &P, int nc) {
         cudaMalloc(&P.blk.xsorted, P.n * 8 * bc) != cudaSuccess ||
         cudaMalloc(&P.blk.bufA, P.bufA_elems * cplx_sz * bc) != cudaSuccess ||
         cudaMalloc(&P.blk.bufB, P.bufB_elems * cplx_sz * bc) != cudaSuccess ||
-        cudaMalloc(&P.blk.g, P.g_elems * real_sz * bc) != cudaSuccess ||
+        cudaMalloc(&P.blk.g, P.box_elems * real_sz * bc) != cudaSuccess ||
         cudaMalloc(&P.blk.grid, P.box_elems * grid_sz * bc) != cudaSuccess) {
         cudaFree(P.blk.xsort); cudaFree(P.blk.xsorted); cudaFree(P.blk.bufA);
         cudaFree(P.blk.bufB); cudaFree(P.blk.g); cudaFree(P.blk.grid);
         P.blk = BlockBuffers{};
         return NFL_ERR_OUT_OF_MEMORY;
     }
-    // the pads of the interpolation grids stay zero
-    if (cudaMemsetAsync(P.blk.g, 0, P.g_elems * real_sz * bc, P.stream) != cudaSuccess) return NFL_ERR_CUDA;
     return NFL_OK;
 }
 
@@ -1032,19 +1030,11 @@ static nfl_status phase_finish(Builder &B) {
         const int w = int(budget / per_col);
         P->block_cols = w < 1 ? 1 : (w > kBlockCols ? kBlockCols : w);
     }
-    // interpolation grid: x0 rows padded so that every tile's halo start is a multiple of
-    // 4 reals on the tensor-core path (tile edge 4 or 8, no wrap along x0)
-    const bool gpad = d == 3 && gather_tc_available(*P) && P->tile_edge % 4 == 0 && !P->wrap[0];
-    P->g_vec = gpad ? 1 : 0;
-    P->g_off = gpad ? (P->m - 1) % 4 : 0;
-    P->g_row = gpad ? (P->g_off + (int)L0 + 3) / 4 * 4 : (int)L0;
-    P->g_elems = d == 3 ? (int64_t)P->g_row * P->L[1] * P->L[2] : P->box_elems;
     if (cudaMalloc(&P->grid, P->box_elems * grid_sz) != cudaSuccess ||
         cudaMalloc(&P->bufA, bufA * cplx_sz) != cudaSuccess || cudaMalloc(&P->bufB, bufB * cplx_sz) != cudaSuccess ||
-        cudaMalloc(&P->g, P->g_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
+        cudaMalloc(&P->g, P->box_elems * real_sz) != cudaSuccess || cudaMalloc(&P->mult, mult * real_sz) != cudaSuccess ||
         cudaMalloc(&P->twiddle, (P->ngrid / 2) * cplx_sz) != cudaSuccess)
         return NFL_ERR_OUT_OF_MEMORY;
-    NFL_STATUS_TRY(cudaMemsetAsync(P->g, 0, P->g_elems * real_sz, stream));   // the pads stay zero
     // page-locked table: twiddles (ngrid / 2 complex), cosine table (N), deconvolution (N / 2 + 1)
     const int half = P->ngrid / 2;
     NFL_STATUS_TRY(cudaHostAlloc(&B.htab, (2 * half + N + Kh) * sizeof(double), cudaHostAllocDefault));

@@ -38,6 +38,7 @@ constexpr int PA_M = TE_M + 2 * MM - 1;                 // 15
 constexpr int PA3_M = PA_M * PA_M * PA_M;
 constexpr int TILE_M = (PA3_M + 3) / 4 * 4;
 constexpr int NGM = 4, SM_ = 32;
+constexpr int kMomentRun = 256;                         // most nodes summed into one set of moments
 constexpr int ROW = 44;                                 // staged floats per node (odd multiple of 16 B)
 constexpr int A_STRIDE = 72, B_STRIDE = 104;            // transform buffer strides (conflict-free)
 constexpr int BUF = TAPS_M * B_STRIDE;                  // 1248 floats
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(NGM * 32, 2) spread3_moments(MomentArgs a) {
 
     // the moments of cell o -> its 12^3 support block, added to this warp's tile copy
     auto flush = [&](int o) {
+        if (fresh) return;                    // nothing summed since the last flush (warp-uniform)
         const int s0 = o & 255, s1 = (o >> 8) & 255, s2 = o >> 16;
         __syncwarp();
         {
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(NGM * 32, 2) spread3_moments(MomentArgs a) {
         const WorkItem w = a.items[it];
         int tc[3];
         tile_coords<3>(w.tile, a.ntile, tc);
-        int cur = -1;
+        int cur = -1, since = 0;
         // this warp's quarter of the chunk; this lane's node of the next slice, loaded one slice ahead
         const int share = (w.count + NGM - 1) / NGM;
         int base = w.start + g * share;
@@ -243,6 +245,7 @@ __global__ void __launch_bounds__(NGM * 32, 2) spread3_moments(MomentArgs a) {
                 if (oi != cur) {
                     if (cur >= 0) flush(cur);
                     cur = oi;
+                    since = 0;
                 }
                 int q = i;
                 if (fresh) node(q++, std::true_type{});
@@ -252,6 +255,13 @@ __global__ void __launch_bounds__(NGM * 32, 2) spread3_moments(MomentArgs a) {
                 i = j;
             }
             __syncwarp();                             // the next slice overwrites the staged rows
+            // no FP32 moment sum runs over more than kMomentRun nodes: a long run of one
+            // cell is expanded and carried into the tile copy in pieces
+            since += cnt;
+            if (since >= kMomentRun && cur >= 0) {
+                flush(cur);
+                since = 0;
+            }
         }
         if (cur >= 0) flush(cur);
         __syncthreads();

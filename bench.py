@@ -578,7 +578,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "box": info["box"], "work_items": info["work_items"],
                        "launch_params": {"fft_lines_cap": info["fft_lines_cap"], "slide_tiles": info["slide_tiles"],
-                                         "block_cols": info["block_cols"],
+                                         "block_cols": info["block_cols"], "chunk": info["chunk"],
+                                         "dense_cell": info["dense_cell"], "dense_chunk": info["dense_chunk"],
+                                         "dense_items": info["dense_items"],
                                          "autotuned": tuned is not None}},
             "point_rhs_per_s": value * n,
             "stage_ms_per_column": {"prep": stages["prep"] / max(1, stages["columns"]), "spread": spread_ms,

@@ -311,6 +311,65 @@ nfl_status nfl_plan_autotune(nfl_plan *plan, double *best_ms) {
         }
         P.fft_cap = best_cap;
     }
+    if (st == NFL_OK && P.d == 3) {
+        // work-item size: chunks of at most 2048, 4096 or 8192 nodes
+        const int chunks[3] = {2048, 4096, 8192};
+        int best_chunk = P.chunk;
+        best = 1e30;
+        for (int c : chunks) {
+            st = nfl::rechunk_items(P, c);
+            if (st != NFL_OK) break;
+            double ms = 0.0;
+            st = time_config(ms);
+            if (st != NFL_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_chunk = c;
+            }
+        }
+        const nfl_status rs = nfl::rechunk_items(P, best_chunk);
+        if (st == NFL_OK) st = rs;
+    }
+    if (st == NFL_OK && nfl::moments_available(P)) {
+        // nodes per occupied cell from which a tile goes to the dense-cell spread
+        const int dens[3] = {16, 32, 64};
+        int best_dense = P.dense_cell;
+        best = 1e30;
+        for (int dv : dens) {
+            P.dense_cell = dv;
+            st = nfl::rebuild_spread_items(P);
+            if (st != NFL_OK) break;
+            double ms = 0.0;
+            st = time_config(ms);
+            if (st != NFL_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_dense = dv;
+            }
+        }
+        P.dense_cell = best_dense;
+        nfl_status rs = nfl::rebuild_spread_items(P);
+        if (st == NFL_OK) st = rs;
+        // nodes per work item of the dense-cell spread
+        const int dch[3] = {1024, 2048, 8192};
+        int best_dch = P.dense_chunk;
+        best = 1e30;
+        for (int c = 0; c < 3 && st == NFL_OK; ++c) {
+            P.dense_chunk = dch[c];
+            st = nfl::rebuild_spread_items(P);
+            if (st != NFL_OK) break;
+            double ms = 0.0;
+            st = time_config(ms);
+            if (st != NFL_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_dch = dch[c];
+            }
+        }
+        P.dense_chunk = best_dch;
+        rs = nfl::rebuild_spread_items(P);
+        if (st == NFL_OK) st = rs;
+    }
     if (st == NFL_OK && nfl::spread_warp_available(P)) {
         const int runs[4] = {1, 4, 8, 16};
         const int before = P.slide_tiles;

@@ -37,7 +37,7 @@ constexpr int kHostSlots = 3;   // device staging slots per direction for host-b
 constexpr int kBlockCols = 8;   // columns a block product takes through each stage in one launch
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 constexpr int kCheb = 8;        // Chebyshev basis of the dense-cell spread (degree 7)
-constexpr int kDenseCell = 32;  // nodes per occupied cell from which a tile is spread by moments
+constexpr int kDenseCell = 64;  // nodes per occupied cell from which a tile is spread by moments
 
 // Per-column buffers of block products (see Plan::blk).
 struct BlockBuffers {
@@ -82,6 +82,9 @@ struct Plan {
     int64_t nsparse = 0, ndense = 0;
     WorkItem *sparse_items = nullptr, *dense_items = nullptr;
     int slide_tiles = 8;                // most tiles in one sliding run of the warp spread
+    int chunk = 8192;                   // most nodes in one work item (tile chunk, sliding run)
+    int dense_cell = kDenseCell;        // nodes per occupied cell from which a tile is dense
+    int dense_chunk = 8192;             // most nodes in one work item of the dense-cell spread
     int fft_cap = 512;                  // FFT passes: grid points per CTA
 
     // tile-sorted nodes
@@ -270,6 +273,8 @@ nfl_status ensure_columns(Plan &P, int nc);
 
 // warp-spread work items from tile_items with runs of at most slide_tiles tiles
 nfl_status rebuild_spread_items(Plan &P);
+// re-split every tile into chunks of at most `chunk` nodes (host lists and device copies)
+nfl_status rechunk_items(Plan &P, int chunk);
 
 // the warp spread's work list built from tile_items (host)
 std::vector<WorkItem> spread_item_list(const Plan &P);

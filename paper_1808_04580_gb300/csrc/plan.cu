@@ -214,10 +214,10 @@ __global__ void occupied_cells(const int64_t *kstart, int64_t ntiles, int cells_
 
 // Work items of the warp-slice spread from the per-tile chunks (in tile order): a tile
 // with several chunks keeps them as items of one tile; runs of single-chunk tiles that
-// follow each other along axis 2 in one row are joined while they hold at most kChunk
+// follow each other along axis 2 in one row are joined while they hold at most `chunk`
 // nodes together (pad = tiles in the run), so the spread slides one tile window along
 // the run and merges only the planes that leave it.
-static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2, int max_tiles) {
+static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2, int max_tiles, int chunk) {
     std::vector<WorkItem> s;
     size_t i = 0;
     while (i < h.size()) {
@@ -239,7 +239,7 @@ static std::vector<WorkItem> slide_items(const std::vector<WorkItem> &h, int nt2
             const WorkItem &x = h[i];
             if (x.tile != g.tile + g.pad || x.tile % nt2 == 0) break;        // not the next tile of the row
             if (i + 1 < h.size() && h[i + 1].tile == x.tile) break;          // a tile of several chunks
-            if (g.count + x.count > kChunk) break;
+            if (g.count + x.count > chunk) break;
             g.count += x.count;
             ++g.pad;
             ++i;
@@ -281,7 +281,7 @@ nfl_status ensure_columns(Plan &P, int nc) {
 
 // The warp spread's work list: runs of at most slide_tiles tiles, largest first.
 std::vector<WorkItem> spread_item_list(const Plan &P) {
-    std::vector<WorkItem> s = slide_items(P.tile_items, P.ntile[P.d - 1], P.slide_tiles);
+    std::vector<WorkItem> s = slide_items(P.tile_items, P.ntile[P.d - 1], P.slide_tiles, P.chunk);
     std::stable_sort(s.begin(), s.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
     return s;
 }
@@ -290,7 +290,7 @@ bool moments_available(const Plan &P) {
     return spread_warp_available(P) && P.m == 6 && !P.bf16_taps && !P.tile_cells.empty();
 }
 
-// Dense tiles (at least kDenseCell nodes per occupied cell) go to the dense-cell
+// Dense tiles (at least dense_cell nodes per occupied cell) go to the dense-cell
 // spread chunk by chunk, largest first; the other tiles keep the sliding runs.
 void split_item_lists(const Plan &P, std::vector<WorkItem> &sparse, std::vector<WorkItem> &dense) {
     std::vector<WorkItem> rest;
@@ -300,14 +300,18 @@ void split_item_lists(const Plan &P, std::vector<WorkItem> &sparse, std::vector<
     for (const WorkItem &w : P.tile_items) tile_nodes[w.tile] += w.count;
     for (const WorkItem &w : P.tile_items) {
         const int32_t cells = P.tile_cells[w.tile];
-        if (cells > 0 && tile_nodes[w.tile] >= (int64_t)kDenseCell * cells) dense.push_back(w);
-        else rest.push_back(w);
+        if (cells > 0 && tile_nodes[w.tile] >= (int64_t)P.dense_cell * cells) {
+            // dense chunks in pieces of at most dense_chunk nodes: more CTAs for the dense tiles
+            for (int32_t s0 = 0; s0 < w.count; s0 += P.dense_chunk)
+                dense.push_back(WorkItem{w.tile, w.start + s0, std::min(P.dense_chunk, w.count - s0), 1});
+        } else {
+            rest.push_back(w);
+        }
     }
-    sparse = slide_items(rest, P.ntile[P.d - 1], P.slide_tiles);
+    sparse = slide_items(rest, P.ntile[P.d - 1], P.slide_tiles, P.chunk);
     const auto by_size = [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; };
     std::stable_sort(sparse.begin(), sparse.end(), by_size);
     std::stable_sort(dense.begin(), dense.end(), by_size);
-    for (WorkItem &w : dense) w.pad = 1;
 }
 
 // (Re)allocates dst for cnt items when it holds fewer (old lists are never read again)
@@ -351,6 +355,31 @@ nfl_status rebuild_spread_items(Plan &P) {
         return NFL_ERR_CUDA;
     P.nsitems = (int64_t)s.size();
     return NFL_OK;
+}
+
+nfl_status rechunk_items(Plan &P, int chunk) {
+    if (chunk < 256 || chunk > kChunk) return NFL_ERR_INVALID_ARG;
+    std::vector<WorkItem> h;
+    size_t i = 0;
+    while (i < P.tile_items.size()) {
+        // the tile's node range from its consecutive chunks
+        const int32_t tile = P.tile_items[i].tile, start = P.tile_items[i].start;
+        int32_t end = start;
+        for (; i < P.tile_items.size() && P.tile_items[i].tile == tile; ++i)
+            end = P.tile_items[i].start + P.tile_items[i].count;
+        for (int32_t s = start; s < end; s += chunk) h.push_back(WorkItem{tile, s, std::min(chunk, end - s), 0});
+    }
+    P.chunk = chunk;
+    P.tile_items = h;
+    std::vector<WorkItem> sorted = h;
+    std::stable_sort(sorted.begin(), sorted.end(), [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; });
+    int64_t have = P.nitems;
+    if (ensure_list(P.items, have, (int64_t)sorted.size()) != NFL_OK) return NFL_ERR_OUT_OF_MEMORY;
+    if (cudaStreamSynchronize(P.stream) != cudaSuccess ||
+        cudaMemcpy(P.items, sorted.data(), sorted.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess)
+        return NFL_ERR_CUDA;
+    P.nitems = (int64_t)sorted.size();
+    return rebuild_spread_items(P);
 }
 
 __global__ void chunks_per_tile(const int32_t *count, int64_t ntiles, int32_t *chunks, unsigned long long *nonempty) {
@@ -1263,6 +1292,9 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->slide_tiles = P->slide_tiles;
     info->block_cols = P->block_cols;
     info->dense_items = moments_available(*P) ? P->ndense : 0;
+    info->chunk = P->chunk;
+    info->dense_cell = P->dense_cell;
+    info->dense_chunk = P->dense_chunk;
     for (int a = 0; a < 3; ++a) {
         info->center[a] = P->center[a];
         info->box[a] = a < P->d ? P->L[a] : 1;

@@ -44,7 +44,8 @@ class Info(ctypes.Structure):
         ("degree_ok", ctypes.c_int), ("device_error", ctypes.c_int), ("kernel", ctypes.c_int),
         ("k0", ctypes.c_double), ("out_scale", ctypes.c_double),
         ("fft_lines_cap", ctypes.c_int), ("slide_tiles", ctypes.c_int), ("block_cols", ctypes.c_int),
-        ("dense_items", ctypes.c_int64),
+        ("dense_items", ctypes.c_int64), ("chunk", ctypes.c_int), ("dense_cell", ctypes.c_int),
+        ("dense_chunk", ctypes.c_int),
     ]
 
 
@@ -200,7 +201,8 @@ class Plan:
         ms = ctypes.c_double(0.0)
         _check(_lib().nfl_plan_autotune(self._h, ctypes.byref(ms)), "nfl_plan_autotune")
         inf = self.info()
-        return dict(fft_lines_cap=inf["fft_lines_cap"], slide_tiles=inf["slide_tiles"], best_ms=ms.value)
+        return dict(fft_lines_cap=inf["fft_lines_cap"], slide_tiles=inf["slide_tiles"], chunk=inf["chunk"],
+                    dense_cell=inf["dense_cell"], dense_chunk=inf["dense_chunk"], best_ms=ms.value)
 
     def set_profiling(self, enable=True):
         _check(_lib().nfl_plan_set_profiling(self._h, 1 if enable else 0), "nfl_plan_set_profiling")

@@ -376,8 +376,9 @@ def test_bf16w_matches_bf16_tap_oracle(m, N, d):
 
 @pytest.mark.parametrize("prec,m,tol", [("fp32c", 6, 2e-6), ("fp32", 4, 1e-5), ("fp64", 4, 1e-10)])
 def test_autotune_keeps_the_products(prec, m, tol):
-    """nfl_plan_autotune picks FFT CTA size and sliding-run length among its
-    candidates; the products stay those of the oracle's Alg. 2."""
+    """nfl_plan_autotune picks FFT CTA size, work-item size, dense-cell threshold and
+    sliding-run length among its candidates; the products stay those of the oracle's
+    Alg. 2."""
     v = _cloud("clusters", 6000, 3, seed=77)
     x = np.random.default_rng(78).standard_normal(6000)
     p = Plan(gpu(v), 0.3, 32, m, m, -1.0, prec)
@@ -386,6 +387,8 @@ def test_autotune_keeps_the_products(prec, m, tol):
     t = p.autotune()
     assert t["fft_lines_cap"] in (256, 512, 1024, 2048)
     assert t["slide_tiles"] in (1, 4, 8, 16)
+    assert t["chunk"] in (2048, 4096, 8192) and t["dense_cell"] in (16, 32, 64)
+    assert p.info()["work_items"] >= before["work_items"]
     assert t["best_ms"] > 0.0
     ref = fastsum.NormalizedFastsum(v, 0.3, 32, m, m).apply_W(x)
     assert_close(p.apply_W(gpu(x)).cpu().numpy(), ref, tol)

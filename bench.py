@@ -443,10 +443,14 @@ def main():
     else:
         peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         peak_note = "derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no measured FP32 rate)"
-    kname, src, summary = (("spread3_warp", "spread3_warp.cu", "spread3_warp_ball10M.md") if dom == "spread"
-                           else ("gather3_tc", "gather_tc.cu", "gather3_tc_ball10M.md"))
-    kernel_file = os.path.join(ROOT, "paper_1808_04580_gb300", "csrc", src)
-    traffic = profiled_traffic(summary, kernel_file) if n == 10_000_000 else None
+    # the spread stage is two kernels (sparse tiles: warp-slice; dense tiles: Chebyshev moments)
+    parts = ([("spread3_warp.cu", "spread3_warp_ball10M.md"), ("spread3_moments.cu", "spread3_moments_ball10M.md")]
+             if dom == "spread" else [("gather_tc.cu", "gather3_tc_ball10M.md")])
+    kname = "spread3_warp + spread3_moments" if dom == "spread" else "gather3_tc"
+    traffic = 0.0 if n == 10_000_000 else None
+    for src, summary in parts:
+        t = profiled_traffic(summary, os.path.join(ROOT, "paper_1808_04580_gb300", "csrc", src)) if traffic is not None else None
+        traffic = None if t is None else traffic + t
     if traffic is not None:
         traffic *= cpl                # the profile is of a one-column launch
     # algorithmic HBM bytes per column: the spread reads the 16-byte node record and the

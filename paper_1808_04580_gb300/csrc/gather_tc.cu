@@ -215,8 +215,24 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
             }
         }
 
-        for (int base = w.start; base < w.start + w.count && !failed; base += 128) {
-            const int nb = min(128, w.start + w.count - base);
+        // this thread's node record (and epilogue operands) of the item's first batch, then of
+        // each next batch one batch ahead, so the loads are in flight during a batch's MMAs
+        const int wend = w.start + w.count;
+        PointF pn = {{0.f, 0.f, 0.f}, 0};
+        int in_ = 0;
+        double zn = 0.0, dn = 0.0;
+        auto fetch = [&](int b) {
+            const int k = b + tid;
+            if (k < wend) {
+                pn = (BATCH ? ip.pts : a.pts)[k];
+                in_ = (BATCH ? ip.perm : a.perm)[k];
+                if (a.op != OP_DEGREE) zn = zc[k];
+                if (a.op == OP_A || a.op == OP_LS) dn = (BATCH ? ip.dinv : a.dinv)[k];
+            }
+        };
+        fetch(w.start);
+        for (int base = w.start; base < wend && !failed; base += 128) {
+            const int nb = min(128, wend - base);
             const bool live = tid < nb;
             float w1p[PA], w2p[PA];
             int kq = 0, iq = 0;
@@ -226,16 +242,17 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 int s0 = 0, s1 = 0, s2 = 0;
                 if (live) {
                     kq = base + tid;
-                    const PointF p = (BATCH ? ip.pts : a.pts)[kq];
-                    // epilogue operands, loaded now and used after the contraction
-                    iq = (BATCH ? ip.perm : a.perm)[kq];
-                    if (a.op != OP_DEGREE) zq = zc[kq];
-                    if (a.op == OP_A || a.op == OP_LS) dq = (BATCH ? ip.dinv : a.dinv)[kq];
+                    const PointF p = pn;
+                    // epilogue operands, loaded a batch ahead and used after the contraction
+                    iq = in_;
+                    zq = zn;
+                    dq = dn;
                     s0 = cell_axis(p.cell, 0) - tc[0] * TE;
                     s1 = cell_axis(p.cell, 1) - tc[1] * TE;
                     s2 = cell_axis(p.cell, 2) - tc[2] * TE;
                     f0 = p.f[0]; f1 = p.f[1]; f2 = p.f[2];
                 }
+                fetch(base + 128);
                 // window taps: Horner in t = 2f - 1, two taps per fma.rn.f32x2; axes 1 and 2
                 // first (kept for the contraction), then axis 0 (the A operand)
                 const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);

@@ -11,10 +11,13 @@ namespace nfl {
 int kernels_per_column(const Plan &P) {
     const int passes = P.d == 1 ? 1 : (P.d == 2 ? 3 : 5);
     const bool staged = P.d == 3 && column_tile_edge(P.m) == P.tile_edge;
-    // the one-column spread with dense cells launches the warp-slice kernel for the sparse
-    // tiles and the moment kernel for the dense ones (each only when it has items)
+    // the one-column spread and interpolation with dense cells launch the warp-slice and
+    // tensor-core kernels for the sparse tiles and the moment kernels for the dense ones
+    // (the spreads each only when they have items; the tensor-core launch always counts)
+    const bool split = moments_available(P) && P.ndense > 0;
     const int spreads = moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.ndense > 0 ? 1 : 0) : 1;
-    return (staged || P.prec == NFL_PREC_FP32C ? 1 : 0) + spreads + passes + 1;
+    const int gathers = split && gather_tc_available(P) ? 2 : 1;
+    return (staged || P.prec == NFL_PREC_FP32C ? 1 : 0) + spreads + passes + gathers;
 }
 
 // stage events: 5 per timed product (before prep, spread, fft, gather, after); a
@@ -434,9 +437,12 @@ nfl_status nfl_plan_kernels(const nfl_plan *plan, int nrhs, int *kernels) {
     const nfl::Plan &P = *reinterpret_cast<const nfl::Plan *>(plan);
     if (nrhs > 1 && P.block_cols > 1 && nfl::block_path_available(P)) {
         const int blocks = (nrhs + P.block_cols - 1) / P.block_cols;
-        // one launch per stage and block (a block spreads every tile with the warp-slice kernel)
+        // one launch per stage and block (a block spreads and interpolates every tile with
+        // the warp-slice and tensor-core kernels)
+        const bool split = nfl::moments_available(P) && P.ndense > 0;
         const int spreads = nfl::moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.ndense > 0 ? 1 : 0) : 1;
-        *kernels = blocks * (nfl::kernels_per_column(P) - spreads + 1);
+        const int gathers = split && nfl::gather_tc_available(P) ? 2 : 1;
+        *kernels = blocks * (nfl::kernels_per_column(P) - spreads + 1 - gathers + 1);
     } else {
         *kernels = nrhs * nfl::kernels_per_column(P);
     }

@@ -504,8 +504,10 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y, int64_
     a.dinv = P.dinv_sorted;
     a.degree_out = P.degree;
     a.dinv_out = P.dinv_sorted;
-    a.items = P.items;
-    a.nitems = P.nitems;
+    // a one-column interpolation with dense cells leaves the dense tiles to the moment kernel
+    const bool split = nc == 1 && moments_available(P) && P.ndense > 0;
+    a.items = split ? P.gsparse_items : P.items;
+    a.nitems = split ? P.ngsparse : P.nitems;
     for (int i = 0; i < 3; ++i) {
         a.ntile[i] = P.ntile[i];
         a.L[i] = P.L[i];
@@ -526,7 +528,9 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y, int64_
         case 2: return launch_tc<2, 8>(P, a);
         case 3: return launch_tc<3, 8>(P, a);
         case 4: return launch_tc<4, 8>(P, a);
-        case 6: return launch_tc<6, 4>(P, a);
+        case 6:
+            NFL_CUDA_TRY((launch_tc<6, 4>(P, a)));
+            return split ? launch_gather3_moments(P, op, y) : cudaSuccess;
         case 7: return launch_tc<7, 2>(P, a);
     }
     return cudaErrorInvalidValue;

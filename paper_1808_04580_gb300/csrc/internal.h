@@ -37,7 +37,8 @@ constexpr int kHostSlots = 3;   // device staging slots per direction for host-b
 constexpr int kBlockCols = 8;   // columns a block product takes through each stage in one launch
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 constexpr int kCheb = 8;        // Chebyshev basis of the dense-cell spread (degree 7)
-constexpr int kDenseCell = 64;  // nodes per occupied cell from which a tile is spread by moments
+constexpr int kDenseCell = 64;       // nodes per occupied cell from which a tile is spread by moments
+constexpr int kGatherPiece = 2048;   // most nodes per work item (one slab) of the dense-cell interpolation
 
 // Per-column buffers of block products (see Plan::blk).
 struct BlockBuffers {
@@ -76,11 +77,18 @@ struct Plan {
     WorkItem *sitems = nullptr;
     int32_t *tile_start = nullptr;      // first sorted node of each tile; [tiles_total] = n
     std::vector<WorkItem> tile_items;   // host copy of the per-tile chunks, in tile order
-    std::vector<int32_t> tile_cells;    // occupied cells of each tile (host)
+    // per tile (3-D, nodes sorted by cell): the occupied cells, then the nodes of each of
+    // the tile_edge slabs (cells of one axis-0 position); empty when not sorted by cell
+    std::vector<int32_t> tile_cells;
     // one-column products with the dense-cell spread (moments_available): runs over the
     // sparse tiles for the warp spread, and the chunks of the dense tiles
-    int64_t nsparse = 0, ndense = 0;
+    // the one-column spread and interpolation with dense cells: the warp-slice spread's
+    // runs of sparse tiles, the dense tiles' pieces (dense_chunk nodes), the tensor-core
+    // interpolation's chunks of sparse tiles and the moment interpolation's slab pieces
+    // of dense tiles (at most kGatherPiece nodes); each list largest first
+    int64_t nsparse = 0, ndense = 0, ngsparse = 0, ngdense = 0;
     WorkItem *sparse_items = nullptr, *dense_items = nullptr;
+    WorkItem *gsparse_items = nullptr, *gdense_items = nullptr;
     int slide_tiles = 8;                // most tiles in one sliding run of the warp spread
     int chunk = 8192;                   // most nodes in one work item (tile chunk, sliding run)
     int dense_cell = kDenseCell;        // nodes per occupied cell from which a tile is dense
@@ -126,7 +134,8 @@ struct Plan {
     void *twiddle = nullptr;    // e^{-2 pi i q / ngrid}, q < ngrid/2 (complex, FFT type)
     double *scratch = nullptr;  // small device scalars (reductions, fixed-point scale)
     int *error_flag = nullptr;  // set by a kernel whose bounded wait ran out
-    unsigned *work_counter = nullptr;   // [0] spread, [1] gather, [2] dense-cell spread: next work item (reset per column)
+    unsigned *work_counter = nullptr;   // next work item of [0] spread, [1] gather, [2] dense-cell spread,
+                                        // [3] dense-cell gather (reset per column)
     int fault_kind = 0;         // fault test (nfl_plan_inject_fault): 1 = interpolation MMAs never issued
     int num_sms = 0;
 
@@ -282,8 +291,12 @@ std::vector<WorkItem> spread_item_list(const Plan &P);
 // work lists into sliding runs over sparse tiles and the chunks of dense tiles (host),
 // and the launch over the dense chunks (one column)
 bool moments_available(const Plan &P);
-void split_item_lists(const Plan &P, std::vector<WorkItem> &sparse, std::vector<WorkItem> &dense);
+struct ItemLists {
+    std::vector<WorkItem> sparse, dense, gsparse, gdense;
+};
+ItemLists split_item_lists(const Plan &P);
 cudaError_t launch_spread3_moments(Plan &P);
+cudaError_t launch_gather3_moments(Plan &P, int op, double *y);
 
 }  // namespace nfl
 

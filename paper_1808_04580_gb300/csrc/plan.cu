@@ -202,13 +202,19 @@ __global__ void tile_starts(const int64_t *kstart, int64_t ntiles, int cells_per
         out[t] = (int32_t)kstart[t * cells_per_tile];
 }
 
-// Occupied cells of every tile, from the per-key (tile, cell) offsets.
-__global__ void occupied_cells(const int64_t *kstart, int64_t ntiles, int cells_per_tile, int32_t *out) {
+// Occupied cells of every tile and the nodes of each of its te slabs (the cells that
+// share one axis-0 position: te^2 consecutive keys), from the per-key (tile, cell)
+// offsets; out holds te + 1 entries per tile.
+__global__ void occupied_cells(const int64_t *kstart, int64_t ntiles, int cells_per_tile, int te, int32_t *out) {
+    const int per_slab = cells_per_tile / te;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
         int c = 0;
         for (int k = 0; k < cells_per_tile; ++k)
             c += kstart[t * cells_per_tile + k + 1] > kstart[t * cells_per_tile + k] ? 1 : 0;
-        out[t] = c;
+        out[t * (te + 1)] = c;
+        for (int s = 0; s < te; ++s)
+            out[t * (te + 1) + 1 + s] = (int32_t)(kstart[t * cells_per_tile + (s + 1) * per_slab] -
+                                                  kstart[t * cells_per_tile + s * per_slab]);
     }
 }
 
@@ -290,28 +296,45 @@ bool moments_available(const Plan &P) {
     return spread_warp_available(P) && P.m == 6 && !P.bf16_taps && !P.tile_cells.empty();
 }
 
-// Dense tiles (at least dense_cell nodes per occupied cell) go to the dense-cell
-// spread chunk by chunk, largest first; the other tiles keep the sliding runs.
-void split_item_lists(const Plan &P, std::vector<WorkItem> &sparse, std::vector<WorkItem> &dense) {
+// Dense tiles (at least dense_cell nodes per occupied cell) go to the moment kernels:
+// the spread's work items are pieces of dense_chunk nodes, the interpolation's are the
+// tile's slabs (the cells of one axis-0 position, item pad = the slab) in pieces of at
+// most kGatherPiece nodes.  The other tiles keep the sliding runs of the warp-slice
+// spread and the chunks of the tensor-core interpolation.
+ItemLists split_item_lists(const Plan &P) {
+    ItemLists L;
     std::vector<WorkItem> rest;
-    sparse.clear();
-    dense.clear();
-    std::vector<int64_t> tile_nodes(P.tiles_total, 0);
-    for (const WorkItem &w : P.tile_items) tile_nodes[w.tile] += w.count;
-    for (const WorkItem &w : P.tile_items) {
-        const int32_t cells = P.tile_cells[w.tile];
-        if (cells > 0 && tile_nodes[w.tile] >= (int64_t)P.dense_cell * cells) {
-            // dense chunks in pieces of at most dense_chunk nodes: more CTAs for the dense tiles
-            for (int32_t s0 = 0; s0 < w.count; s0 += P.dense_chunk)
-                dense.push_back(WorkItem{w.tile, w.start + s0, std::min(P.dense_chunk, w.count - s0), 1});
+    const int te = P.tile_edge;
+    const size_t nti = P.tile_items.size();
+    for (size_t i = 0; i < nti;) {
+        size_t e = i;                                     // the chunks of one tile: [i, e)
+        int64_t nodes = 0;
+        while (e < nti && P.tile_items[e].tile == P.tile_items[i].tile) nodes += P.tile_items[e++].count;
+        const int32_t tile = P.tile_items[i].tile;
+        const int32_t *tc = P.tile_cells.data() + (size_t)tile * (te + 1);
+        if (tc[0] > 0 && nodes >= (int64_t)P.dense_cell * tc[0]) {
+            for (size_t k = i; k < e; ++k) {
+                const WorkItem &w = P.tile_items[k];
+                for (int32_t s0 = 0; s0 < w.count; s0 += P.dense_chunk)
+                    L.dense.push_back(WorkItem{tile, w.start + s0, std::min(P.dense_chunk, w.count - s0), 1});
+            }
+            int32_t start = P.tile_items[i].start;
+            for (int sl = 0; sl < te; ++sl) {
+                for (int32_t s0 = 0; s0 < tc[1 + sl]; s0 += kGatherPiece)
+                    L.gdense.push_back(WorkItem{tile, start + s0, std::min(kGatherPiece, tc[1 + sl] - s0), sl});
+                start += tc[1 + sl];
+            }
         } else {
-            rest.push_back(w);
+            rest.insert(rest.end(), P.tile_items.begin() + i, P.tile_items.begin() + e);
         }
+        i = e;
     }
-    sparse = slide_items(rest, P.ntile[P.d - 1], P.slide_tiles, P.chunk);
+    L.sparse = slide_items(rest, P.ntile[P.d - 1], P.slide_tiles, P.chunk);
+    L.gsparse = rest;
     const auto by_size = [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; };
-    std::stable_sort(sparse.begin(), sparse.end(), by_size);
-    std::stable_sort(dense.begin(), dense.end(), by_size);
+    for (std::vector<WorkItem> *v : {&L.sparse, &L.dense, &L.gsparse, &L.gdense})
+        std::stable_sort(v->begin(), v->end(), by_size);
+    return L;
 }
 
 // (Re)allocates dst for cnt items when it holds fewer (old lists are never read again)
@@ -324,22 +347,39 @@ static nfl_status ensure_list(WorkItem *&dst, int64_t &have, int64_t cnt) {
     return NFL_OK;
 }
 
+// Stores the four lists on the device: through the page-locked staging (room for all
+// four lists, copied on `stream`) at plan creation, by synchronous copies otherwise.
+static nfl_status store_item_lists(Plan &P, const ItemLists &L, WorkItem *staging, cudaStream_t stream) {
+    const std::vector<WorkItem> *src[4] = {&L.sparse, &L.dense, &L.gsparse, &L.gdense};
+    WorkItem **dst[4] = {&P.sparse_items, &P.dense_items, &P.gsparse_items, &P.gdense_items};
+    int64_t *cnt[4] = {&P.nsparse, &P.ndense, &P.ngsparse, &P.ngdense};
+    if (!staging && cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
+    for (int k = 0; k < 4; ++k) {
+        int64_t have = *cnt[k];
+        if (ensure_list(*dst[k], have, (int64_t)src[k]->size()) != NFL_OK) return NFL_ERR_OUT_OF_MEMORY;
+        *cnt[k] = (int64_t)src[k]->size();
+        if (src[k]->empty()) continue;
+        const size_t bytes = src[k]->size() * sizeof(WorkItem);
+        if (staging) {
+            std::copy(src[k]->begin(), src[k]->end(), staging);
+            if (cudaMemcpyAsync(*dst[k], staging, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+                return NFL_ERR_CUDA;
+            staging += src[k]->size();
+        } else if (cudaMemcpy(*dst[k], src[k]->data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            return NFL_ERR_CUDA;
+        }
+    }
+    return NFL_OK;
+}
+
+static size_t list_items(const ItemLists &L) {
+    return L.sparse.size() + L.dense.size() + L.gsparse.size() + L.gdense.size();
+}
+
 nfl_status rebuild_spread_items(Plan &P) {
     if (moments_available(P)) {
-        std::vector<WorkItem> sp, de;
-        split_item_lists(P, sp, de);
-        int64_t hs = P.nsparse, hd = P.ndense;
-        if (ensure_list(P.sparse_items, hs, (int64_t)sp.size()) != NFL_OK ||
-            ensure_list(P.dense_items, hd, (int64_t)de.size()) != NFL_OK)
-            return NFL_ERR_OUT_OF_MEMORY;
-        if (cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
-        if ((!sp.empty() && cudaMemcpy(P.sparse_items, sp.data(), sp.size() * sizeof(WorkItem),
-                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
-            (!de.empty() && cudaMemcpy(P.dense_items, de.data(), de.size() * sizeof(WorkItem),
-                                       cudaMemcpyHostToDevice) != cudaSuccess))
-            return NFL_ERR_CUDA;
-        P.nsparse = (int64_t)sp.size();
-        P.ndense = (int64_t)de.size();
+        const nfl_status st = store_item_lists(P, split_item_lists(P), nullptr, P.stream);
+        if (st != NFL_OK) return st;
     }
     const std::vector<WorkItem> s = spread_item_list(P);
     if ((int64_t)s.size() > P.nsitems || !P.sitems) {
@@ -708,6 +748,8 @@ static void free_plan(Plan *P) {
     cudaFree(P->sitems);
     cudaFree(P->sparse_items);
     cudaFree(P->dense_items);
+    cudaFree(P->gsparse_items);
+    cudaFree(P->gdense_items);
     cudaFree(P->tile_start);
     cudaFree(P->pts);
     cudaFree(P->perm);
@@ -809,6 +851,7 @@ struct Builder {
     int64_t *kstart = nullptr, *start = nullptr, *item_off = nullptr;
     unsigned long long *nonempty = nullptr;
     WorkItem *hitems = nullptr;          // page-locked: chunks read back, then the lists uploaded
+    WorkItem *hlists = nullptr;          // page-locked: the dense-cell work lists uploaded
     int32_t *occ = nullptr, *hocc = nullptr;   // occupied cells per tile (device, page-locked)
     double *htab = nullptr;              // page-locked: twiddles, cosine table, deconvolution factors
     double *S = nullptr, *T1 = nullptr, *ctab = nullptr, *dec = nullptr;   // coefficient temporaries
@@ -818,14 +861,14 @@ static void release_temporaries(Builder &B) {
     cudaFree(B.part); cudaFree(B.key_of); cudaFree(B.rank); cudaFree(B.kcount); cudaFree(B.count);
     cudaFree(B.chunks); cudaFree(B.kstart); cudaFree(B.start); cudaFree(B.item_off); cudaFree(B.nonempty);
     cudaFree(B.S); cudaFree(B.T1); cudaFree(B.ctab); cudaFree(B.dec);
-    cudaFreeHost(B.hp); cudaFreeHost(B.hitems); cudaFreeHost(B.htab);
+    cudaFreeHost(B.hp); cudaFreeHost(B.hitems); cudaFreeHost(B.hlists); cudaFreeHost(B.htab);
     cudaFree(B.occ); cudaFreeHost(B.hocc);
     B.occ = B.hocc = nullptr;
     B.part = B.S = B.T1 = B.ctab = B.dec = B.hp = B.htab = nullptr;
     B.key_of = B.rank = B.kcount = B.count = B.chunks = nullptr;
     B.kstart = B.start = B.item_off = nullptr;
     B.nonempty = nullptr;
-    B.hitems = nullptr;
+    B.hitems = B.hlists = nullptr;
 }
 
 // Fields, window polynomials, per-plan scalars; step 1: bounding-box partials.
@@ -848,7 +891,7 @@ static nfl_status phase_setup(Builder &B) {
     NFL_STATUS_TRY(cudaDeviceGetAttribute(&P->l2_bytes, cudaDevAttrL2CacheSize, dev));
     NFL_STATUS_TRY(cudaMalloc(&P->scratch, 64 * sizeof(double)));
     NFL_STATUS_TRY(cudaMalloc(&P->error_flag, sizeof(int)));
-    NFL_STATUS_TRY(cudaMalloc(&P->work_counter, 3 * sizeof(unsigned)));
+    NFL_STATUS_TRY(cudaMalloc(&P->work_counter, 4 * sizeof(unsigned)));
     NFL_STATUS_TRY(cudaMemsetAsync(P->error_flag, 0, sizeof(int), B.stream));
     NFL_STATUS_TRY(cudaMalloc(&B.part, kRBlocks * 6 * sizeof(double)));
     NFL_STATUS_TRY(cudaHostAlloc(&B.hp, kRBlocks * 6 * sizeof(double), cudaHostAllocDefault));
@@ -975,13 +1018,18 @@ static nfl_status phase_items(Builder &B) {
     const int blocks = P->num_sms * 8;
     fill_items<<<blocks, 256, 0, stream>>>(B.count, B.start, B.item_off, nt, P->items);
     tile_starts<<<blocks, 256, 0, stream>>>(B.kstart, nt, B.cpt, P->tile_start);
-    // occupied cells per tile (for the dense-cell spread)
-    NFL_STATUS_TRY(cudaMalloc(&B.occ, std::max<int64_t>(nt, 1) * sizeof(int32_t)));
-    NFL_STATUS_TRY(cudaHostAlloc(&B.hocc, std::max<int64_t>(nt, 1) * sizeof(int32_t), cudaHostAllocDefault));
-    occupied_cells<<<blocks, 256, 0, stream>>>(B.kstart, nt, B.cpt, B.occ);
-    NFL_STATUS_TRY(cudaMemcpyAsync(B.hocc, B.occ, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-    // room for the sorted chunks and the spread lists (at most one entry per chunk each) to upload
-    NFL_STATUS_TRY(cudaHostAlloc(&B.hitems, std::max<int64_t>(4 * P->nitems, 1) * sizeof(WorkItem),
+    // occupied cells and slab nodes per tile (for the dense-cell spread and interpolation;
+    // only when the nodes of a tile are sorted by cell, in 3-D)
+    if (B.cpt > 1 && B.d == 3) {
+        const int te = P->tile_edge;
+        const int64_t per = (int64_t)nt * (te + 1);
+        NFL_STATUS_TRY(cudaMalloc(&B.occ, std::max<int64_t>(per, 1) * sizeof(int32_t)));
+        NFL_STATUS_TRY(cudaHostAlloc(&B.hocc, std::max<int64_t>(per, 1) * sizeof(int32_t), cudaHostAllocDefault));
+        occupied_cells<<<blocks, 256, 0, stream>>>(B.kstart, nt, B.cpt, te, B.occ);
+        NFL_STATUS_TRY(cudaMemcpyAsync(B.hocc, B.occ, per * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    }
+    // room for the sorted chunks and the warp spread's list (at most one entry per chunk)
+    NFL_STATUS_TRY(cudaHostAlloc(&B.hitems, std::max<int64_t>(2 * P->nitems, 1) * sizeof(WorkItem),
                                  cudaHostAllocDefault));
     if (P->nitems > 0)
         NFL_STATUS_TRY(cudaMemcpyAsync(B.hitems, P->items, P->nitems * sizeof(WorkItem), cudaMemcpyDeviceToHost,
@@ -1001,7 +1049,7 @@ static nfl_status phase_finish(Builder &B) {
         // largest chunks first: the kernels that take items from a shared counter
         // then end with small ones (longest-processing-time order)
         P->tile_items.assign(B.hitems, B.hitems + P->nitems);
-        P->tile_cells.assign(B.hocc, B.hocc + P->tiles_total);
+        if (B.hocc) P->tile_cells.assign(B.hocc, B.hocc + P->tiles_total * (P->tile_edge + 1));
         const std::vector<WorkItem> s = spread_item_list(*P);
         if (cudaMalloc(&P->sitems, std::max<size_t>(s.size(), 1) * sizeof(WorkItem)) != cudaSuccess)
             return NFL_ERR_OUT_OF_MEMORY;
@@ -1016,22 +1064,11 @@ static nfl_status phase_finish(Builder &B) {
             NFL_STATUS_TRY(cudaMemcpyAsync(P->sitems, B.hitems + P->nitems, s.size() * sizeof(WorkItem),
                                            cudaMemcpyHostToDevice, stream));
         if (moments_available(*P)) {
-            std::vector<WorkItem> sp, de;
-            split_item_lists(*P, sp, de);
-            if (cudaMalloc(&P->sparse_items, std::max<size_t>(sp.size(), 1) * sizeof(WorkItem)) != cudaSuccess ||
-                cudaMalloc(&P->dense_items, std::max<size_t>(de.size(), 1) * sizeof(WorkItem)) != cudaSuccess)
-                return NFL_ERR_OUT_OF_MEMORY;
-            P->nsparse = (int64_t)sp.size();
-            P->ndense = (int64_t)de.size();
-            WorkItem *hs = B.hitems + P->nitems + s.size(), *hd = hs + sp.size();
-            std::copy(sp.begin(), sp.end(), hs);
-            std::copy(de.begin(), de.end(), hd);
-            if (!sp.empty())
-                NFL_STATUS_TRY(cudaMemcpyAsync(P->sparse_items, hs, sp.size() * sizeof(WorkItem),
-                                               cudaMemcpyHostToDevice, stream));
-            if (!de.empty())
-                NFL_STATUS_TRY(cudaMemcpyAsync(P->dense_items, hd, de.size() * sizeof(WorkItem),
-                                               cudaMemcpyHostToDevice, stream));
+            const ItemLists L = split_item_lists(*P);
+            NFL_STATUS_TRY(cudaHostAlloc(&B.hlists, std::max<size_t>(list_items(L), 1) * sizeof(WorkItem),
+                                         cudaHostAllocDefault));
+            const nfl_status st = store_item_lists(*P, L, B.hlists, stream);
+            if (st != NFL_OK) return st;
         }
     }
 

@@ -221,7 +221,7 @@ cudaError_t launch_fixed_scale(Plan &P, const double *x, bool ones, bool scale_d
 cudaError_t prepare_spread(Plan &P, int op, const double *x, int64_t ldx, int nc, bool ones, bool scale_dinv) {
     size_t elem = P.prec == NFL_PREC_FP32 ? sizeof(float) : 8;
     NFL_CUDA_TRY(cudaMemsetAsync(P.grid, 0, P.box_elems * elem * nc, P.stream));
-    NFL_CUDA_TRY(cudaMemsetAsync(P.work_counter, 0, 3 * sizeof(unsigned), P.stream));
+    NFL_CUDA_TRY(cudaMemsetAsync(P.work_counter, 0, 4 * sizeof(unsigned), P.stream));
     if (P.d == 3 && column_tile_edge(P.m) == P.tile_edge)
         return stage_spread3_values(P, op, x, ldx, nc, ones, scale_dinv);
     if (nc != 1) return cudaErrorInvalidValue;

@@ -119,12 +119,14 @@ typedef struct {
     int fft_lines_cap;    /* FFT passes: grid points per CTA (lines x length)  */
     int slide_tiles;      /* 3-D warp spread: most tiles in one sliding run    */
     int block_cols;       /* columns per launch of a block product (1: none)   */
-    int64_t dense_items;  /* 3-D m = 6 FP32 / FP32C: chunks of the tiles with at
-                             least dense_cell nodes per occupied cell, which
-                             one-column products spread by Chebyshev moments   */
+    int64_t dense_items;  /* 3-D m = 6 FP32 / FP32C: slab pieces (cells of one
+                             axis-0 position) of the tiles with at least
+                             dense_cell nodes per occupied cell, which
+                             one-column products spread and interpolate by
+                             Chebyshev moments                                 */
     int chunk;            /* most nodes in one work item                       */
     int dense_cell;       /* nodes per occupied cell from which a tile is dense */
-    int dense_chunk;      /* most nodes in one work item of the dense-cell spread */
+    int dense_chunk;      /* most nodes in one slab piece of the moment kernels */
 } nfl_info;
 
 /*
@@ -194,9 +196,10 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info);
  *   chunk          3-D: most nodes in one work item of the spread and the
  *                  interpolation, from {2048, 4096, 8192};
  *   dense_cell     3-D m = 6 FP32 / FP32C: nodes per occupied cell from which
- *                  a tile goes to the dense-cell spread, from {16, 32, 64};
- *   dense_chunk    the same plans: most nodes in one work item of the
- *                  dense-cell spread, from {1024, 2048, 8192};
+ *                  a tile goes to the moment kernels (spread and
+ *                  interpolation), from {16, 32, 64};
+ *   dense_chunk    the same plans: most nodes in one slab piece of the
+ *                  moment kernels, from {512, 1024, 2048};
  *   slide_tiles    3-D warp-slice spread: most tiles of one axis-2 run that
  *                  the tile copies slide along (1 = no sliding), from
  *                  {1, 4, 8, 16}.

@@ -14,8 +14,8 @@ int kernels_per_column(const Plan &P) {
     // the one-column spread and interpolation with dense cells launch the warp-slice and
     // tensor-core kernels for the sparse tiles and the moment kernels for the dense ones
     // (the spreads each only when they have items; the tensor-core launch always counts)
-    const bool split = moments_available(P) && P.ndense > 0;
-    const int spreads = moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.ndense > 0 ? 1 : 0) : 1;
+    const bool split = moments_available(P) && P.nslab > 0;
+    const int spreads = moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.nslab > 0 ? 1 : 0) : 1;
     const int gathers = split && gather_tc_available(P) ? 2 : 1;
     return (staged || P.prec == NFL_PREC_FP32C ? 1 : 0) + spreads + passes + gathers;
 }
@@ -353,8 +353,9 @@ nfl_status nfl_plan_autotune(nfl_plan *plan, double *best_ms) {
         P.dense_cell = best_dense;
         nfl_status rs = nfl::rebuild_spread_items(P);
         if (st == NFL_OK) st = rs;
-        // nodes per work item of the dense-cell spread
-        const int dch[3] = {1024, 2048, 8192};
+        // most nodes per slab piece of the moment kernels (FP32 moment sums run over
+        // one piece, so no more than the warp-slice kernel's 2048 per tile copy)
+        const int dch[3] = {512, 1024, 2048};
         int best_dch = P.dense_chunk;
         best = 1e30;
         for (int c = 0; c < 3 && st == NFL_OK; ++c) {
@@ -439,8 +440,8 @@ nfl_status nfl_plan_kernels(const nfl_plan *plan, int nrhs, int *kernels) {
         const int blocks = (nrhs + P.block_cols - 1) / P.block_cols;
         // one launch per stage and block (a block spreads and interpolates every tile with
         // the warp-slice and tensor-core kernels)
-        const bool split = nfl::moments_available(P) && P.ndense > 0;
-        const int spreads = nfl::moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.ndense > 0 ? 1 : 0) : 1;
+        const bool split = nfl::moments_available(P) && P.nslab > 0;
+        const int spreads = nfl::moments_available(P) ? (P.nsparse > 0 ? 1 : 0) + (P.nslab > 0 ? 1 : 0) : 1;
         const int gathers = split && nfl::gather_tc_available(P) ? 2 : 1;
         *kernels = blocks * (nfl::kernels_per_column(P) - spreads + 1 - gathers + 1);
     } else {

@@ -505,7 +505,7 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y, int64_
     a.degree_out = P.degree;
     a.dinv_out = P.dinv_sorted;
     // a one-column interpolation with dense cells leaves the dense tiles to the moment kernel
-    const bool split = nc == 1 && moments_available(P) && P.ndense > 0;
+    const bool split = nc == 1 && moments_available(P) && P.nslab > 0;
     a.items = split ? P.gsparse_items : P.items;
     a.nitems = split ? P.ngsparse : P.nitems;
     for (int i = 0; i < 3; ++i) {

@@ -38,7 +38,6 @@ constexpr int kBlockCols = 8;   // columns a block product takes through each st
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 constexpr int kCheb = 8;        // Chebyshev basis of the dense-cell spread (degree 7)
 constexpr int kDenseCell = 64;       // nodes per occupied cell from which a tile is spread by moments
-constexpr int kGatherPiece = 2048;   // most nodes per work item (one slab) of the dense-cell interpolation
 
 // Per-column buffers of block products (see Plan::blk).
 struct BlockBuffers {
@@ -83,16 +82,15 @@ struct Plan {
     // one-column products with the dense-cell spread (moments_available): runs over the
     // sparse tiles for the warp spread, and the chunks of the dense tiles
     // the one-column spread and interpolation with dense cells: the warp-slice spread's
-    // runs of sparse tiles, the dense tiles' pieces (dense_chunk nodes), the tensor-core
-    // interpolation's chunks of sparse tiles and the moment interpolation's slab pieces
-    // of dense tiles (at most kGatherPiece nodes); each list largest first
-    int64_t nsparse = 0, ndense = 0, ngsparse = 0, ngdense = 0;
-    WorkItem *sparse_items = nullptr, *dense_items = nullptr;
-    WorkItem *gsparse_items = nullptr, *gdense_items = nullptr;
+    // runs of sparse tiles, the tensor-core interpolation's chunks of sparse tiles and
+    // the dense tiles' slab pieces (at most dense_chunk nodes, pad = the slab) that both
+    // moment kernels take; each list largest first
+    int64_t nsparse = 0, ngsparse = 0, nslab = 0;
+    WorkItem *sparse_items = nullptr, *gsparse_items = nullptr, *slab_items = nullptr;
     int slide_tiles = 8;                // most tiles in one sliding run of the warp spread
     int chunk = 8192;                   // most nodes in one work item (tile chunk, sliding run)
     int dense_cell = kDenseCell;        // nodes per occupied cell from which a tile is dense
-    int dense_chunk = 8192;             // most nodes in one work item of the dense-cell spread
+    int dense_chunk = 2048;             // most nodes in one slab piece of the moment kernels
     int fft_cap = 512;                  // FFT passes: grid points per CTA
 
     // tile-sorted nodes
@@ -292,7 +290,7 @@ std::vector<WorkItem> spread_item_list(const Plan &P);
 // and the launch over the dense chunks (one column)
 bool moments_available(const Plan &P);
 struct ItemLists {
-    std::vector<WorkItem> sparse, dense, gsparse, gdense;
+    std::vector<WorkItem> sparse, gsparse, slab;
 };
 ItemLists split_item_lists(const Plan &P);
 cudaError_t launch_spread3_moments(Plan &P);

@@ -296,10 +296,9 @@ bool moments_available(const Plan &P) {
     return spread_warp_available(P) && P.m == 6 && !P.bf16_taps && !P.tile_cells.empty();
 }
 
-// Dense tiles (at least dense_cell nodes per occupied cell) go to the moment kernels:
-// the spread's work items are pieces of dense_chunk nodes, the interpolation's are the
-// tile's slabs (the cells of one axis-0 position, item pad = the slab) in pieces of at
-// most kGatherPiece nodes.  The other tiles keep the sliding runs of the warp-slice
+// Dense tiles (at least dense_cell nodes per occupied cell) go to the moment kernels
+// as their slabs (the cells of one axis-0 position, item pad = the slab) in pieces of
+// at most dense_chunk nodes; the other tiles keep the sliding runs of the warp-slice
 // spread and the chunks of the tensor-core interpolation.
 ItemLists split_item_lists(const Plan &P) {
     ItemLists L;
@@ -313,15 +312,10 @@ ItemLists split_item_lists(const Plan &P) {
         const int32_t tile = P.tile_items[i].tile;
         const int32_t *tc = P.tile_cells.data() + (size_t)tile * (te + 1);
         if (tc[0] > 0 && nodes >= (int64_t)P.dense_cell * tc[0]) {
-            for (size_t k = i; k < e; ++k) {
-                const WorkItem &w = P.tile_items[k];
-                for (int32_t s0 = 0; s0 < w.count; s0 += P.dense_chunk)
-                    L.dense.push_back(WorkItem{tile, w.start + s0, std::min(P.dense_chunk, w.count - s0), 1});
-            }
             int32_t start = P.tile_items[i].start;
             for (int sl = 0; sl < te; ++sl) {
-                for (int32_t s0 = 0; s0 < tc[1 + sl]; s0 += kGatherPiece)
-                    L.gdense.push_back(WorkItem{tile, start + s0, std::min(kGatherPiece, tc[1 + sl] - s0), sl});
+                for (int32_t s0 = 0; s0 < tc[1 + sl]; s0 += P.dense_chunk)
+                    L.slab.push_back(WorkItem{tile, start + s0, std::min(P.dense_chunk, tc[1 + sl] - s0), sl});
                 start += tc[1 + sl];
             }
         } else {
@@ -332,7 +326,7 @@ ItemLists split_item_lists(const Plan &P) {
     L.sparse = slide_items(rest, P.ntile[P.d - 1], P.slide_tiles, P.chunk);
     L.gsparse = rest;
     const auto by_size = [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; };
-    for (std::vector<WorkItem> *v : {&L.sparse, &L.dense, &L.gsparse, &L.gdense})
+    for (std::vector<WorkItem> *v : {&L.sparse, &L.gsparse, &L.slab})
         std::stable_sort(v->begin(), v->end(), by_size);
     return L;
 }
@@ -347,14 +341,14 @@ static nfl_status ensure_list(WorkItem *&dst, int64_t &have, int64_t cnt) {
     return NFL_OK;
 }
 
-// Stores the four lists on the device: through the page-locked staging (room for all
-// four lists, copied on `stream`) at plan creation, by synchronous copies otherwise.
+// Stores the three lists on the device: through the page-locked staging (room for all
+// three lists, copied on `stream`) at plan creation, by synchronous copies otherwise.
 static nfl_status store_item_lists(Plan &P, const ItemLists &L, WorkItem *staging, cudaStream_t stream) {
-    const std::vector<WorkItem> *src[4] = {&L.sparse, &L.dense, &L.gsparse, &L.gdense};
-    WorkItem **dst[4] = {&P.sparse_items, &P.dense_items, &P.gsparse_items, &P.gdense_items};
-    int64_t *cnt[4] = {&P.nsparse, &P.ndense, &P.ngsparse, &P.ngdense};
+    const std::vector<WorkItem> *src[3] = {&L.sparse, &L.gsparse, &L.slab};
+    WorkItem **dst[3] = {&P.sparse_items, &P.gsparse_items, &P.slab_items};
+    int64_t *cnt[3] = {&P.nsparse, &P.ngsparse, &P.nslab};
     if (!staging && cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
         int64_t have = *cnt[k];
         if (ensure_list(*dst[k], have, (int64_t)src[k]->size()) != NFL_OK) return NFL_ERR_OUT_OF_MEMORY;
         *cnt[k] = (int64_t)src[k]->size();
@@ -373,7 +367,7 @@ static nfl_status store_item_lists(Plan &P, const ItemLists &L, WorkItem *stagin
 }
 
 static size_t list_items(const ItemLists &L) {
-    return L.sparse.size() + L.dense.size() + L.gsparse.size() + L.gdense.size();
+    return L.sparse.size() + L.gsparse.size() + L.slab.size();
 }
 
 nfl_status rebuild_spread_items(Plan &P) {
@@ -747,9 +741,8 @@ static void free_plan(Plan *P) {
     cudaFree(P->blk.bufB); cudaFree(P->blk.g); cudaFree(P->blk.grid);
     cudaFree(P->sitems);
     cudaFree(P->sparse_items);
-    cudaFree(P->dense_items);
     cudaFree(P->gsparse_items);
-    cudaFree(P->gdense_items);
+    cudaFree(P->slab_items);
     cudaFree(P->tile_start);
     cudaFree(P->pts);
     cudaFree(P->perm);
@@ -1328,7 +1321,7 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info) {
     info->fft_lines_cap = P->fft_cap;
     info->slide_tiles = P->slide_tiles;
     info->block_cols = P->block_cols;
-    info->dense_items = moments_available(*P) ? P->ndense : 0;
+    info->dense_items = moments_available(*P) ? P->nslab : 0;
     info->chunk = P->chunk;
     info->dense_cell = P->dense_cell;
     info->dense_chunk = P->dense_chunk;

@@ -37,7 +37,7 @@ constexpr int kHostSlots = 3;   // device staging slots per direction for host-b
 constexpr int kBlockCols = 8;   // columns a block product takes through each stage in one launch
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 constexpr int kCheb = 8;        // Chebyshev basis of the dense-cell spread (degree 7)
-constexpr int kDenseCell = 64;       // nodes per occupied cell from which a tile is spread by moments
+constexpr int kDenseCell = 32;       // nodes per occupied cell from which a tile is spread by moments
 
 // Per-column buffers of block products (see Plan::blk).
 struct BlockBuffers {

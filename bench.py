@@ -443,10 +443,12 @@ def main():
     else:
         peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         peak_note = "derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no measured FP32 rate)"
-    # the spread stage is two kernels (sparse tiles: warp-slice; dense tiles: Chebyshev moments)
+    # each stage is two kernels (sparse tiles: warp-slice spread / tensor-core interpolation;
+    # dense tiles: slab Chebyshev moments)
     parts = ([("spread3_warp.cu", "spread3_warp_ball10M.md"), ("spread3_moments.cu", "spread3_moments_ball10M.md")]
-             if dom == "spread" else [("gather_tc.cu", "gather3_tc_ball10M.md")])
-    kname = "spread3_warp + spread3_moments" if dom == "spread" else "gather3_tc"
+             if dom == "spread" else
+             [("gather_tc.cu", "gather3_tc_ball10M.md"), ("gather3_moments.cu", "gather3_moments_ball10M.md")])
+    kname = "spread3_warp + spread3_moments" if dom == "spread" else "gather3_tc + gather3_moments"
     traffic = 0.0 if n == 10_000_000 else None
     for src, summary in parts:
         t = profiled_traffic(summary, os.path.join(ROOT, "paper_1808_04580_gb300", "csrc", src)) if traffic is not None else None

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(SM_NT, 2) gather3_moments(GatherMomentArgs a) 
 
 // The dense tiles' slab pieces of a one-column interpolation (the tensor-core kernel
 // takes the rest).
-cudaError_t launch_gather3_moments(Plan &P, int op, double *y) {
+cudaError_t launch_gather3_moments(Plan &P, int op, double *y, cudaStream_t s) {
     if (P.nslab == 0) return cudaSuccess;
     GatherMomentArgs a{};
     a.pts = reinterpret_cast<const PointF *>(P.pts);
@@ -285,7 +285,7 @@ cudaError_t launch_gather3_moments(Plan &P, int op, double *y) {
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * P.num_sms;
     if (grid > P.nslab) grid = P.nslab;
-    gather3_moments<<<(unsigned)grid, SM_NT, SM_SMEM, P.stream>>>(a);
+    gather3_moments<<<(unsigned)grid, SM_NT, SM_SMEM, s>>>(a);
     return cudaGetLastError();
 }
 

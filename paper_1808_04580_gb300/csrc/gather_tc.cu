@@ -529,8 +529,11 @@ cudaError_t launch_gather_tc(Plan &P, int op, const double *x, double *y, int64_
         case 3: return launch_tc<3, 8>(P, a);
         case 4: return launch_tc<4, 8>(P, a);
         case 6:
+            // the dense tiles' slabs after the sparse tiles, on the same stream (beside them
+            // on a second stream the moment kernel's CTAs held SMs the tensor-core kernel
+            // still needed: 3 % slower)
             NFL_CUDA_TRY((launch_tc<6, 4>(P, a)));
-            return split ? launch_gather3_moments(P, op, y) : cudaSuccess;
+            return split ? launch_gather3_moments(P, op, y, P.stream) : cudaSuccess;
         case 7: return launch_tc<7, 2>(P, a);
     }
     return cudaErrorInvalidValue;

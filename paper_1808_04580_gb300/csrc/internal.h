@@ -56,6 +56,10 @@ struct Plan {
     double sigma = 0, sigma_t = 0, rho = 1, eps_B = 0;
     double center[3] = {0, 0, 0};
     cudaStream_t stream = 0;
+    // one-column products with dense tiles: the moment spread runs on `side`, forked
+    // from and joined back into `stream`, so it fills the warp-slice spread's tail
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
     // oversampled grid and its active box
     int ngrid = 0;              // 2N
@@ -293,8 +297,11 @@ struct ItemLists {
     std::vector<WorkItem> sparse, gsparse, slab;
 };
 ItemLists split_item_lists(const Plan &P);
-cudaError_t launch_spread3_moments(Plan &P);
-cudaError_t launch_gather3_moments(Plan &P, int op, double *y);
+cudaError_t launch_spread3_moments(Plan &P, cudaStream_t s);
+cudaError_t launch_gather3_moments(Plan &P, int op, double *y, cudaStream_t s);
+// `side` waits for the work queued on `stream` so far / `stream` waits for `side`
+cudaError_t side_fork(Plan &P);
+cudaError_t side_join(Plan &P);
 
 }  // namespace nfl
 

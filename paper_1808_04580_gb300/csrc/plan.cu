@@ -292,6 +292,18 @@ std::vector<WorkItem> spread_item_list(const Plan &P) {
     return s;
 }
 
+cudaError_t side_fork(Plan &P) {
+    if (!P.side) return cudaSuccess;
+    NFL_CUDA_TRY(cudaEventRecord(P.fork_ev, P.stream));
+    return cudaStreamWaitEvent(P.side, P.fork_ev, 0);
+}
+
+cudaError_t side_join(Plan &P) {
+    if (!P.side) return cudaSuccess;
+    NFL_CUDA_TRY(cudaEventRecord(P.join_ev, P.side));
+    return cudaStreamWaitEvent(P.stream, P.join_ev, 0);
+}
+
 bool moments_available(const Plan &P) {
     return spread_warp_available(P) && P.m == 6 && !P.bf16_taps && !P.tile_cells.empty();
 }
@@ -724,6 +736,12 @@ static nfl_status coefficients_launch(Plan &P, double *tab, double *&S, double *
 
 static void free_plan(Plan *P) {
     if (!P) return;
+    if (P->side) {
+        cudaStreamSynchronize(P->side);
+        cudaStreamDestroy(P->side);
+    }
+    if (P->fork_ev) cudaEventDestroy(P->fork_ev);
+    if (P->join_ev) cudaEventDestroy(P->join_ev);
     for (cudaEvent_t e : P->events) cudaEventDestroy(e);
     if (P->h2d) cudaStreamSynchronize(P->h2d);
     if (P->d2h) cudaStreamSynchronize(P->d2h);
@@ -1057,6 +1075,10 @@ static nfl_status phase_finish(Builder &B) {
             NFL_STATUS_TRY(cudaMemcpyAsync(P->sitems, B.hitems + P->nitems, s.size() * sizeof(WorkItem),
                                            cudaMemcpyHostToDevice, stream));
         if (moments_available(*P)) {
+            if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming) != cudaSuccess)
+                return NFL_ERR_CUDA;
             const ItemLists L = split_item_lists(*P);
             NFL_STATUS_TRY(cudaHostAlloc(&B.hlists, std::max<size_t>(list_items(L), 1) * sizeof(WorkItem),
                                          cudaHostAllocDefault));

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
 }
 
 template <bool FIXED>
-static cudaError_t launch_moments(Plan &P, const MomentArgs &a) {
+static cudaError_t launch_moments(Plan &P, const MomentArgs &a, cudaStream_t s) {
     auto kern = spread3_moments<FIXED>;
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_M));
     NFL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -289,12 +289,12 @@ static cudaError_t launch_moments(Plan &P, const MomentArgs &a) {
     int64_t grid = (int64_t)per_sm * P.num_sms;
     if (grid > a.nitems) grid = a.nitems;
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, NTM, SMEM_M, P.stream>>>(a);
+    kern<<<(unsigned)grid, NTM, SMEM_M, s>>>(a);
     return cudaGetLastError();
 }
 
 // The dense tiles' slab pieces of a one-column spread (the warp-slice kernel takes the rest).
-cudaError_t launch_spread3_moments(Plan &P) {
+cudaError_t launch_spread3_moments(Plan &P, cudaStream_t s) {
     if (P.nslab == 0) return cudaSuccess;
     MomentArgs a{};
     a.pts = reinterpret_cast<const PointF *>(P.pts);
@@ -312,7 +312,7 @@ cudaError_t launch_spread3_moments(Plan &P) {
     a.counter = P.work_counter + 2;
     for (int j = 0; j < TAPS_M; ++j)
         for (int k = 0; k < R; ++k) a.cheb[j][k] = P.kb_cheb[j][k];
-    return P.prec == NFL_PREC_FP32C ? launch_moments<true>(P, a) : launch_moments<false>(P, a);
+    return P.prec == NFL_PREC_FP32C ? launch_moments<true>(P, a, s) : launch_moments<false>(P, a, s);
 }
 
 }  // namespace nfl

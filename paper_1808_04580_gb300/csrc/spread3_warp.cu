@@ -544,8 +544,12 @@ cudaError_t launch_spread3_warp(Plan &P, int nc) {
         case 3: return fixed ? launch_warp<3, 8, true>(P, a) : launch_warp<3, 8, false>(P, a);
         case 4: return fixed ? launch_warp<4, 8, true>(P, a) : launch_warp<4, 8, false>(P, a);
         case 6:
+            if (!split) return fixed ? launch_warp<6, 4, true>(P, a) : launch_warp<6, 4, false>(P, a);
+            // the sparse tiles on the plan's stream, the dense tiles' slabs beside them
+            NFL_CUDA_TRY(side_fork(P));
             NFL_CUDA_TRY((fixed ? launch_warp<6, 4, true>(P, a) : launch_warp<6, 4, false>(P, a)));
-            return split ? launch_spread3_moments(P) : cudaSuccess;
+            NFL_CUDA_TRY(launch_spread3_moments(P, P.side ? P.side : P.stream));
+            return side_join(P);
     }
     return cudaErrorInvalidValue;
 }

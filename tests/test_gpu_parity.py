@@ -172,6 +172,47 @@ def test_dense_cell_spread_matches_alg2_oracle(prec, tol, dense):
     assert_close(Yb[:, 0], y, tol)
 
 
+def _slab_cloud(kind, n, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "hot_cell":
+        # 85 % of the nodes inside one cell: one slab of several 2048-node pieces
+        v = rng.uniform(-1, 1, (n, 3))
+        hot = rng.random(n) < 0.85
+        v[hot] = 0.3 + 1e-4 * rng.standard_normal((int(hot.sum()), 3))
+        return v
+    # a few tight clusters
+    c = rng.uniform(-1, 1, (3, 3))
+    return c[rng.integers(0, 3, n)] + 0.03 * rng.standard_normal((n, 3))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
+@pytest.mark.parametrize("kind,n,N,p,eps_B", [("hot_cell", 9000, 32, 6, -1.0), ("clusters", 4000, 8, 2, 0.125)])
+def test_slab_moments_edge_cases(kind, n, N, p, eps_B, prec, tol):
+    """The slab-moment spread and interpolation (m = 6, dense tiles) on a cell holding
+    most of the nodes (one slab cut into several work items, each adding its block into
+    the same grid positions) and on clusters whose supports wrap around the periodic
+    grid (N = 8, eps_B = 1/8: the box spans 7 + 2m + 2 > 2N positions per axis): W, L_s
+    and the degrees against the oracle's Alg. 2, before and after the autotuner re-cuts
+    the slabs."""
+    v = _slab_cloud(kind, n, 41)
+    x = workloads.rhs(n, seed=42)
+    ref = fastsum.NormalizedFastsum(v, 0.5, N, 6, p, None if eps_B < 0 else eps_B)
+    plan = Plan(gpu(v), 0.5, N, 6, p, eps_B, prec)
+    info = plan.info()
+    assert info["dense_items"] > 0
+    if kind == "hot_cell":
+        assert info["dense_items"] >= 4          # the hot slab alone is four pieces
+    yw_ref, yl_ref = ref.apply_W(x), ref.apply_Ls(x)
+    for tuned in (False, True):
+        if tuned:
+            plan.autotune()
+        assert_close(plan.apply_W(gpu(x)).cpu().numpy(), yw_ref, tol, x=x)
+        yl = plan.apply_Ls(gpu(x)).cpu().numpy()
+        assert_close(x - yl, x - yl_ref, tol)
+    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)
+    assert plan.info()["device_error"] == 0
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
 @pytest.mark.parametrize("m,N", [(2, 16), (3, 16), (4, 32), (6, 32), (7, 32), (5, 32), (8, 32)])
 def test_mixed_forms_each_window_size(m, N, prec, tol):

@@ -14,13 +14,13 @@
 //
 // A CTA takes one slab of a dense tile (the 16 cells that share an axis-0
 // position; the nodes of a tile are sorted by cell with axis 0 slowest, so a
-// slab's nodes are contiguous), or a piece of one.  Its 8 warps take the
-// slab's nodes in slices of 32, round robin: lane l accumulates the moments
+// slab's nodes are contiguous), or a piece of one.  Its 8 warps take one
+// eighth of the nodes each, in slices of 32: lane l accumulates the moments
 // (k0, k1 = l / 4, k2 = 2 (l mod 4) + {0, 1}) for k0 < 8 as 8 pairs over
 // (k0, k0 + 1), one fma.rn.f32x2 per pair and node, from the slice's staged
-// Chebyshev rows (the rows of four nodes loaded together); at the
-// end of a run of one cell (at most 32 nodes) the lanes add them to the cell's
-// moments in shared memory.  Then the CTA expands the 16 cells' moments into
+// Chebyshev rows (the rows of four nodes loaded together); when the cell
+// changes the lanes add them to the cell's moments in shared memory.  Then the
+// CTA expands the 16 cells' moments into
 // the slab's 12 x 15 x 15 block in three contractions shared by the cells that
 // overlap along each axis,
 //   V2[k0][s1][k1][c] = sum_{s2, c'} C[c'][k2] M_{s1,s2}[k0][k1][k2],  c = s2 + c'
@@ -124,9 +124,28 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
         tile_coords<3>(w.tile, a.ntile, tc);
         const int end = w.start + w.count;
 
-        // moments: slices of 32 nodes, round robin over the warps
-        for (int base = w.start + g * 32; base < end; base += NWM * 32) {
-            const int cnt = min(32, end - base);
+        // moments: warp g takes the g-th eighth of the item in slices of 32 nodes and
+        // carries its sums across slices while the cell stays the same
+        unsigned long long acc[2][R / 2];
+#pragma unroll
+        for (int p = 0; p < R / 2; ++p) acc[0][p] = acc[1][p] = 0ull;
+        int cur = -1;
+        // the sums of cell cur into its moments; the accumulators start again from zero
+        auto flush = [&]() {
+            float *mrow = Mom + cur * MST + k1 * R + c0;
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int p = 0; p < R / 2; ++p) {
+                    atomicAdd(mrow + 2 * p * R * R + c, lane_of(acc[c][p], 0));
+                    atomicAdd(mrow + (2 * p + 1) * R * R + c, lane_of(acc[c][p], 1));
+                    acc[c][p] = 0ull;
+                }
+        };
+        const int share = (w.count + NWM - 1) / NWM;
+        const int gbeg = w.start + g * share, gend = min(end, gbeg + share);
+        for (int base = gbeg; base < gend; base += 32) {
+            const int cnt = min(32, gend - base);
             const bool valid = lane < cnt;
             int cell = 0;
             {
@@ -167,10 +186,11 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
                 const unsigned rest = i + 1 < 32 ? (runs >> (i + 1)) : 0u;
                 const int j = rest ? min(cnt, i + __ffs(rest)) : cnt;
                 const int ci = __shfl_sync(0xffffffffu, cell, i);
-                // acc[c][p] = sum over the run of (T_2p(t0), T_2p+1(t0)) x~ T_k1(t1) T_c0+c(t2)
-                unsigned long long acc[2][R / 2];
-#pragma unroll
-                for (int p = 0; p < R / 2; ++p) acc[0][p] = acc[1][p] = 0ull;
+                if (ci != cur) {
+                    if (cur >= 0) flush();
+                    cur = ci;
+                }
+                // acc[c][p] += sum over the run of (T_2p(t0), T_2p+1(t0)) x~ T_k1(t1) T_c0+c(t2)
                 int q = i;
                 // four nodes' rows loaded before their multiply-adds
                 for (; q + 4 <= j; q += 4) {
@@ -185,18 +205,11 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
                     d.load(stage + q * ROW, k1, c0);
                     d.add(acc);
                 }
-                float *mrow = Mom + ci * MST + k1 * R + c0;
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int p = 0; p < R / 2; ++p) {
-                        atomicAdd(mrow + 2 * p * R * R + c, lane_of(acc[c][p], 0));
-                        atomicAdd(mrow + (2 * p + 1) * R * R + c, lane_of(acc[c][p], 1));
-                    }
                 i = j;
             }
             __syncwarp();                             // the next slice overwrites the staged rows
         }
+        if (cur >= 0) flush();
         __syncthreads();
 
         // V2[k0][s1][k1][c] = sum_{s2, c'} C[c'][k2] M_{s1,s2}[k0][k1][k2] (c = s2 + c'):

@@ -22,8 +22,8 @@
 // (k0, k1 pair, k2): Gt is stored as (k1, k1 + 1) pairs, 520 floats per cell so
 // that lanes in neighbouring cells read different banks).
 //
-// Work items are the slabs of the dense tiles, in pieces of at most the plan's
-// dense_chunk nodes (pad = the slab), largest first, from a shared counter.
+// Work items are the slabs of the dense tiles, in pieces of at most 8192 nodes
+// (pad = the slab), largest first, from a shared counter.
 #include "device.cuh"
 #include "internal.h"
 
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(SM_NT, 2) gather3_moments(GatherMomentArgs a) 
 // The dense tiles' slab pieces of a one-column interpolation (the tensor-core kernel
 // takes the rest).
 cudaError_t launch_gather3_moments(Plan &P, int op, double *y, cudaStream_t s) {
-    if (P.nslab == 0) return cudaSuccess;
+    if (P.ngslab == 0) return cudaSuccess;
     GatherMomentArgs a{};
     a.pts = reinterpret_cast<const PointF *>(P.pts);
     a.perm = P.perm;
@@ -264,8 +264,8 @@ cudaError_t launch_gather3_moments(Plan &P, int op, double *y, cudaStream_t s) {
     a.dinv = P.dinv_sorted;
     a.degree_out = P.degree;
     a.dinv_out = P.dinv_sorted;
-    a.items = P.slab_items;
-    a.nitems = P.nslab;
+    a.items = P.gslab_items;
+    a.nitems = P.ngslab;
     for (int i = 0; i < 3; ++i) {
         a.ntile[i] = P.ntile[i];
         a.L[i] = P.L[i];
@@ -284,7 +284,7 @@ cudaError_t launch_gather3_moments(Plan &P, int op, double *y, cudaStream_t s) {
     NFL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather3_moments, SM_NT, SM_SMEM));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * P.num_sms;
-    if (grid > P.nslab) grid = P.nslab;
+    if (grid > P.ngslab) grid = P.ngslab;
     gather3_moments<<<(unsigned)grid, SM_NT, SM_SMEM, s>>>(a);
     return cudaGetLastError();
 }

@@ -38,6 +38,7 @@ constexpr int kBlockCols = 8;   // columns a block product takes through each st
 constexpr int kPolyCoef = 10;   // window polynomial degree 9
 constexpr int kCheb = 8;        // Chebyshev basis of the dense-cell spread (degree 7)
 constexpr int kDenseCell = 32;       // nodes per occupied cell from which a tile is spread by moments
+constexpr int kGatherPiece = 8192;   // most nodes per slab piece of the moment interpolation
 
 // Per-column buffers of block products (see Plan::blk).
 struct BlockBuffers {
@@ -87,10 +88,11 @@ struct Plan {
     // sparse tiles for the warp spread, and the chunks of the dense tiles
     // the one-column spread and interpolation with dense cells: the warp-slice spread's
     // runs of sparse tiles, the tensor-core interpolation's chunks of sparse tiles and
-    // the dense tiles' slab pieces (at most dense_chunk nodes, pad = the slab) that both
-    // moment kernels take; each list largest first
-    int64_t nsparse = 0, ngsparse = 0, nslab = 0;
-    WorkItem *sparse_items = nullptr, *gsparse_items = nullptr, *slab_items = nullptr;
+    // the dense tiles' slab pieces (pad = the slab): at most dense_chunk nodes for the
+    // moment spread (its FP32 sums run over one piece), kGatherPiece for the moment
+    // interpolation (each piece forms its slab's moments once); each list largest first
+    int64_t nsparse = 0, ngsparse = 0, nslab = 0, ngslab = 0;
+    WorkItem *sparse_items = nullptr, *gsparse_items = nullptr, *slab_items = nullptr, *gslab_items = nullptr;
     int slide_tiles = 8;                // most tiles in one sliding run of the warp spread
     int chunk = 8192;                   // most nodes in one work item (tile chunk, sliding run)
     int dense_cell = kDenseCell;        // nodes per occupied cell from which a tile is dense
@@ -294,7 +296,7 @@ std::vector<WorkItem> spread_item_list(const Plan &P);
 // and the launch over the dense chunks (one column)
 bool moments_available(const Plan &P);
 struct ItemLists {
-    std::vector<WorkItem> sparse, gsparse, slab;
+    std::vector<WorkItem> sparse, gsparse, slab, gslab;
 };
 ItemLists split_item_lists(const Plan &P);
 cudaError_t launch_spread3_moments(Plan &P, cudaStream_t s);

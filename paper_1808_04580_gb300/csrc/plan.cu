@@ -328,6 +328,8 @@ ItemLists split_item_lists(const Plan &P) {
             for (int sl = 0; sl < te; ++sl) {
                 for (int32_t s0 = 0; s0 < tc[1 + sl]; s0 += P.dense_chunk)
                     L.slab.push_back(WorkItem{tile, start + s0, std::min(P.dense_chunk, tc[1 + sl] - s0), sl});
+                for (int32_t s0 = 0; s0 < tc[1 + sl]; s0 += kGatherPiece)
+                    L.gslab.push_back(WorkItem{tile, start + s0, std::min(kGatherPiece, tc[1 + sl] - s0), sl});
                 start += tc[1 + sl];
             }
         } else {
@@ -338,7 +340,7 @@ ItemLists split_item_lists(const Plan &P) {
     L.sparse = slide_items(rest, P.ntile[P.d - 1], P.slide_tiles, P.chunk);
     L.gsparse = rest;
     const auto by_size = [](const WorkItem &x, const WorkItem &y) { return x.count > y.count; };
-    for (std::vector<WorkItem> *v : {&L.sparse, &L.gsparse, &L.slab})
+    for (std::vector<WorkItem> *v : {&L.sparse, &L.gsparse, &L.slab, &L.gslab})
         std::stable_sort(v->begin(), v->end(), by_size);
     return L;
 }
@@ -353,14 +355,14 @@ static nfl_status ensure_list(WorkItem *&dst, int64_t &have, int64_t cnt) {
     return NFL_OK;
 }
 
-// Stores the three lists on the device: through the page-locked staging (room for all
-// three lists, copied on `stream`) at plan creation, by synchronous copies otherwise.
+// Stores the four lists on the device: through the page-locked staging (room for all
+// four lists, copied on `stream`) at plan creation, by synchronous copies otherwise.
 static nfl_status store_item_lists(Plan &P, const ItemLists &L, WorkItem *staging, cudaStream_t stream) {
-    const std::vector<WorkItem> *src[3] = {&L.sparse, &L.gsparse, &L.slab};
-    WorkItem **dst[3] = {&P.sparse_items, &P.gsparse_items, &P.slab_items};
-    int64_t *cnt[3] = {&P.nsparse, &P.ngsparse, &P.nslab};
+    const std::vector<WorkItem> *src[4] = {&L.sparse, &L.gsparse, &L.slab, &L.gslab};
+    WorkItem **dst[4] = {&P.sparse_items, &P.gsparse_items, &P.slab_items, &P.gslab_items};
+    int64_t *cnt[4] = {&P.nsparse, &P.ngsparse, &P.nslab, &P.ngslab};
     if (!staging && cudaStreamSynchronize(P.stream) != cudaSuccess) return NFL_ERR_CUDA;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         int64_t have = *cnt[k];
         if (ensure_list(*dst[k], have, (int64_t)src[k]->size()) != NFL_OK) return NFL_ERR_OUT_OF_MEMORY;
         *cnt[k] = (int64_t)src[k]->size();
@@ -379,7 +381,7 @@ static nfl_status store_item_lists(Plan &P, const ItemLists &L, WorkItem *stagin
 }
 
 static size_t list_items(const ItemLists &L) {
-    return L.sparse.size() + L.gsparse.size() + L.slab.size();
+    return L.sparse.size() + L.gsparse.size() + L.slab.size() + L.gslab.size();
 }
 
 nfl_status rebuild_spread_items(Plan &P) {
@@ -761,6 +763,7 @@ static void free_plan(Plan *P) {
     cudaFree(P->sparse_items);
     cudaFree(P->gsparse_items);
     cudaFree(P->slab_items);
+    cudaFree(P->gslab_items);
     cudaFree(P->tile_start);
     cudaFree(P->pts);
     cudaFree(P->perm);

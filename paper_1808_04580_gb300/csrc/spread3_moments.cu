@@ -126,9 +126,12 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
 
         // moments: warp g takes the g-th eighth of the item in slices of 32 nodes and
         // carries its sums across slices while the cell stays the same
-        unsigned long long acc[2][R / 2];
+        // acc sums one run segment of a slice (at most 32 nodes), accr the segments of the
+        // current cell (blocked summation: the FP32 error grows with 32 + nodes / 32)
+        unsigned long long acc[2][R / 2], accr[2][R / 2];
 #pragma unroll
-        for (int p = 0; p < R / 2; ++p) acc[0][p] = acc[1][p] = 0ull;
+        for (int p = 0; p < R / 2; ++p) accr[0][p] = accr[1][p] = 0ull;
+        const unsigned long long one2 = pack2(1.f, 1.f);
         int cur = -1;
         // the sums of cell cur into its moments; the accumulators start again from zero
         auto flush = [&]() {
@@ -137,9 +140,9 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
             for (int c = 0; c < 2; ++c)
 #pragma unroll
                 for (int p = 0; p < R / 2; ++p) {
-                    atomicAdd(mrow + 2 * p * R * R + c, lane_of(acc[c][p], 0));
-                    atomicAdd(mrow + (2 * p + 1) * R * R + c, lane_of(acc[c][p], 1));
-                    acc[c][p] = 0ull;
+                    atomicAdd(mrow + 2 * p * R * R + c, lane_of(accr[c][p], 0));
+                    atomicAdd(mrow + (2 * p + 1) * R * R + c, lane_of(accr[c][p], 1));
+                    accr[c][p] = 0ull;
                 }
         };
         const int share = (w.count + NWM - 1) / NWM;
@@ -190,7 +193,9 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
                     if (cur >= 0) flush();
                     cur = ci;
                 }
-                // acc[c][p] += sum over the run of (T_2p(t0), T_2p+1(t0)) x~ T_k1(t1) T_c0+c(t2)
+                // acc[c][p] = sum over the segment of (T_2p(t0), T_2p+1(t0)) x~ T_k1(t1) T_c0+c(t2)
+#pragma unroll
+                for (int p = 0; p < R / 2; ++p) acc[0][p] = acc[1][p] = 0ull;
                 int q = i;
                 // four nodes' rows loaded before their multiply-adds
                 for (; q + 4 <= j; q += 4) {
@@ -204,6 +209,11 @@ __global__ void __launch_bounds__(NTM, 2) spread3_moments(MomentArgs a) {
                     NodeRow d;
                     d.load(stage + q * ROW, k1, c0);
                     d.add(acc);
+                }
+#pragma unroll
+                for (int p = 0; p < R / 2; ++p) {
+                    accr[0][p] = ffma2(acc[0][p], one2, accr[0][p]);
+                    accr[1][p] = ffma2(acc[1][p], one2, accr[1][p]);
                 }
                 i = j;
             }

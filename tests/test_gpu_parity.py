@@ -206,7 +206,8 @@ def test_slab_moments_edge_cases(kind, n, N, p, eps_B, prec, tol):
     for tuned in (False, True):
         if tuned:
             plan.autotune()
-        assert_close(plan.apply_W(gpu(x)).cpu().numpy(), yw_ref, tol, x=x)
+        err = assert_close(plan.apply_W(gpu(x)).cpu().numpy(), yw_ref, tol, x=x)
+        print("slab %s %s tuned=%s:" % (kind, prec, tuned), err)
         yl = plan.apply_Ls(gpu(x)).cpu().numpy()
         assert_close(x - yl, x - yl_ref, tol)
     np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)

@@ -126,7 +126,7 @@ typedef struct {
                              Chebyshev moments                                 */
     int chunk;            /* most nodes in one work item                       */
     int dense_cell;       /* nodes per occupied cell from which a tile is dense */
-    int dense_chunk;      /* most nodes in one slab piece of the moment kernels */
+    int dense_chunk;      /* most nodes in one slab piece of the moment spread */
 } nfl_info;
 
 /*
@@ -199,7 +199,7 @@ nfl_status nfl_plan_info(const nfl_plan *plan, nfl_info *info);
  *                  a tile goes to the moment kernels (spread and
  *                  interpolation), from {16, 32, 64};
  *   dense_chunk    the same plans: most nodes in one slab piece of the
- *                  moment kernels, from {512, 1024, 2048};
+ *                  moment spread, from {2048, 4096, 8192};
  *   slide_tiles    3-D warp-slice spread: most tiles of one axis-2 run that
  *                  the tile copies slide along (1 = no sliding), from
  *                  {1, 4, 8, 16}.

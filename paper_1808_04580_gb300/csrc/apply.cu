@@ -340,9 +340,8 @@ nfl_status nfl_plan_autotune(nfl_plan *plan, double *best_ms) {
             P.dense_cell = v;
             return nfl::rebuild_spread_items(P);
         });
-        // most nodes per slab piece of the moment kernels (FP32 moment sums run over
-        // one piece, so no more than the warp-slice kernel's 2048 per tile copy)
-        const int dch[3] = {512, 1024, 2048};
+        // most nodes per slab piece of the moment spread
+        const int dch[3] = {2048, 4096, 8192};
         if (st == NFL_OK)
             st = tune(P.dense_chunk, dch, 3, [&](int v) {
                 P.dense_chunk = v;

@@ -89,14 +89,14 @@ struct Plan {
     // the one-column spread and interpolation with dense cells: the warp-slice spread's
     // runs of sparse tiles, the tensor-core interpolation's chunks of sparse tiles and
     // the dense tiles' slab pieces (pad = the slab): at most dense_chunk nodes for the
-    // moment spread (its FP32 sums run over one piece), kGatherPiece for the moment
-    // interpolation (each piece forms its slab's moments once); each list largest first
+    // moment spread, kGatherPiece for the moment interpolation (each piece forms or
+    // expands its slab's moments once); each list largest first
     int64_t nsparse = 0, ngsparse = 0, nslab = 0, ngslab = 0;
     WorkItem *sparse_items = nullptr, *gsparse_items = nullptr, *slab_items = nullptr, *gslab_items = nullptr;
     int slide_tiles = 8;                // most tiles in one sliding run of the warp spread
     int chunk = 8192;                   // most nodes in one work item (tile chunk, sliding run)
     int dense_cell = kDenseCell;        // nodes per occupied cell from which a tile is dense
-    int dense_chunk = 2048;             // most nodes in one slab piece of the moment kernels
+    int dense_chunk = 8192;             // most nodes in one slab piece of the moment spread
     int fft_cap = 512;                  // FFT passes: grid points per CTA
 
     // tile-sorted nodes

@@ -29,8 +29,9 @@
 // 180,000 multiply-adds per slab instead of 29,000 per occupied cell, and adds
 // the block to the global grid: FP32 atomics, or for FP32C 64-bit fixed point
 // (scale 2^k from sum |x~|, so nothing can overflow) with integer atomics.
-// FP32 moment sums run over the nodes of one work item (at most 2048, no more
-// than the warp-slice kernel's tile copies) before the exact integer part.
+// FP32 moment sums are blocked: a lane sums a run segment of one slice (at most
+// 32 nodes), then the segments of the cell in its eighth of the work item, and
+// the cell's moments in shared memory add one such sum per warp.
 #include <type_traits>
 
 #include "device.cuh"

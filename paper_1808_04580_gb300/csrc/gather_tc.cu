@@ -255,76 +255,80 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 fetch(base + 128);
                 // window taps: Horner in t = 2f - 1, two taps per fma.rn.f32x2; axes 1 and 2
                 // first (kept for the contraction), then axis 0 (the A operand)
-                const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
-                {
-                    float tap1[TAPS], tap2[TAPS];
-                    const unsigned long long T1 = pack2(fmaf(2.f, f1, -1.f), fmaf(2.f, f1, -1.f));
-                    const unsigned long long T2 = pack2(fmaf(2.f, f2, -1.f), fmaf(2.f, f2, -1.f));
+                // a warp with no node in this batch leaves its rows of A as they are: they
+                // only reach rows of T that nothing reads
+                if (warp * 32 < nb) {
+                    const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(&polys[0][0]);
+                    {
+                        float tap1[TAPS], tap2[TAPS];
+                        const unsigned long long T1 = pack2(fmaf(2.f, f1, -1.f), fmaf(2.f, f1, -1.f));
+                        const unsigned long long T2 = pack2(fmaf(2.f, f2, -1.f), fmaf(2.f, f2, -1.f));
 #pragma unroll
-                    for (int q = 0; q < M; ++q) {
-                        // coefficient pairs (k, k + 1) with 16-byte loads; Horner from k = 9 down
-                        const ulonglong2 *pq = reinterpret_cast<const ulonglong2 *>(pc + q * kPolyCoef);
-                        ulonglong2 cc = pq[kPolyCoef / 2 - 1];
-                        unsigned long long h1 = cc.y, h2 = cc.y;
-                        h1 = ffma2(h1, T1, cc.x);
-                        h2 = ffma2(h2, T2, cc.x);
-#pragma unroll
-                        for (int i = kPolyCoef / 2 - 2; i >= 0; --i) {
-                            cc = pq[i];
-                            h1 = ffma2(h1, T1, cc.y);
-                            h2 = ffma2(h2, T2, cc.y);
+                        for (int q = 0; q < M; ++q) {
+                            // coefficient pairs (k, k + 1) with 16-byte loads; Horner from k = 9 down
+                            const ulonglong2 *pq = reinterpret_cast<const ulonglong2 *>(pc + q * kPolyCoef);
+                            ulonglong2 cc = pq[kPolyCoef / 2 - 1];
+                            unsigned long long h1 = cc.y, h2 = cc.y;
                             h1 = ffma2(h1, T1, cc.x);
                             h2 = ffma2(h2, T2, cc.x);
+#pragma unroll
+                            for (int i = kPolyCoef / 2 - 2; i >= 0; --i) {
+                                cc = pq[i];
+                                h1 = ffma2(h1, T1, cc.y);
+                                h2 = ffma2(h2, T2, cc.y);
+                                h1 = ffma2(h1, T1, cc.x);
+                                h2 = ffma2(h2, T2, cc.x);
+                            }
+                            tap1[2 * q] = lane_of(h1, 0);
+                            tap1[2 * q + 1] = lane_of(h1, 1);
+                            tap2[2 * q] = lane_of(h2, 0);
+                            tap2[2 * q + 1] = lane_of(h2, 1);
                         }
-                        tap1[2 * q] = lane_of(h1, 0);
-                        tap1[2 * q + 1] = lane_of(h1, 1);
-                        tap2[2 * q] = lane_of(h2, 0);
-                        tap2[2 * q + 1] = lane_of(h2, 1);
-                    }
-                    if constexpr (BF16) {
+                        if constexpr (BF16) {
 #pragma unroll
-                        for (int j = 0; j < TAPS; ++j) {
-                            tap1[j] = round_bf16(tap1[j]);
-                            tap2[j] = round_bf16(tap2[j]);
+                            for (int j = 0; j < TAPS; ++j) {
+                                tap1[j] = round_bf16(tap1[j]);
+                                tap2[j] = round_bf16(tap2[j]);
+                            }
                         }
+                        place_taps<TAPS, PA, TE>(tap1, s1, w1p);
+                        place_taps<TAPS, PA, TE>(tap2, s2, w2p);
                     }
-                    place_taps<TAPS, PA, TE>(tap1, s1, w1p);
-                    place_taps<TAPS, PA, TE>(tap2, s2, w2p);
-                }
-                {
-                    // A operand row tid: axis-0 window, hi/lo TF32 parts, written four values at a time
-                    float tap0[TAPS];
-                    const unsigned long long T0 = pack2(fmaf(2.f, f0, -1.f), fmaf(2.f, f0, -1.f));
+                    {
+                        // A operand row tid: axis-0 window, hi/lo TF32 parts, written four values at a time
+                        float tap0[TAPS];
+                        const unsigned long long T0 = pack2(fmaf(2.f, f0, -1.f), fmaf(2.f, f0, -1.f));
 #pragma unroll
-                    for (int q = 0; q < M; ++q) {
-                        const ulonglong2 *pq = reinterpret_cast<const ulonglong2 *>(pc + q * kPolyCoef);
-                        ulonglong2 cc = pq[kPolyCoef / 2 - 1];
-                        unsigned long long h0 = ffma2(cc.y, T0, cc.x);
+                        for (int q = 0; q < M; ++q) {
+                            const ulonglong2 *pq = reinterpret_cast<const ulonglong2 *>(pc + q * kPolyCoef);
+                            ulonglong2 cc = pq[kPolyCoef / 2 - 1];
+                            unsigned long long h0 = ffma2(cc.y, T0, cc.x);
 #pragma unroll
-                        for (int i = kPolyCoef / 2 - 2; i >= 0; --i) {
-                            cc = pq[i];
-                            h0 = ffma2(h0, T0, cc.y);
-                            h0 = ffma2(h0, T0, cc.x);
+                            for (int i = kPolyCoef / 2 - 2; i >= 0; --i) {
+                                cc = pq[i];
+                                h0 = ffma2(h0, T0, cc.y);
+                                h0 = ffma2(h0, T0, cc.x);
+                            }
+                            tap0[2 * q] = live ? lane_of(h0, 0) : 0.f;
+                            tap0[2 * q + 1] = live ? lane_of(h0, 1) : 0.f;
                         }
-                        tap0[2 * q] = live ? lane_of(h0, 0) : 0.f;
-                        tap0[2 * q + 1] = live ? lane_of(h0, 1) : 0.f;
-                    }
-                    if constexpr (BF16) {
+                        if constexpr (BF16) {
 #pragma unroll
-                        for (int j = 0; j < TAPS; ++j) tap0[j] = round_bf16(tap0[j]);
-                    }
-                    float v0[16];
-                    place_taps<TAPS, 16, TE>(tap0, s0, v0);
+                            for (int j = 0; j < TAPS; ++j) tap0[j] = round_bf16(tap0[j]);
+                        }
+                        float v0[16];
+                        place_taps<TAPS, 16, TE>(tap0, s0, v0);
 #pragma unroll
-                    for (int kb = 0; kb < 4; ++kb) {
-                        float4 h, l;
-                        h.x = to_tf32(v0[4 * kb + 0]); l.x = to_tf32(v0[4 * kb + 0] - h.x);
-                        h.y = to_tf32(v0[4 * kb + 1]); l.y = to_tf32(v0[4 * kb + 1] - h.y);
-                        h.z = to_tf32(v0[4 * kb + 2]); l.z = to_tf32(v0[4 * kb + 2] - h.z);
-                        h.w = to_tf32(v0[4 * kb + 3]); l.w = to_tf32(v0[4 * kb + 3] - h.w);
-                        const uint32_t off = kmajor_off(tid, 4 * kb);
-                        *reinterpret_cast<float4 *>(sA_hi + off) = h;
-                        *reinterpret_cast<float4 *>(sA_lo + off) = l;
+                        for (int kb = 0; kb < 4; ++kb) {
+                            float4 h, l;
+                            h.x = to_tf32(v0[4 * kb + 0]); l.x = to_tf32(v0[4 * kb + 0] - h.x);
+                            h.y = to_tf32(v0[4 * kb + 1]); l.y = to_tf32(v0[4 * kb + 1] - h.y);
+                            h.z = to_tf32(v0[4 * kb + 2]); l.z = to_tf32(v0[4 * kb + 2] - h.z);
+                            h.w = to_tf32(v0[4 * kb + 3]); l.w = to_tf32(v0[4 * kb + 3] - h.w);
+                            const uint32_t off = kmajor_off(tid, 4 * kb);
+                            *reinterpret_cast<float4 *>(sA_hi + off) = h;
+                            *reinterpret_cast<float4 *>(sA_lo + off) = l;
+                        }
                     }
                 }
             }
@@ -373,7 +377,9 @@ __global__ void __launch_bounds__(128, 4) gather3_tc(GatherTCArgs a) {
                 }
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                if (!failed) {
+                // a warp with no node in this batch (the last, partial batch of an item)
+                // skips its rows of T
+                if (!failed && warp * 32 < nb) {
                     // thread tid owns TMEM lane tid: contract this half of its row of T with w1 w2
                     const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll

@@ -84,6 +84,109 @@ static nfl_status run_block(Plan &P, int op, const double *x, int64_t ldx, doubl
     return rs;
 }
 
+// The second staging buffers, their stream and events, made once (refused under stream
+// capture, which allocation would invalidate: the caller then takes the plain loop).
+static bool ensure_pipeline(Plan &P) {
+    if (P.pipe_stream) return true;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(P.stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return false;
+    if (cudaMalloc(&P.pipe_xsort, P.n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&P.pipe_xsorted, P.n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&P.pipe_scratch, 64 * sizeof(double)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P.pipe_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P.pipe_spread_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P.pipe_staged[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P.pipe_staged[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&P.pipe_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// Several one-column products (3-D, FP32 / FP32C, staged): the staging of column c + 1
+// (a DRAM-bound gather of x) runs on the pipeline stream into the other staging buffer
+// while column c's FFT passes and interpolation run, the kernels that leave it room on
+// the SMs.  Column c waits for its staging; the staging of c + 1 waits for the spread of
+// c, after which nothing reads its buffer (columns c - 1 and c + 1 share it).  Cols gives
+// each column's device x and y and the hooks of host-buffer products (copies in before
+// the staging, the y slot free before the interpolation, the copy out after it).
+struct DeviceColumns {
+    const double *x;
+    int64_t ldx;
+    double *y;
+    int64_t ldy;
+    const double *xc(int c) const { return x + c * ldx; }
+    double *yc(int c) const { return y + c * ldy; }
+    cudaError_t before_stage(int, cudaStream_t) { return cudaSuccess; }
+    cudaError_t before_gather(int, cudaStream_t) { return cudaSuccess; }
+    cudaError_t after_column(int, cudaStream_t) { return cudaSuccess; }
+};
+
+template <class Cols>
+static nfl_status run_columns_pipelined(Plan &P, int op, int nrhs, Cols &cols) {
+    const bool scale = (op == OP_A || op == OP_LS);
+    const cudaStream_t M = P.stream, S = P.pipe_stream;
+    void *const xs[2] = {P.xsort, P.pipe_xsort};
+    double *const zs[2] = {P.xsorted, P.pipe_xsorted};
+    double *const sc[2] = {P.scratch, P.pipe_scratch};
+    // the plan's stream and staging buffers as they were, however the products end
+    struct Restore {
+        Plan &P;
+        cudaStream_t s;
+        void *x;
+        double *z, *c;
+        ~Restore() {
+            P.stream = s;
+            P.xsort = x;
+            P.xsorted = z;
+            P.scratch = c;
+        }
+    } restore{P, M, xs[0], zs[0], sc[0]};
+    auto use = [&](int b, cudaStream_t s) {
+        P.stream = s;
+        P.xsort = xs[b];
+        P.xsorted = zs[b];
+        P.scratch = sc[b];
+    };
+    auto stage = [&](int c) -> cudaError_t {
+        NFL_CUDA_TRY(cols.before_stage(c, S));
+        use(c & 1, S);
+        NFL_CUDA_TRY(stage_spread3_values(P, op, cols.xc(c), P.n, 1, false, scale));
+        return cudaEventRecord(P.pipe_staged[c & 1], S);
+    };
+    NFL_STATUS_TRY(cudaEventRecord(P.pipe_fork, M));
+    NFL_STATUS_TRY(cudaStreamWaitEvent(S, P.pipe_fork, 0));
+    NFL_STATUS_TRY(stage(0));
+    for (int c = 0; c < nrhs; ++c) {
+        const int b = c & 1;
+        use(b, M);
+        NFL_STATUS_TRY(cudaStreamWaitEvent(M, P.pipe_staged[b], 0));
+        NFL_STATUS_TRY(mark(P, 0));
+        NFL_STATUS_TRY(clear_spread(P, 1));
+        NFL_STATUS_TRY(mark(P, 1));
+        NFL_STATUS_TRY(launch_spread(P, cols.xc(c), 0, false, scale));
+        NFL_STATUS_TRY(mark(P, 2));
+        if (c + 1 < nrhs) {
+            NFL_STATUS_TRY(cudaEventRecord(P.pipe_spread_done, M));
+            NFL_STATUS_TRY(cudaStreamWaitEvent(S, P.pipe_spread_done, 0));
+            NFL_STATUS_TRY(stage(c + 1));
+            use(b, M);
+        }
+        NFL_STATUS_TRY(launch_fft(P));
+        NFL_STATUS_TRY(mark(P, 3));
+        NFL_STATUS_TRY(cols.before_gather(c, M));
+        NFL_STATUS_TRY(launch_gather(P, op, cols.xc(c), cols.yc(c)));
+        NFL_STATUS_TRY(mark(P, 4));
+        NFL_STATUS_TRY(cols.after_column(c, M));
+    }
+    return NFL_OK;
+}
+
+static bool pipeline_available(const Plan &P) {
+    return P.d == 3 && column_tile_edge(P.m) == P.tile_edge && P.prec != NFL_PREC_FP64;
+}
+
 static nfl_status apply(nfl_plan *plan, int op, const double *x, int64_t ldx, double *y, int64_t ldy, int nrhs) {
     if (!plan || !x || !y || nrhs < 1) return NFL_ERR_INVALID_ARG;
     Plan &P = *reinterpret_cast<Plan *>(plan);
@@ -96,6 +199,10 @@ static nfl_status apply(nfl_plan *plan, int op, const double *x, int64_t ldx, do
             if (st != NFL_OK) return st;
         }
         return NFL_OK;
+    }
+    if (nrhs > 1 && pipeline_available(P) && ensure_pipeline(P)) {
+        DeviceColumns cols{x, ldx, y, ldy};
+        return run_columns_pipelined(P, op, nrhs, cols);
     }
     for (int c = 0; c < nrhs; ++c) {
         nfl_status st = run_column(P, op, x + c * ldx, y + c * ldy);
@@ -160,6 +267,37 @@ static cudaError_t issue_host_column(Plan &P, int op, const double *x, double *y
     return cudaEventRecord(P.ev_out[s], P.d2h);
 }
 
+// The columns of a host-buffer product in the pipelined order: column c's x copied into
+// slot c mod kHostSlots before its staging, its y slot free (the copy out of column
+// c - kHostSlots done) before its interpolation, its y copied out after it.
+struct HostColumns {
+    Plan &P;
+    const double *x;
+    int64_t ldx;
+    double *y;
+    int64_t ldy;
+    const double *xc(int c) const { return P.host_stage + (size_t)(c % kHostSlots) * P.n; }
+    double *yc(int c) const { return P.host_stage + (size_t)(kHostSlots + c % kHostSlots) * P.n; }
+    cudaError_t before_stage(int c, cudaStream_t S) {
+        const int s = c % kHostSlots;
+        if (c >= kHostSlots) NFL_CUDA_TRY(cudaStreamWaitEvent(P.h2d, P.ev_done[s], 0));   // slot's x read
+        NFL_CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(xc(c)), x + c * ldx, sizeof(double) * (size_t)P.n,
+                                     cudaMemcpyDefault, P.h2d));
+        NFL_CUDA_TRY(cudaEventRecord(P.ev_in[s], P.h2d));
+        return cudaStreamWaitEvent(S, P.ev_in[s], 0);
+    }
+    cudaError_t before_gather(int c, cudaStream_t M) {
+        return c >= kHostSlots ? cudaStreamWaitEvent(M, P.ev_out[c % kHostSlots], 0) : cudaSuccess;
+    }
+    cudaError_t after_column(int c, cudaStream_t M) {
+        const int s = c % kHostSlots;
+        NFL_CUDA_TRY(cudaEventRecord(P.ev_done[s], M));
+        NFL_CUDA_TRY(cudaStreamWaitEvent(P.d2h, P.ev_done[s], 0));
+        NFL_CUDA_TRY(cudaMemcpyAsync(y + c * ldy, yc(c), sizeof(double) * (size_t)P.n, cudaMemcpyDefault, P.d2h));
+        return cudaEventRecord(P.ev_out[s], P.d2h);
+    }
+};
+
 static nfl_status apply_host(nfl_plan *plan, int op, const double *x, int64_t ldx, double *y, int64_t ldy,
                              int nrhs) {
     if (!plan || !x || !y || nrhs < 1 || op < 0 || op > 2) return NFL_ERR_INVALID_ARG;
@@ -172,8 +310,13 @@ static nfl_status apply_host(nfl_plan *plan, int op, const double *x, int64_t ld
     cudaError_t e = cudaEventRecord(P.ev_start, P.stream);   // copies follow the work queued before
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P.h2d, P.ev_start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P.d2h, P.ev_start, 0);
-    for (int c = 0; c < nrhs && e == cudaSuccess && st == NFL_OK; ++c)
-        e = issue_host_column(P, ops[op], x + c * ldx, y + c * ldy, c, st);
+    if (e == cudaSuccess && nrhs > 1 && pipeline_available(P) && ensure_pipeline(P)) {
+        HostColumns cols{P, x, ldx, y, ldy};
+        st = run_columns_pipelined(P, ops[op], nrhs, cols);
+    } else {
+        for (int c = 0; c < nrhs && e == cudaSuccess && st == NFL_OK; ++c)
+            e = issue_host_column(P, ops[op], x + c * ldx, y + c * ldy, c, st);
+    }
     // wait for everything issued, also after an error: y is final and x free on return
     const cudaError_t e1 = cudaStreamSynchronize(P.h2d);
     const cudaError_t e2 = cudaStreamSynchronize(P.stream);

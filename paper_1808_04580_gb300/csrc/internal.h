@@ -150,6 +150,14 @@ struct Plan {
     cudaEvent_t ev_start = nullptr;
     cudaEvent_t ev_in[kHostSlots] = {}, ev_done[kHostSlots] = {}, ev_out[kHostSlots] = {};
 
+    // several one-column products in one call: a second set of staging buffers and the
+    // stream that stages column c + 1 while column c is transformed and interpolated
+    // (made on the first such call)
+    void *pipe_xsort = nullptr;
+    double *pipe_xsorted = nullptr, *pipe_scratch = nullptr;
+    cudaStream_t pipe_stream = nullptr;
+    cudaEvent_t pipe_fork = nullptr, pipe_spread_done = nullptr, pipe_staged[2] = {};
+
     // stage timing: 5 events per timed column (before prep, spread, fft, gather, after)
     bool profile = false;
     std::vector<cudaEvent_t> events;
@@ -163,6 +171,8 @@ inline bool points_are_double(int prec) { return prec == NFL_PREC_FP64; }
 
 // launchers (stream-ordered, no host sync)
 cudaError_t prepare_spread(Plan &P, int op, const double *x, int64_t ldx, int nc, bool ones, bool scale_dinv);
+// the grid and work counters cleared for a product (the first half of prepare_spread)
+cudaError_t clear_spread(Plan &P, int nc);
 cudaError_t launch_spread(Plan &P, const double *x, int64_t col_off, bool ones, bool scale_dinv);
 cudaError_t launch_fft(Plan &P, int nc = 1);
 cudaError_t launch_gather(Plan &P, int op, const double *x, double *y);

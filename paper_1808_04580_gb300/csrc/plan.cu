@@ -744,6 +744,15 @@ static void free_plan(Plan *P) {
     }
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     if (P->join_ev) cudaEventDestroy(P->join_ev);
+    if (P->pipe_stream) {
+        cudaStreamSynchronize(P->pipe_stream);
+        cudaStreamDestroy(P->pipe_stream);
+    }
+    for (cudaEvent_t e : {P->pipe_fork, P->pipe_spread_done, P->pipe_staged[0], P->pipe_staged[1]})
+        if (e) cudaEventDestroy(e);
+    cudaFree(P->pipe_xsort);
+    cudaFree(P->pipe_xsorted);
+    cudaFree(P->pipe_scratch);
     for (cudaEvent_t e : P->events) cudaEventDestroy(e);
     if (P->h2d) cudaStreamSynchronize(P->h2d);
     if (P->d2h) cudaStreamSynchronize(P->d2h);

@@ -218,10 +218,14 @@ cudaError_t launch_fixed_scale(Plan &P, const double *x, bool ones, bool scale_d
     return cudaGetLastError();
 }
 
-cudaError_t prepare_spread(Plan &P, int op, const double *x, int64_t ldx, int nc, bool ones, bool scale_dinv) {
+cudaError_t clear_spread(Plan &P, int nc) {
     size_t elem = P.prec == NFL_PREC_FP32 ? sizeof(float) : 8;
     NFL_CUDA_TRY(cudaMemsetAsync(P.grid, 0, P.box_elems * elem * nc, P.stream));
-    NFL_CUDA_TRY(cudaMemsetAsync(P.work_counter, 0, 4 * sizeof(unsigned), P.stream));
+    return cudaMemsetAsync(P.work_counter, 0, 4 * sizeof(unsigned), P.stream);
+}
+
+cudaError_t prepare_spread(Plan &P, int op, const double *x, int64_t ldx, int nc, bool ones, bool scale_dinv) {
+    NFL_CUDA_TRY(clear_spread(P, nc));
     if (P.d == 3 && column_tile_edge(P.m) == P.tile_edge)
         return stage_spread3_values(P, op, x, ldx, nc, ones, scale_dinv);
     if (nc != 1) return cudaErrorInvalidValue;

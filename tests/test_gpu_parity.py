@@ -212,7 +212,11 @@ def test_slab_moments_edge_cases(kind, n, N, p, eps_B, prec, tol):
         print("slab %s %s tuned=%s:" % (kind, prec, tuned), err)
         yl = plan.apply_Ls(gpu(x)).cpu().numpy()
         assert_close(x - yl, x - yl_ref, tol)
-    np.testing.assert_allclose(plan.degree().cpu().numpy(), ref.degree, rtol=tol)
+    # degrees here span two orders of magnitude (87 beside the hot cell's 10^4): the FP32
+    # error is relative to the largest sums, as in the paper's error measure of W x
+    # (max error over ||x||_1 K(0); x = 1), so the bound is absolute at tol * max d
+    deg = plan.degree().cpu().numpy()
+    np.testing.assert_allclose(deg, ref.degree, rtol=tol, atol=tol * ref.degree.max())
     assert plan.info()["device_error"] == 0
 
 
@@ -436,6 +440,32 @@ def test_autotune_keeps_the_products(prec, m, tol):
     assert t["best_ms"] > 0.0
     ref = fastsum.NormalizedFastsum(v, 0.3, 32, m, m).apply_W(x)
     assert_close(p.apply_W(gpu(x)).cpu().numpy(), ref, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32c", 2e-6), ("fp32", 1e-5)])
+@pytest.mark.parametrize("m,N,n", [(7, 32, 3000), (6, 128, 20000)])
+def test_column_pipeline_equals_single_columns(m, N, n, prec, tol):
+    """Several columns in one call without a block path (m = 7; or N = 128, whose grids
+    leave no room for blocks): the staging of each next column runs on a second stream
+    into a second buffer.  Every column equals the same column in a call of its own
+    (bit for bit with FP32C's fixed-point sums), and for m = 7 L_s matches the oracle."""
+    # N = 128: the ball workload's shape, whose full box leaves no room for blocks
+    v = _cloud("clusters", n, 3, seed=95) if m == 7 else workloads.ball_plus_clusters(n, seed=95)
+    p = Plan(gpu(v), 0.3, N, m, m, -1.0, prec)
+    assert p.info()["block_cols"] == 1 or m == 7
+    X = np.random.default_rng(96).standard_normal((n, 5))
+    for op in ("W", "Ls"):
+        fn = getattr(p, "apply_" + op)
+        Y = fn(gpu(X)).cpu().numpy()
+        for c in range(5):
+            yc = fn(gpu(X[:, c])).cpu().numpy()
+            if prec == "fp32c":
+                np.testing.assert_array_equal(Y[:, c], yc)
+            else:
+                assert rel(Y[:, c], yc) < 1e-6
+    if m == 7:
+        ref = fastsum.NormalizedFastsum(v, 0.3, N, m, m).apply_Ls(X[:, 3])
+        assert_close(X[:, 3] - Y[:, 3], X[:, 3] - ref, tol)
 
 
 @pytest.mark.parametrize("prec,m,tol", [("fp32c", 6, 1e-6), ("fp32", 4, 5e-6), ("bf16w", 3, 5e-6)])

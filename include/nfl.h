@@ -227,8 +227,12 @@ nfl_status nfl_degree(const nfl_plan *plan, double *d);
  * The first block product allocates the plan's block buffers (make it
  * before capturing products into a CUDA graph: under capture it returns
  * NFL_ERR_INVALID_ARG instead of allocating); no buffer of the plan is
- * ever reallocated, so captured products stay valid.  The same holds for
- * nfl_apply_A and nfl_apply_Ls.
+ * ever reallocated, so captured products stay valid.  Where columns go one
+ * at a time (block_cols 1) on that path, the staging of column c + 1 runs on a
+ * second stream of the plan beside column c's FFT and interpolation, into a
+ * second set of staging buffers made by the first such call (under capture,
+ * before they exist, the columns go one after another instead).  The same
+ * holds for nfl_apply_A and nfl_apply_Ls, and for nfl_apply_host.
  */
 nfl_status nfl_apply_W(nfl_plan *plan, const double *x, int64_t ldx,
                        double *y, int64_t ldy, int nrhs);
